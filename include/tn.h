@@ -1,0 +1,192 @@
+/*
+ * tn.h -- C ABI of the multiple-amplitude tensor-network contraction library.
+ *
+ * The library computes exact amplitudes <b|U|0^n> of a quantum circuit for a
+ * batch of bitstrings b by contracting the circuit's tensor network along a
+ * fixed contraction tree, sliced over a set of bond indices, with every
+ * intermediate shared by several bitstrings computed once and reused (the
+ * multiple-amplitude "store-and-compute" scheme of the paper's main text,
+ * Eq. (1), and SM Sec. III).  Per-slice partial amplitudes are summed in
+ * complex128 (first-level slicing, SM Sec. IV.B).
+ *
+ * Conventions shared by every entry point
+ *   - Qubit q of a bitstring is column q of a row-major k x n uint8 array
+ *     (values 0/1).  As a basis index, qubit 0 is the most significant bit.
+ *   - Gate matrices are row-major complex128 (re, im interleaved), row =
+ *     output basis state.  A two-qubit gate on (q0, q1) with q0 < q1 uses the
+ *     basis |x_q0 x_q1>, matrix index 2*x_q0 + x_q1 (SM Sec. I).
+ *   - Fused network (SM Sec. II): one tensor per two-qubit gate, numbered in
+ *     gate order; single-qubit gates and the |0> inputs are absorbed into the
+ *     next two-qubit gate on their qubit, the final single-qubit layer into
+ *     the last one.  Bond edge e is the wire segment of one qubit between two
+ *     consecutive two-qubit gates, numbered in creation order while walking
+ *     the two-qubit gates in order and, for each gate (a, b), q in (a, b).
+ *     Every qubit must take part in at least one two-qubit gate.
+ *   - Contraction tree: SSA pair list of (T-1) x 2 int32, leaves 0..T-1,
+ *     pair i creates node T+i, the root is node 2T-2.
+ *   - Slicing: sliced_edges[j] takes the value (s >> j) & 1 in slice s,
+ *     s in [0, 2^n_sliced).  The amplitude is the sum over all slices.
+ *   - Amplitude buffers are complex128 (2 doubles per bitstring), one entry
+ *     per *input* row of the bitstring array, duplicates included.
+ *
+ * Errors: every int-returning call returns TN_OK (0) or a negative code;
+ * tn_last_error() then holds a thread-local message.  Nothing is written to
+ * caller buffers on a host-side validation error.
+ *
+ * Ownership: inputs are copied at plan time.  Device memory (workspace and
+ * amplitude buffers) belongs to the caller; the library allocates no device
+ * memory of its own.  Streams belong to the caller.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    TN_OK = 0,
+    TN_EINVAL = -1,       /* malformed circuit, tree, bitstrings or sliced edge */
+    TN_ENOMEM = -2,       /* workspace smaller than tn_plan_info.workspace_bytes */
+    TN_ECUDA = -3,        /* a CUDA runtime call failed (message has the name) */
+    TN_ETIMEOUT = -4,     /* a bounded device-side wait gave up */
+    TN_EUNSUPPORTED = -5, /* e.g. an intermediate rank above 40 */
+    TN_ESTATE = -6        /* call made in the wrong order (e.g. no workspace) */
+};
+
+/* Arithmetic of the pairwise contractions (accumulation is always FP32;
+ * the cross-slice sum and XEB are FP64). */
+enum {
+    TN_FP32 = 0,    /* complex64 operands, FP32 FMA on the CUDA cores */
+    TN_TF32 = 1,    /* tensor cores, TF32 operands, FP32 accumulate */
+    TN_BF16X3 = 2   /* tensor cores, hi/lo BF16 split, three products */
+};
+
+typedef struct {
+    int32_t q0, q1;   /* q1 = -1 for a single-qubit gate; q0 < q1 otherwise */
+    int32_t layer;    /* informational */
+    int32_t pad;
+    double m[32];     /* 2x2 (first 8 doubles) or 4x4 complex128, row-major */
+} tn_gate;
+
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_gates;
+    const tn_gate *gates;   /* in time order */
+} tn_circuit;
+
+typedef struct {
+    int64_t workspace_limit;  /* bytes the plan may use; <= 0: 64 GiB */
+    int32_t slice_batch_log2; /* sliced edges run side by side in one pass;
+                                 -1: largest that fits workspace_limit */
+    int32_t rescale;          /* 1: per-instance power-of-two rescaling */
+    int32_t fuse;             /* 1: rewrite chains of big x small steps into
+                                 one GEMM against a pre-contracted operator */
+    int32_t fuse_max_bits;    /* d^t: largest K or N bit count of a fused
+                                 chain operator (SM Sec. V.C); 0: default 7 */
+    int32_t reserved[10];
+} tn_options;
+
+typedef struct {
+    int32_t n_tensors, n_edges, n_nodes, n_steps;
+    int32_t n_unique;             /* distinct bitstrings */
+    int32_t n_sliced, slice_batch_log2, n_batches;
+    int32_t max_rank;             /* largest per-instance intermediate rank */
+    int32_t n_static_steps;       /* steps independent of the sliced edges */
+    double flops_ma;              /* Eq. (1) summed over all slices: 8 per complex MAC */
+    double flops_sa;              /* single-amplitude cost of all slices times k_unique */
+    double flops_exec;            /* flops the executed schedule performs */
+    double bytes_min;             /* algorithmic bytes: every materialised
+                                     intermediate written once, read once per use */
+    int64_t workspace_bytes;      /* device bytes tn_plan_bind needs */
+    int64_t peak_tensor_bytes;    /* largest intermediate set (all instances) */
+} tn_plan_info;
+
+typedef struct tn_plan_s *tn_plan_t;
+
+/* Zero-initialised defaults. */
+void tn_options_default(tn_options *opt);
+
+/* Structure of the fused network (SM Sec. II).  Host only.
+ * edge_ends (2*n_edges int32, earlier tensor first) and out_tensor (n_qubits
+ * int32, the tensor carrying each output leg) may be NULL. */
+int tn_network(const tn_circuit *circ, int32_t *n_tensors, int32_t *n_edges,
+               int32_t *edge_ends, int32_t *out_tensor);
+
+/* Build a plan: fused network, slicing, the static reuse-instance DAG
+ * (SM Sec. III), step schedule and workspace layout.  Host only; touches no
+ * GPU.  bits: k x n_qubits uint8.  tree_ssa: (T-1) x 2 int32.
+ * sliced_edges: n_sliced distinct bond edges (may be NULL if n_sliced = 0). */
+int tn_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k,
+            const int32_t *tree_ssa, const int32_t *sliced_edges, int32_t n_sliced,
+            const tn_options *opt, tn_plan_t *out);
+
+int tn_plan_query(tn_plan_t plan, tn_plan_info *info);
+
+/* Per-node reuse widths w_v (distinct projections of the bitstrings onto
+ * the node's output qubits) and per-instance ranks, 2T-1 entries each; the
+ * data behind Eq. (1).  Either pointer may be NULL. */
+int tn_plan_widths(tn_plan_t plan, int64_t *width_out, int32_t *rank, int32_t *n_slice_vars);
+
+/* One row per step, in execution order (the features a kernel choice
+ * depends on): */
+typedef struct {
+    int32_t node, a, b;       /* tree node produced and its operands (a: larger) */
+    int32_t mb, kb, nb;       /* free bits of a, contracted bits, free bits of b */
+    int32_t rank_a, rank_b;   /* per-instance ranks of the operands */
+    int32_t level;            /* slice-loop level (64: once per call) */
+    int32_t kernel;           /* 0 per-row SIMT, 1 tiled GEMM */
+    int64_t n_inst, n_inst_a, n_inst_b;  /* instances of the output and operands */
+    double flops, bytes;      /* per pass: 8 * n_inst * 2^(mb+kb+nb); A + B reads + C write */
+    double runs;              /* passes over all slice batches */
+} tn_step_info;
+
+int tn_plan_steps(tn_plan_t plan, tn_step_info *steps, int32_t n);
+
+/* Bind caller-owned device memory (>= info.workspace_bytes, 256-byte
+ * aligned) and upload the plan's tables and gate tensors into it on
+ * `stream`.  Must precede tn_contract*. */
+int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream);
+
+/* Accumulate into amps (device, complex128, k entries) the partial
+ * amplitudes of every slice in slice batches [batch_lo, batch_hi).  The plan
+ * partitions the 2^n_sliced slices into tn_plan_info.n_batches batches of
+ * 2^slice_batch_log2 slices each (its own order of the sliced edges:
+ * batch b holds the slices whose looped sliced edges take the bits of b);
+ * [0, n_batches) covers every slice once, and disjoint ranges can run on
+ * different devices and be summed.  Within a call, a batch re-runs only the
+ * steps whose sliced edges changed since the previous batch.  Partials are
+ * added in a fixed order (deterministic).  Asynchronous on `stream`. */
+int tn_contract(tn_plan_t plan, int precision, int64_t batch_lo, int64_t batch_hi,
+                double *amps, void *stream);
+
+/* Partial amplitudes of individual slices, for comparison with an oracle:
+ * partials (device, complex128) receives ns x k entries, slice-major, each
+ * already scaled back by its power-of-two exponent. */
+int tn_contract_slices(tn_plan_t plan, int precision, const int64_t *slice_ids, int32_t ns,
+                       double *partials, void *stream);
+
+/* Linear XEB fidelity F = (2^n / k) * sum_b |amp_b|^2 - 1 of k device
+ * complex128 amplitudes (the estimator whose mean matches the density of
+ * Eq. (fxeb): E[N p] = 1 + F), reduced in FP64 on the device in a fixed
+ * order.  Writes one double to the caller's device word *xeb_dev;
+ * asynchronous on `stream`. */
+int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, void *stream);
+
+/* Device time of each step of the last tn_contract* call, when profiling is
+ * on (tn_plan_profile(plan, 1)); ms has n_steps entries. */
+int tn_plan_profile(tn_plan_t plan, int enable);
+int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t n);
+
+void tn_destroy(tn_plan_t plan);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *tn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

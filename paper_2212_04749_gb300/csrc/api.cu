@@ -1,0 +1,376 @@
+// C ABI of the contraction library (declared in include/tn.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/tn.h"
+#include "kernels.cuh"
+#include "plan.hpp"
+
+namespace {
+
+thread_local std::string g_err;
+
+int set_err(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return set_err(TN_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+struct PlanObj {
+    tnp::Plan P;
+    uint8_t *ws = nullptr;
+    size_t ws_bytes = 0;
+    std::vector<tnk::StepDesc> desc;  // per step
+    int32_t *err_flag = nullptr;      // device word for bounded waits
+    bool profile = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<double> step_ms;
+    int64_t last_batches = 0;
+};
+
+template <class T>
+T *at(PlanObj *o, int64_t off) {
+    return reinterpret_cast<T *>(o->ws + off);
+}
+
+void build_descs(PlanObj *o) {
+    tnp::Plan &P = o->P;
+    o->desc.clear();
+    for (const tnp::Step &st : P.steps) {
+        const tnp::Node &nd = P.nodes[st.node];
+        const tnp::Node &A = P.nodes[st.a], &B = P.nodes[st.b];
+        tnk::StepDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.A = at<const float2>(o, A.buf.data);
+        d.B = at<const float2>(o, B.buf.data);
+        d.C = at<float2>(o, nd.buf.data);
+        d.sA = int64_t(1) << A.rank;
+        d.sB = int64_t(1) << B.rank;
+        d.sC = int64_t(1) << nd.rank;
+        const bool a_left = (st.a == nd.left);
+        const int32_t *sig = at<const int32_t>(o, nd.buf.sig);
+        const int32_t *out = at<const int32_t>(o, nd.buf.out);
+        d.sigA = a_left ? sig : sig + nd.n_sig;
+        d.sigB = a_left ? sig + nd.n_sig : sig;
+        d.outA = a_left ? out : out + nd.n_out;
+        d.outB = a_left ? out + nd.n_out : out;
+        d.nOutA = A.n_out;
+        d.nOutB = B.n_out;
+        d.nOut = nd.n_out;
+        d.nInst = nd.n_inst;
+        d.EA = at<const int32_t>(o, A.buf.E);
+        d.EB = at<const int32_t>(o, B.buf.E);
+        d.EC = at<int32_t>(o, nd.buf.E);
+        const bool rs = P.opt.rescale != 0;
+        d.mxA = rs ? at<const uint32_t>(o, A.buf.mx) : nullptr;
+        d.mxB = rs ? at<const uint32_t>(o, B.buf.mx) : nullptr;
+        d.mxC = rs ? at<uint32_t>(o, nd.buf.mx) : nullptr;
+        d.mb = st.mb;
+        d.kb = st.kb;
+        d.nb = st.nb;
+        for (int j = 0; j < st.mb; ++j) d.pAm[j] = st.pAm[j];
+        for (int j = 0; j < st.kb; ++j) {
+            d.pAk[j] = st.pAk[j];
+            d.pBk[j] = st.pBk[j];
+        }
+        for (int j = 0; j < st.nb; ++j) d.pBn[j] = st.pBn[j];
+        o->desc.push_back(d);
+    }
+}
+
+int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
+    const tnp::Step &S = o->P.steps[s];
+    const tnk::StepDesc &d = o->desc[s];
+    cudaError_t e;
+    if (S.kernel == 0) {
+        e = tnk::launch_step_row(d, st);
+    } else if (precision != TN_FP32 && tnk::gemm_tc_supports(d)) {
+        e = tnk::launch_step_gemm_tc(d, precision, o->err_flag, st);
+    } else {
+        e = tnk::launch_step_gemm_simt(d, st);
+    }
+    if (e != cudaSuccess)
+        return set_err(TN_ECUDA, "step " + std::to_string(s) + ": " + cudaGetErrorString(e));
+    return TN_OK;
+}
+
+// Batches [b_lo, b_hi) in order.  The first batch of the call runs every
+// step; batch b > b_lo re-runs only the steps whose sliced edges changed
+// from batch b-1 (level <= ctz(b)).  `per_batch(b)` runs after each batch.
+template <class F>
+int run_batches(PlanObj *o, int precision, int64_t b_lo, int64_t b_hi, cudaStream_t st, F per_batch) {
+    tnp::Plan &P = o->P;
+    const int nst = (int)P.steps.size();
+    if (o->profile) {
+        for (int i = (int)o->ev.size(); i < 2 * nst; ++i) {
+            cudaEvent_t e;
+            CU(cudaEventCreate(&e));
+            o->ev.push_back(e);
+        }
+        o->step_ms.assign(nst, 0.0);
+    }
+    const auto *jobs = at<const tnk::FillJobD>(o, P.off_fill_jobs);
+    const auto *highs = at<const tnk::LeafHighD>(o, P.off_leaf_high);
+    std::vector<int> ran;
+    for (int64_t b = b_lo; b < b_hi; ++b) {
+        const int lv = (b == b_lo) ? 64 : __builtin_ctzll((unsigned long long)b);
+        const int64_t clear = (b == b_lo) ? P.emax_bytes : P.emax_prefix[lv];
+        if (clear) CU(cudaMemsetAsync(o->ws + P.off_emax, 0, clear, st));
+        cudaError_t e = tnk::launch_fill(jobs, P.n_fill_jobs, highs, b, at<float2>(o, 0), st);
+        if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("leaf fill: ") + cudaGetErrorString(e));
+        ran.clear();
+        for (int s = 0; s < nst; ++s) {
+            if (b != b_lo && P.steps[s].level > lv) continue;
+            if (o->profile) CU(cudaEventRecord(o->ev[2 * s], st));
+            if (int rc = run_step(o, s, precision, st)) return rc;
+            if (o->profile) CU(cudaEventRecord(o->ev[2 * s + 1], st));
+            ran.push_back(s);
+        }
+        if (o->profile) {
+            CU(cudaStreamSynchronize(st));
+            for (int s : ran) {
+                float ms = 0.f;
+                CU(cudaEventElapsedTime(&ms, o->ev[2 * s], o->ev[2 * s + 1]));
+                o->step_ms[s] += ms;
+            }
+        }
+        if (int rc = per_batch(b)) return rc;
+    }
+    o->last_batches = b_hi - b_lo;
+    return TN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tn_last_error(void) { return g_err.c_str(); }
+
+int tn_network(const tn_circuit *circ, int32_t *n_tensors, int32_t *n_edges, int32_t *edge_ends,
+               int32_t *out_tensor) {
+    tnp::Network net;
+    std::string err;
+    if (!tnp::build_network(circ, net, err)) return set_err(TN_EINVAL, err);
+    if (n_tensors) *n_tensors = net.n_tensors;
+    if (n_edges) *n_edges = net.n_edges;
+    if (edge_ends)
+        for (int e = 0; e < net.n_edges; ++e) {
+            edge_ends[2 * e] = net.edge_ends[e][0];
+            edge_ends[2 * e + 1] = net.edge_ends[e][1];
+        }
+    if (out_tensor)
+        for (int q = 0; q < net.n_qubits; ++q) out_tensor[q] = net.out_tensor[q];
+    g_err.clear();
+    return TN_OK;
+}
+
+int tn_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int32_t *tree_ssa,
+            const int32_t *sliced_edges, int32_t n_sliced, const tn_options *opt, tn_plan_t *out) {
+    if (!out) return set_err(TN_EINVAL, "tn_plan: null output handle");
+    *out = nullptr;
+    std::unique_ptr<PlanObj> o(new PlanObj());
+    std::string err;
+    int code = TN_OK;
+    try {
+        if (!tnp::make_plan(circ, bits, k, tree_ssa, sliced_edges, n_sliced, opt, o->P, err, code))
+            return set_err(code, err);
+    } catch (const std::bad_alloc &) {
+        return set_err(TN_ENOMEM, "tn_plan: host allocation failed");
+    }
+    *out = reinterpret_cast<tn_plan_t>(o.release());
+    g_err.clear();
+    return TN_OK;
+}
+
+int tn_plan_query(tn_plan_t plan, tn_plan_info *info) {
+    if (!plan || !info) return set_err(TN_EINVAL, "tn_plan_query: null argument");
+    const tnp::Plan &P = reinterpret_cast<PlanObj *>(plan)->P;
+    std::memset(info, 0, sizeof(*info));
+    info->n_tensors = P.net.n_tensors;
+    info->n_edges = P.net.n_edges;
+    info->n_nodes = (int32_t)P.nodes.size();
+    info->n_steps = (int32_t)P.steps.size();
+    info->n_unique = (int32_t)P.k_unique;
+    info->n_sliced = (int32_t)P.sliced.size();
+    info->slice_batch_log2 = P.m_low;
+    info->n_batches = (int32_t)P.n_batches;
+    info->max_rank = P.max_rank;
+    info->n_static_steps = P.n_static_steps;
+    info->flops_ma = P.flops_ma;
+    info->flops_sa = P.flops_sa;
+    info->flops_exec = P.flops_exec;
+    info->bytes_min = P.bytes_min;
+    info->workspace_bytes = P.ws_bytes;
+    info->peak_tensor_bytes = P.peak_tensor_bytes;
+    return TN_OK;
+}
+
+int tn_plan_widths(tn_plan_t plan, int64_t *width_out, int32_t *rank, int32_t *n_slice_vars) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_widths: null plan");
+    const tnp::Plan &P = reinterpret_cast<PlanObj *>(plan)->P;
+    for (size_t v = 0; v < P.nodes.size(); ++v) {
+        if (width_out) width_out[v] = P.nodes[v].n_out;
+        if (rank) rank[v] = P.nodes[v].rank;
+        if (n_slice_vars) n_slice_vars[v] = (int32_t)P.nodes[v].slices.size();
+    }
+    return TN_OK;
+}
+
+int tn_plan_steps(tn_plan_t plan, tn_step_info *out, int32_t n) {
+    if (!plan || (n > 0 && !out)) return set_err(TN_EINVAL, "tn_plan_steps: null argument");
+    const tnp::Plan &P = reinterpret_cast<PlanObj *>(plan)->P;
+    for (int32_t s = 0; s < n && s < (int32_t)P.steps.size(); ++s) {
+        const tnp::Step &st = P.steps[s];
+        tn_step_info &r = out[s];
+        r.node = st.node;
+        r.a = st.a;
+        r.b = st.b;
+        r.mb = st.mb;
+        r.kb = st.kb;
+        r.nb = st.nb;
+        r.rank_a = P.nodes[st.a].rank;
+        r.rank_b = P.nodes[st.b].rank;
+        r.level = st.level;
+        r.kernel = st.kernel;
+        r.n_inst = P.nodes[st.node].n_inst;
+        r.n_inst_a = P.nodes[st.a].n_inst;
+        r.n_inst_b = P.nodes[st.b].n_inst;
+        r.flops = st.flops;
+        r.bytes = st.bytes;
+        r.runs = st.runs;
+    }
+    return TN_OK;
+}
+
+int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_bind: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return set_err(TN_EINVAL, "tn_plan_bind: workspace must be a 256-byte aligned device pointer");
+    if ((int64_t)bytes < o->P.ws_bytes)
+        return set_err(TN_ENOMEM, "tn_plan_bind: workspace has " + std::to_string(bytes) + " bytes, plan needs " +
+                                      std::to_string(o->P.ws_bytes));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    o->ws = static_cast<uint8_t *>(workspace);
+    o->ws_bytes = bytes;
+    for (auto &u : o->P.uploads) {
+        if (u.second.empty()) continue;
+        CU(cudaMemcpyAsync(o->ws + u.first, u.second.data(), u.second.size(), cudaMemcpyHostToDevice, st));
+    }
+    o->err_flag = at<int32_t>(o, o->P.off_scratch);
+    CU(cudaMemsetAsync(o->err_flag, 0, 4, st));
+    CU(cudaStreamSynchronize(st));
+    build_descs(o);
+    g_err.clear();
+    return TN_OK;
+}
+
+int tn_contract(tn_plan_t plan, int precision, int64_t batch_lo, int64_t batch_hi, double *amps, void *stream) {
+    if (!plan) return set_err(TN_EINVAL, "tn_contract: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    if (!o->ws) return set_err(TN_ESTATE, "tn_contract: no workspace bound (call tn_plan_bind)");
+    if (precision < TN_FP32 || precision > TN_BF16X3) return set_err(TN_EINVAL, "tn_contract: bad precision");
+    tnp::Plan &P = o->P;
+    if (batch_lo < 0 || batch_hi > P.n_batches || batch_lo > batch_hi)
+        return set_err(TN_EINVAL, "tn_contract: batch range outside [0, n_batches)");
+    if (P.k == 0 || batch_lo == batch_hi) return TN_OK;
+    if (!amps) return set_err(TN_EINVAL, "tn_contract: null amplitude buffer");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const tnp::Node &R = P.nodes[P.root];
+    const float2 *root = at<const float2>(o, R.buf.data);
+    const int32_t *E = at<const int32_t>(o, R.buf.E);
+    const int32_t *uniq = at<const int32_t>(o, P.off_uniq);
+    int rc = run_batches(o, precision, batch_lo, batch_hi, st, [&](int64_t) -> int {
+        cudaError_t e = tnk::launch_accumulate(root, E, uniq, P.k, R.n_sig, R.n_out, amps, st);
+        if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("accumulate: ") + cudaGetErrorString(e));
+        return TN_OK;
+    });
+    if (rc) return rc;
+    g_err.clear();
+    return TN_OK;
+}
+
+int tn_contract_slices(tn_plan_t plan, int precision, const int64_t *slice_ids, int32_t ns, double *partials,
+                       void *stream) {
+    if (!plan) return set_err(TN_EINVAL, "tn_contract_slices: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    if (!o->ws) return set_err(TN_ESTATE, "tn_contract_slices: no workspace bound");
+    if (precision < TN_FP32 || precision > TN_BF16X3) return set_err(TN_EINVAL, "bad precision");
+    if (ns < 0 || (ns > 0 && (!slice_ids || !partials))) return set_err(TN_EINVAL, "tn_contract_slices: bad args");
+    tnp::Plan &P = o->P;
+    const int64_t n_slices = int64_t(1) << P.sliced.size();
+    const int64_t per = int64_t(1) << P.m_low;
+    std::map<int64_t, std::vector<int32_t>> by_batch;
+    std::vector<int64_t> internal(ns);
+    for (int32_t i = 0; i < ns; ++i) {
+        if (slice_ids[i] < 0 || slice_ids[i] >= n_slices) return set_err(TN_EINVAL, "slice id out of range");
+        int64_t v = 0;  // external bit j = P.perm[t]  ->  internal bit t
+        for (size_t t = 0; t < P.perm.size(); ++t) v |= ((slice_ids[i] >> P.perm[t]) & 1) << t;
+        internal[i] = v;
+        by_batch[v / per].push_back(i);
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const tnp::Node &R = P.nodes[P.root];
+    const float2 *root = at<const float2>(o, R.buf.data);
+    const int32_t *E = at<const int32_t>(o, R.buf.E);
+    const int32_t *uniq = at<const int32_t>(o, P.off_uniq);
+    for (auto &kv : by_batch) {
+        const int64_t b = kv.first;
+        int rc = run_batches(o, precision, b, b + 1, st, [&](int64_t) -> int {
+            for (int32_t i : kv.second) {
+                const int64_t sigma = internal[i] % per;
+                cudaError_t e = tnk::launch_extract(root, E, uniq, P.k, sigma, R.n_out, partials + 2 * P.k * i, st);
+                if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("extract: ") + cudaGetErrorString(e));
+            }
+            return TN_OK;
+        });
+        if (rc) return rc;
+    }
+    g_err.clear();
+    return TN_OK;
+}
+
+int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, void *stream) {
+    if (!amps || !xeb_dev || k <= 0 || n_qubits < 1 || n_qubits > 1000)
+        return set_err(TN_EINVAL, "tn_xeb: need k > 0, amplitudes and an output word");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = tnk::launch_xeb(amps, k, std::ldexp(1.0, n_qubits) / double(k), xeb_dev, st);
+    if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("xeb: ") + cudaGetErrorString(e));
+    g_err.clear();
+    return TN_OK;
+}
+
+int tn_plan_profile(tn_plan_t plan, int enable) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_profile: null plan");
+    reinterpret_cast<PlanObj *>(plan)->profile = enable != 0;
+    return TN_OK;
+}
+
+int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t n) {
+    if (!plan || !ms) return set_err(TN_EINVAL, "tn_plan_step_times: null argument");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    for (int32_t i = 0; i < n && i < (int32_t)o->step_ms.size(); ++i) ms[i] = o->step_ms[i];
+    return TN_OK;
+}
+
+void tn_destroy(tn_plan_t plan) {
+    if (!plan) return;
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    for (cudaEvent_t e : o->ev) cudaEventDestroy(e);
+    delete o;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Device-side descriptors and launchers shared by the C ABI (api.cu) and
+// the kernels (kernels.cu, gemm_tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace tnk {
+
+// One pairwise contraction step, passed by value to every step kernel.
+//   C[i](m, n) = sum_k  A[a(i)](m, k) * B[b(i)](k, n)       (complex)
+// Instance i = sigma * nOut + beta;  a(i) = sigA[sigma] * nOutA + outA[beta],
+// b(i) likewise.  Entry (m, k) of an A instance sits at element offset
+// dep(m, pAm) + dep(k, pAk), where dep scatters the bits of its first
+// argument to the listed bit positions.  C is row-major: C[i][m * N + n].
+struct StepDesc {
+    const float2 *A;
+    const float2 *B;
+    float2 *C;
+    int64_t sA, sB, sC;           // elements per instance
+    const int32_t *sigA, *sigB;   // [n_sig]
+    const int32_t *outA, *outB;   // [nOut]
+    int32_t nOutA, nOutB, nOut;
+    int32_t pad0;
+    int64_t nInst;
+    const int32_t *EA, *EB;       // accumulated exponents of the operands
+    int32_t *EC;
+    const uint32_t *mxA, *mxB;    // max-|component| bits of the operands (null: no rescale)
+    uint32_t *mxC;                // max-|component| bits of C (null: not tracked)
+    int32_t mb, kb, nb;
+    int32_t pad1;
+    int8_t pAm[40];
+    int8_t pAk[24];
+    int8_t pBk[24];
+    int8_t pBn[24];
+};
+
+struct FillJobD {
+    int64_t dst, src;
+    int32_t leaf_high, n;
+};
+
+struct LeafHighD {
+    int32_t cnt;
+    int32_t j[4];
+    int32_t stride[4];
+};
+
+// Launchers return cudaGetLastError() of the launch.
+cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *highs, int64_t batch,
+                        float2 *ws, cudaStream_t s);
+cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s);
+cudaError_t launch_step_gemm_simt(const StepDesc &d, cudaStream_t s);
+cudaError_t launch_accumulate(const float2 *root, const int32_t *E, const int32_t *uniq, int64_t k,
+                              int64_t n_sig, int32_t n_out, double *amps, cudaStream_t s);
+cudaError_t launch_extract(const float2 *root, const int32_t *E, const int32_t *uniq, int64_t k,
+                           int64_t sigma, int32_t n_out, double *out, cudaStream_t s);
+cudaError_t launch_xeb(const double *amps, int64_t k, double scale, double *out, cudaStream_t s);
+
+// Tensor-core path (gemm_tc.cu).  precision: 1 = TF32, 2 = BF16x3.
+// Returns cudaErrorNotSupported for shapes it does not take.
+bool gemm_tc_supports(const StepDesc &d);
+cudaError_t launch_step_gemm_tc(const StepDesc &d, int precision, int32_t *err_flag, cudaStream_t s);
+
+}  // namespace tnk

@@ -1,0 +1,735 @@
+// Host planner: fused network, reuse-instance DAG, step schedule, workspace.
+// See plan.hpp for the overview.  No CUDA here: tn_plan runs on any host.
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <set>
+#include <string>
+#include <unordered_map>
+
+extern "C" void tn_options_default(tn_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->workspace_limit = int64_t(64) << 30;
+    opt->slice_batch_log2 = -1;
+    opt->rescale = 1;
+    opt->fuse = 0;
+    opt->fuse_max_bits = 7;
+}
+
+namespace tnp {
+
+namespace {
+
+using M2 = std::array<cd, 4>;  // row-major 2x2
+
+M2 eye2() { return {cd(1), cd(0), cd(0), cd(1)}; }
+
+M2 mul2(const M2 &a, const M2 &b) {
+    M2 c;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) c[2 * i + j] = a[2 * i] * b[j] + a[2 * i + 1] * b[2 + j];
+    return c;
+}
+
+M2 gate2(const tn_gate &g) {
+    M2 m;
+    for (int i = 0; i < 4; ++i) m[i] = cd(g.m[2 * i], g.m[2 * i + 1]);
+    return m;
+}
+
+// First-fit allocator over byte offsets, 256-byte granules.
+struct Arena {
+    int64_t base = 0, top = 0, high = 0;
+    std::map<int64_t, int64_t> free_;  // offset -> size
+    static int64_t align(int64_t x) { return (x + 255) & ~int64_t(255); }
+    int64_t alloc(int64_t bytes) {
+        bytes = align(std::max<int64_t>(bytes, 1));
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                int64_t off = it->first, sz = it->second;
+                free_.erase(it);
+                if (sz > bytes) free_[off + bytes] = sz - bytes;
+                return off;
+            }
+        }
+        int64_t off = top;
+        top += bytes;
+        high = std::max(high, top);
+        return off;
+    }
+    void release(int64_t off, int64_t bytes) {
+        bytes = align(std::max<int64_t>(bytes, 1));
+        auto it = free_.emplace(off, bytes).first;
+        // coalesce with next
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+                it = pv;
+            }
+        }
+        if (it->first + it->second == top) {
+            top = it->first;
+            free_.erase(it);
+        }
+    }
+};
+
+template <class T>
+void push_upload(Plan &p, int64_t off, const std::vector<T> &v) {
+    std::vector<uint8_t> bytes(v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(bytes.data(), v.data(), bytes.size());
+    p.uploads.emplace_back(off, std::move(bytes));
+}
+
+}  // namespace
+
+bool build_network(const tn_circuit *circ, Network &net, std::string &err) {
+    if (!circ || circ->n_qubits < 1 || circ->n_qubits > 64 || circ->n_gates < 0 ||
+        (circ->n_gates > 0 && !circ->gates)) {
+        err = "invalid circuit header (need 1 <= n_qubits <= 64)";
+        return false;
+    }
+    const int n = circ->n_qubits;
+    net = Network();
+    net.n_qubits = n;
+    std::vector<M2> pend(n, eye2());
+    std::vector<int> last(n, -1);
+    std::vector<std::array<cd, 16>> G;  // raw 4x4 gate per tensor
+    std::vector<std::array<M2, 2>> U;   // absorbed input-side products
+    for (int gi = 0; gi < circ->n_gates; ++gi) {
+        const tn_gate &g = circ->gates[gi];
+        if (g.q1 < 0) {
+            if (g.q0 < 0 || g.q0 >= n) {
+                err = "gate " + std::to_string(gi) + ": qubit out of range";
+                return false;
+            }
+            pend[g.q0] = mul2(gate2(g), pend[g.q0]);
+            continue;
+        }
+        if (g.q0 < 0 || g.q1 >= n || g.q0 >= g.q1) {
+            err = "gate " + std::to_string(gi) + ": two-qubit gate needs 0 <= q0 < q1 < n";
+            return false;
+        }
+        const int t = (int)net.leaves.size();
+        LeafTensor L{};
+        L.gate = gi;
+        L.qa = g.q0;
+        L.qb = g.q1;
+        std::array<cd, 16> gm;
+        for (int i = 0; i < 16; ++i) gm[i] = cd(g.m[2 * i], g.m[2 * i + 1]);
+        std::array<M2, 2> u;
+        const int qs[2] = {g.q0, g.q1};
+        for (int s = 0; s < 2; ++s) {
+            const int q = qs[s];
+            if (last[q] >= 0) {
+                const int e = net.n_edges++;
+                net.edge_ends.push_back({last[q], t});
+                LeafTensor &P = net.leaves[last[q]];
+                const int slot = (P.qa == q) ? 0 : 1;
+                P.legs[slot] = Leg{LEG_BOND, e};
+                L.legs[2 + s] = Leg{LEG_BOND, e};
+            } else {
+                L.legs[2 + s] = Leg{LEG_FIXED, -1};
+            }
+            L.legs[s] = Leg{LEG_OUT, q};
+            u[s] = pend[q];
+            pend[q] = eye2();
+            last[q] = t;
+        }
+        net.leaves.push_back(L);
+        G.push_back(gm);
+        U.push_back(u);
+    }
+    for (int q = 0; q < n; ++q) {
+        if (last[q] < 0) {
+            err = "qubit " + std::to_string(q) + " takes part in no two-qubit gate";
+            return false;
+        }
+    }
+    net.n_tensors = (int)net.leaves.size();
+    net.out_tensor = last;
+    // entries: T[oa,ob,ia,ib] = sum V_a[oa,x] V_b[ob,y] G[2x+y, 2z+w] U_a[z,ia] U_b[w,ib]
+    for (int t = 0; t < net.n_tensors; ++t) {
+        LeafTensor &L = net.leaves[t];
+        M2 V[2];
+        for (int s = 0; s < 2; ++s) {
+            const int q = s == 0 ? L.qa : L.qb;
+            V[s] = (L.legs[s].kind == LEG_OUT) ? pend[q] : eye2();
+        }
+        for (int oa = 0; oa < 2; ++oa)
+            for (int ob = 0; ob < 2; ++ob)
+                for (int ia = 0; ia < 2; ++ia)
+                    for (int ib = 0; ib < 2; ++ib) {
+                        cd acc = 0;
+                        if ((L.legs[2].kind != LEG_FIXED || ia == 0) &&
+                            (L.legs[3].kind != LEG_FIXED || ib == 0)) {
+                            for (int x = 0; x < 2; ++x)
+                                for (int y = 0; y < 2; ++y)
+                                    for (int z = 0; z < 2; ++z)
+                                        for (int w = 0; w < 2; ++w)
+                                            acc += V[0][2 * oa + x] * V[1][2 * ob + y] *
+                                                   G[t][4 * (2 * x + y) + (2 * z + w)] *
+                                                   U[t][0][2 * z + ia] * U[t][1][2 * w + ib];
+                        }
+                        L.t[((oa * 2 + ob) * 2 + ia) * 2 + ib] = acc;
+                    }
+    }
+    return true;
+}
+
+namespace {
+
+struct Builder {
+    Plan &P;
+    std::string &err;
+    int &code;
+    int T = 0, NN = 0, m = 0;
+    std::vector<std::vector<int32_t>> oi;  // node -> per distinct bitstring out-instance
+    std::vector<int> slice_of;             // bond edge -> internal slice index (-1: not sliced)
+
+    bool fail(int c, const std::string &msg) {
+        code = c;
+        err = msg;
+        return false;
+    }
+
+    // Reuse-instance DAG over the distinct bitstrings (SM Sec. III): the
+    // out-instances of a node are the distinct projections of the
+    // bitstrings onto its output qubits.  Ordered by (left, right) child
+    // instance so that instances sharing a child instance are adjacent.
+    void out_instances() {
+        const int64_t ku = P.k_unique;
+        oi.assign(NN, {});
+        for (int v = 0; v < T; ++v) {
+            Node &nd = P.nodes[v];
+            std::vector<int32_t> key(ku);
+            for (int64_t u = 0; u < ku; ++u) {
+                int val = 0;
+                for (size_t t = 0; t < nd.outs.size(); ++t) val |= int(P.ubits[u][nd.outs[t]]) << t;
+                key[u] = val;
+            }
+            std::vector<int32_t> vals(key);
+            std::sort(vals.begin(), vals.end());
+            vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+            if (vals.empty()) vals.push_back(0);
+            nd.leaf_outval = vals;
+            nd.n_out = (int)vals.size();
+            oi[v].resize(ku);
+            for (int64_t u = 0; u < ku; ++u)
+                oi[v][u] = int32_t(std::lower_bound(vals.begin(), vals.end(), key[u]) - vals.begin());
+        }
+        for (int v = T; v < NN; ++v) {
+            Node &nd = P.nodes[v];
+            const int a = nd.left, b = nd.right;
+            const int64_t nb = P.nodes[b].n_out;
+            std::vector<int64_t> key(ku);
+            for (int64_t u = 0; u < ku; ++u) key[u] = int64_t(oi[a][u]) * nb + oi[b][u];
+            std::vector<int64_t> vals(key);
+            std::sort(vals.begin(), vals.end());
+            vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+            if (vals.empty()) vals.push_back(0);
+            nd.n_out = (int)vals.size();
+            nd.outL.resize(vals.size());
+            nd.outR.resize(vals.size());
+            for (size_t i = 0; i < vals.size(); ++i) {
+                nd.outL[i] = int32_t(vals[i] / nb);
+                nd.outR[i] = int32_t(vals[i] % nb);
+            }
+            oi[v].resize(ku);
+            for (int64_t u = 0; u < ku; ++u)
+                oi[v][u] = int32_t(std::lower_bound(vals.begin(), vals.end(), key[u]) - vals.begin());
+        }
+    }
+
+    static std::vector<int32_t> compress_map(const std::vector<int> &parent_low,
+                                             const std::vector<int> &child_low) {
+        // sigma over parent_low bits -> sigma over child_low bits (a subset)
+        std::vector<int> pos;
+        for (int j : child_low) pos.push_back(int(std::find(parent_low.begin(), parent_low.end(), j) -
+                                                  parent_low.begin()));
+        const int64_t n = int64_t(1) << parent_low.size();
+        std::vector<int32_t> out(n);
+        for (int64_t s = 0; s < n; ++s) {
+            int32_t c = 0;
+            for (size_t t = 0; t < pos.size(); ++t) c |= int32_t((s >> pos[t]) & 1) << t;
+            out[s] = c;
+        }
+        return out;
+    }
+
+    bool schedule(int m_low) {
+        P.m_low = m_low;
+        const int h = m - m_low;
+        P.n_batches = int64_t(1) << h;
+        for (int v = 0; v < NN; ++v) {
+            Node &nd = P.nodes[v];
+            nd.slices_low.clear();
+            nd.hmask = 0;
+            for (int t : nd.slices) {
+                if (t < m_low) nd.slices_low.push_back(t);
+                else nd.hmask |= uint64_t(1) << (t - m_low);
+            }
+            nd.level = nd.hmask ? __builtin_ctzll(nd.hmask) : 64;
+            nd.n_sig = int64_t(1) << nd.slices_low.size();
+            nd.n_inst = nd.n_sig * nd.n_out;
+            nd.buf = NodeBuf();
+            nd.step = -1;
+            nd.last_use = -1;
+        }
+        for (int v = T; v < NN; ++v) {
+            Node &nd = P.nodes[v];
+            nd.sigL = compress_map(nd.slices_low, P.nodes[nd.left].slices_low);
+            nd.sigR = compress_map(nd.slices_low, P.nodes[nd.right].slices_low);
+        }
+        // A node is kept across slice batches when its parent is recomputed
+        // more often than it is (the parent depends on a sliced edge it does
+        // not): the slice analogue of storing the tensor before a branching
+        // node of the reuse tree (SM Sec. III.C).
+        for (int v = 0; v < NN; ++v) {
+            Node &nd = P.nodes[v];
+            nd.persistent = (v < T) || (nd.parent >= 0 && nd.level > P.nodes[nd.parent].level);
+        }
+        // steps in SSA order
+        P.steps.clear();
+        P.n_static_steps = 0;
+        for (int v = T; v < NN; ++v) {
+            Node &nd = P.nodes[v];
+            Step st;
+            st.node = v;
+            const Node &l = P.nodes[nd.left], &r = P.nodes[nd.right];
+            const bool left_big = l.rank >= r.rank;
+            st.a = left_big ? nd.left : nd.right;
+            st.b = left_big ? nd.right : nd.left;
+            st.level = nd.level;
+            nd.step = (int)P.steps.size();
+            P.n_static_steps += nd.level == 64;
+            P.steps.push_back(st);
+        }
+        // layouts and bit positions
+        P.max_rank = 0;
+        for (int v = 0; v < T; ++v) P.max_rank = std::max(P.max_rank, P.nodes[v].rank);
+        for (Step &st : P.steps) {
+            Node &nd = P.nodes[st.node];
+            const Node &A = P.nodes[st.a], &B = P.nodes[st.b];
+            std::vector<int> fa, fb, kk;
+            for (int e : A.layout) {
+                if (std::find(B.layout.begin(), B.layout.end(), e) != B.layout.end()) kk.push_back(e);
+                else fa.push_back(e);
+            }
+            for (int e : B.layout)
+                if (std::find(A.layout.begin(), A.layout.end(), e) == A.layout.end()) fb.push_back(e);
+            auto pos = [](const std::vector<int> &lay, int e) {
+                return int8_t(std::find(lay.begin(), lay.end(), e) - lay.begin());
+            };
+            st.mb = (int)fa.size();
+            st.kb = (int)kk.size();
+            st.nb = (int)fb.size();
+            st.pAm.clear(); st.pAk.clear(); st.pBk.clear(); st.pBn.clear();
+            for (int e : fa) st.pAm.push_back(pos(A.layout, e));
+            for (int e : kk) { st.pAk.push_back(pos(A.layout, e)); st.pBk.push_back(pos(B.layout, e)); }
+            for (int e : fb) st.pBn.push_back(pos(B.layout, e));
+            nd.layout = fb;
+            nd.layout.insert(nd.layout.end(), fa.begin(), fa.end());
+            nd.rank = (int)nd.layout.size();
+            P.max_rank = std::max(P.max_rank, nd.rank);
+            if (nd.rank > 40 || st.mb > 40 || st.kb > 24 || st.nb > 24)
+                return fail(TN_EUNSUPPORTED, "intermediate rank above 40 (or contracted/free bits above 24)");
+            const double macs = std::ldexp(1.0, st.mb + st.kb + st.nb);
+            st.flops = 8.0 * double(nd.n_inst) * macs;
+            st.bytes = 8.0 * (double(A.n_inst) * std::ldexp(1.0, A.rank) +
+                              double(B.n_inst) * std::ldexp(1.0, B.rank) +
+                              double(nd.n_inst) * std::ldexp(1.0, nd.rank));
+            st.runs = st.level >= h ? 1.0 : std::ldexp(1.0, h - st.level);
+            st.kernel = (st.kb + st.nb <= 6 && st.nb <= 4) ? 0 : 1;
+        }
+        for (int s = 0; s < (int)P.steps.size(); ++s) {
+            P.nodes[P.steps[s].a].last_use = s;
+            P.nodes[P.steps[s].b].last_use = s;
+        }
+        return true;
+    }
+
+    // Workspace layout; returns total bytes.
+    int64_t layout_workspace(bool emit) {
+        Plan &p = P;
+        if (emit) p.uploads.clear();
+        int64_t off = 0;
+        auto take = [&](int64_t bytes) {
+            int64_t o = off;
+            off += Arena::align(std::max<int64_t>(bytes, 1));
+            return o;
+        };
+        // full leaf tensors, extended layout: open bonds, outputs, sliced legs
+        std::vector<int64_t> full_off(T);
+        int64_t full_elems = 0;
+        for (int v = 0; v < T; ++v) {
+            const LeafTensor &L = p.net.leaves[v];
+            int legs_used = 0;
+            for (int g = 0; g < 4; ++g) legs_used += L.legs[g].kind != LEG_FIXED;
+            full_off[v] = full_elems;
+            full_elems += int64_t(1) << legs_used;
+        }
+        p.off_leaf_full = take(full_elems * 8);
+        // internal slice index of each leaf's sliced legs, increasing
+        std::vector<std::vector<int>> leaf_sl(T);
+        for (int v = 0; v < T; ++v) {
+            const LeafTensor &L = p.net.leaves[v];
+            for (int g = 0; g < 4; ++g)
+                if (L.legs[g].kind == LEG_BOND && slice_of[L.legs[g].id] >= 0)
+                    leaf_sl[v].push_back(slice_of[L.legs[g].id]);
+            std::sort(leaf_sl[v].begin(), leaf_sl[v].end());
+        }
+        if (emit) {
+            std::vector<float> full(full_elems * 2, 0.f);
+            for (int v = 0; v < T; ++v) {
+                const LeafTensor &L = p.net.leaves[v];
+                const Node &nd = p.nodes[v];
+                int bitpos[4] = {-1, -1, -1, -1};
+                for (int g = 0; g < 4; ++g) {
+                    if (L.legs[g].kind == LEG_BOND && slice_of[L.legs[g].id] < 0) {
+                        auto it = std::find(nd.layout.begin(), nd.layout.end(), L.legs[g].id);
+                        bitpos[g] = int(it - nd.layout.begin());
+                    }
+                }
+                int nxt = nd.rank;
+                for (int g = 0; g < 4; ++g)
+                    if (L.legs[g].kind == LEG_OUT) bitpos[g] = nxt++;
+                for (int t : leaf_sl[v])
+                    for (int g = 0; g < 4; ++g)
+                        if (L.legs[g].kind == LEG_BOND && slice_of[L.legs[g].id] == t) bitpos[g] = nxt++;
+                for (int idx = 0; idx < 16; ++idx) {
+                    const int bits[4] = {(idx >> 3) & 1, (idx >> 2) & 1, (idx >> 1) & 1, idx & 1};
+                    bool ok = true;
+                    int64_t e = 0;
+                    for (int g = 0; g < 4; ++g) {
+                        if (L.legs[g].kind == LEG_FIXED) { ok &= bits[g] == 0; continue; }
+                        e |= int64_t(bits[g]) << bitpos[g];
+                    }
+                    if (!ok) continue;
+                    full[2 * (full_off[v] + e)] = (float)L.t[idx].real();
+                    full[2 * (full_off[v] + e) + 1] = (float)L.t[idx].imag();
+                }
+            }
+            push_upload(p, p.off_leaf_full, full);
+        }
+        // max-|x| words ordered by recompute level, so that the words of the
+        // nodes recomputed in a batch form one prefix
+        std::vector<int> by_level(NN);
+        std::iota(by_level.begin(), by_level.end(), 0);
+        std::stable_sort(by_level.begin(), by_level.end(),
+                         [&](int x, int y) { return p.nodes[x].level < p.nodes[y].level; });
+        p.off_emax = off;
+        p.emax_prefix.assign(65, 0);
+        for (int v : by_level) p.nodes[v].buf.mx = take(p.nodes[v].n_inst * 4);
+        p.emax_bytes = off - p.off_emax;
+        for (int lv = 0; lv <= 64; ++lv) {
+            int64_t end = p.off_emax;
+            for (int v : by_level)
+                if (p.nodes[v].level <= lv) end = std::max(end, p.nodes[v].buf.mx + Arena::align(p.nodes[v].n_inst * 4));
+            p.emax_prefix[lv] = end - p.off_emax;
+        }
+        for (int v = 0; v < NN; ++v) {
+            Node &nd = p.nodes[v];
+            nd.buf.E = take(nd.n_inst * 4);
+            if (v >= T) {
+                nd.buf.sig = take(nd.n_sig * 8);
+                nd.buf.out = take(int64_t(nd.n_out) * 8);
+                if (emit) {
+                    std::vector<int32_t> s(nd.sigL), o(nd.outL);
+                    s.insert(s.end(), nd.sigR.begin(), nd.sigR.end());
+                    o.insert(o.end(), nd.outR.begin(), nd.outR.end());
+                    push_upload(p, nd.buf.sig, s);
+                    push_upload(p, nd.buf.out, o);
+                }
+            } else if (emit) {
+                std::vector<int32_t> zeros(nd.n_inst, 0);
+                push_upload(p, nd.buf.E, zeros);
+            }
+            if (nd.persistent) nd.buf.data = take(nd.n_inst * (int64_t(8) << nd.rank));
+        }
+        // fill jobs (one per leaf instance)
+        std::vector<LeafHigh> highs;
+        std::vector<FillJob> jobs;
+        for (int v = 0; v < T; ++v) {
+            const Node &nd = p.nodes[v];
+            LeafHigh hh{};
+            const std::vector<int> &sj = leaf_sl[v];
+            const int base_bit = nd.rank + (int)nd.outs.size();
+            for (size_t t = 0; t < sj.size(); ++t) {
+                if (sj[t] >= p.m_low) {
+                    hh.j[hh.cnt] = sj[t] - p.m_low;
+                    hh.stride[hh.cnt] = int32_t(1) << (base_bit + int(t));
+                    hh.cnt++;
+                }
+            }
+            const int32_t hidx = (int32_t)highs.size();
+            highs.push_back(hh);
+            for (int64_t sg = 0; sg < nd.n_sig; ++sg) {
+                int64_t slice_bits = 0;  // bit t <-> sj[t]; low ones from sigma
+                for (size_t t = 0; t < sj.size(); ++t) {
+                    auto it = std::find(nd.slices_low.begin(), nd.slices_low.end(), sj[t]);
+                    if (it != nd.slices_low.end())
+                        slice_bits |= ((sg >> int(it - nd.slices_low.begin())) & 1) << t;
+                }
+                for (int b = 0; b < nd.n_out; ++b) {
+                    FillJob j{};
+                    const int64_t inst = sg * nd.n_out + b;
+                    j.dst = (nd.buf.data / 8) + inst * (int64_t(1) << nd.rank);
+                    const int64_t block = (slice_bits << nd.outs.size()) | nd.leaf_outval[b];
+                    j.src = (p.off_leaf_full / 8) + full_off[v] + (block << nd.rank);
+                    j.leaf_high = hidx;
+                    j.n = int32_t(1) << nd.rank;
+                    jobs.push_back(j);
+                }
+            }
+        }
+        p.n_fill_jobs = (int64_t)jobs.size();
+        p.off_fill_jobs = take(int64_t(jobs.size()) * sizeof(FillJob));
+        p.off_leaf_high = take(int64_t(highs.size()) * sizeof(LeafHigh));
+        if (emit) {
+            push_upload(p, p.off_fill_jobs, jobs);
+            push_upload(p, p.off_leaf_high, highs);
+        }
+        p.off_uniq = take(p.k * 4);
+        if (emit) {
+            std::vector<int32_t> r(p.k);
+            for (int64_t i = 0; i < p.k; ++i) r[i] = oi[p.root][p.uniq_of[i]];
+            push_upload(p, p.off_uniq, r);
+        }
+        p.off_scratch = take(256);
+        // transient intermediates: first-fit over one full pass of the steps
+        Arena ar;
+        ar.base = ar.top = ar.high = off;
+        p.peak_tensor_bytes = 0;
+        const int nst = (int)p.steps.size();
+        for (int s = 0; s < nst; ++s) {
+            const Step &st = p.steps[s];
+            Node &nd = p.nodes[st.node];
+            const int64_t bytes = nd.n_inst * (int64_t(8) << nd.rank);
+            if (!nd.persistent) nd.buf.data = ar.alloc(bytes);
+            for (int c : {st.a, st.b}) {
+                Node &ch = p.nodes[c];
+                if (ch.persistent || ch.last_use != s) continue;
+                ar.release(ch.buf.data, ch.n_inst * (int64_t(8) << ch.rank));
+            }
+            p.peak_tensor_bytes = std::max(p.peak_tensor_bytes, bytes);
+        }
+        return Arena::align(ar.high);
+    }
+};
+
+}  // namespace
+
+bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int32_t *ssa,
+               const int32_t *sliced, int32_t n_sliced, const tn_options *opt, Plan &P,
+               std::string &err, int &code) {
+    code = TN_EINVAL;
+    if (!build_network(circ, P.net, err)) return false;
+    const int n = P.net.n_qubits;
+    const int T = P.net.n_tensors;
+    P.n_qubits = n;
+    if (opt) P.opt = *opt;
+    else tn_options_default(&P.opt);
+    if (P.opt.workspace_limit <= 0) P.opt.workspace_limit = int64_t(64) << 30;
+    if (k < 0 || (k > 0 && !bits)) { err = "bitstrings: need k >= 0 and a buffer"; return false; }
+    if (k > (int64_t(1) << 30)) { err = "bitstrings: k too large"; return false; }
+    // distinct bitstrings (c6: deduplicate, answer per input row)
+    P.k = k;
+    P.uniq_of.assign(k, 0);
+    {
+        std::unordered_map<std::string, int32_t> seen;
+        for (int64_t r = 0; r < k; ++r) {
+            std::string key(reinterpret_cast<const char *>(bits + r * n), n);
+            for (int q = 0; q < n; ++q)
+                if (uint8_t(key[q]) > 1) { err = "bitstrings: entries must be 0 or 1"; return false; }
+            auto it = seen.find(key);
+            if (it == seen.end()) {
+                it = seen.emplace(key, (int32_t)P.ubits.size()).first;
+                P.ubits.emplace_back(key.begin(), key.end());
+            }
+            P.uniq_of[r] = it->second;
+        }
+        P.k_unique = (int64_t)P.ubits.size();
+    }
+    // sliced edges
+    if (n_sliced < 0 || n_sliced > 40 || (n_sliced > 0 && !sliced)) { err = "sliced edges: bad count"; return false; }
+    P.sliced.assign(sliced, sliced + n_sliced);
+    {
+        std::set<int> s(P.sliced.begin(), P.sliced.end());
+        if ((int)s.size() != n_sliced) { err = "sliced edges: duplicates"; return false; }
+        for (int e : P.sliced)
+            if (e < 0 || e >= P.net.n_edges) { err = "sliced edges: id out of range"; return false; }
+    }
+    // tree
+    const int NN = 2 * T - 1;
+    P.nodes.assign(NN, Node());
+    if (T > 1 && !ssa) { err = "tree: missing"; return false; }
+    {
+        std::vector<int> used(NN, 0);
+        for (int i = 0; i < T - 1; ++i) {
+            const int a = ssa[2 * i], b = ssa[2 * i + 1];
+            if (a < 0 || b < 0 || a >= T + i || b >= T + i || a == b) {
+                err = "tree: pair " + std::to_string(i) + " refers to a node not yet created";
+                return false;
+            }
+            if (++used[a] > 1 || ++used[b] > 1) {
+                err = "tree: node used twice (pair " + std::to_string(i) + ")";
+                return false;
+            }
+            P.nodes[T + i].left = a;
+            P.nodes[T + i].right = b;
+            P.nodes[a].parent = T + i;
+            P.nodes[b].parent = T + i;
+        }
+    }
+    P.root = NN - 1;
+    // leaves: layout = open (unsliced) bond legs, ib first; outs; slices
+    std::vector<int> slice_index(P.net.n_edges, -1);
+    for (int j = 0; j < n_sliced; ++j) slice_index[P.sliced[j]] = j;  // external j for now
+    for (int v = 0; v < T; ++v) {
+        const LeafTensor &L = P.net.leaves[v];
+        Node &nd = P.nodes[v];
+        for (int g = 3; g >= 0; --g) {
+            if (L.legs[g].kind == LEG_BOND) {
+                if (slice_index[L.legs[g].id] >= 0) nd.slices.push_back(slice_index[L.legs[g].id]);
+                else nd.layout.push_back(L.legs[g].id);
+            }
+        }
+        for (int g = 0; g < 2; ++g)
+            if (L.legs[g].kind == LEG_OUT) nd.outs.push_back(L.legs[g].id);
+        std::sort(nd.outs.begin(), nd.outs.end());
+        std::sort(nd.slices.begin(), nd.slices.end());
+        nd.rank = (int)nd.layout.size();
+    }
+    std::vector<std::vector<int>> open(NN);
+    for (int v = 0; v < T; ++v) {
+        open[v] = P.nodes[v].layout;
+        std::sort(open[v].begin(), open[v].end());
+    }
+    for (int v = T; v < NN; ++v) {
+        Node &nd = P.nodes[v];
+        const Node &a = P.nodes[nd.left], &b = P.nodes[nd.right];
+        std::set_symmetric_difference(open[nd.left].begin(), open[nd.left].end(), open[nd.right].begin(),
+                                      open[nd.right].end(), std::back_inserter(open[v]));
+        nd.rank = (int)open[v].size();
+        std::set_union(a.outs.begin(), a.outs.end(), b.outs.begin(), b.outs.end(), std::back_inserter(nd.outs));
+        std::set_union(a.slices.begin(), a.slices.end(), b.slices.begin(), b.slices.end(),
+                       std::back_inserter(nd.slices));
+    }
+    if ((int)P.nodes[P.root].outs.size() != n) { err = "tree: root does not hold every output leg"; return false; }
+
+    Builder B{P, err, code, 0, 0, 0, {}, {}};
+    B.T = T;
+    B.NN = NN;
+    B.m = n_sliced;
+    B.out_instances();
+    // Internal slice order.  The first m_low sliced edges run side by side in
+    // one pass; the rest are looped over, bit t - m_low of the batch index,
+    // and in batch b only the nodes whose looped edges include a bit below
+    // ctz(b) + 1 are recomputed.  A node with looped edge set S is then
+    // computed 2^(h - min S) times instead of 2^|S| (depth-first reuse over
+    // slices, ideal when every node's edges are the most significant bits).
+    // Candidate orders are scored with that exact count, weighted by each
+    // node's flops, and the cheapest is kept.
+    {
+        std::vector<double> fl(NN, 0.0);
+        for (int v = T; v < NN; ++v) {
+            const Node &nd = P.nodes[v];
+            const int uni = (P.nodes[nd.left].rank + P.nodes[nd.right].rank + nd.rank) / 2;
+            fl[v] = 8.0 * std::ldexp(1.0, uni) * nd.n_out;
+        }
+        auto cost = [&](const std::vector<int> &order) {  // order[t] = external j
+            std::vector<int> pos(n_sliced);
+            for (int t = 0; t < n_sliced; ++t) pos[order[t]] = t;
+            double c = 0;
+            for (int v = T; v < NN; ++v) {
+                if (P.nodes[v].slices.empty()) { c += fl[v]; continue; }
+                int lo = n_sliced;
+                for (int j : P.nodes[v].slices) lo = std::min(lo, pos[j]);
+                c += fl[v] * std::ldexp(1.0, n_sliced - lo);
+            }
+            return c;
+        };
+        std::vector<std::vector<int>> cands;
+        std::vector<double> first(n_sliced, 0), nodes_with(n_sliced, 0), flops_with(n_sliced, 0);
+        for (int j = 0; j < n_sliced; ++j) {
+            const auto &ends = P.net.edge_ends[P.sliced[j]];
+            first[j] = std::min(P.nodes[ends[0]].parent, P.nodes[ends[1]].parent);
+        }
+        for (int v = T; v < NN; ++v)
+            for (int j : P.nodes[v].slices) {
+                nodes_with[j] += 1;
+                flops_with[j] += fl[v];
+            }
+        for (int c = 0; c < 3; ++c) {
+            std::vector<int> ord(n_sliced);
+            std::iota(ord.begin(), ord.end(), 0);
+            const std::vector<double> &key = c == 0 ? first : (c == 1 ? nodes_with : flops_with);
+            // fast-changing (low) bits first: latest met / used by the fewest / cheapest nodes
+            std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+                return c == 0 ? key[x] > key[y] : key[x] < key[y];
+            });
+            cands.push_back(ord);
+        }
+        size_t best = 0;
+        for (size_t c = 1; c < cands.size(); ++c)
+            if (cost(cands[c]) < cost(cands[best])) best = c;
+        P.perm = cands[best];
+        std::vector<int> internal(n_sliced);
+        for (int t = 0; t < n_sliced; ++t) internal[P.perm[t]] = t;
+        for (Node &nd : P.nodes) {
+            for (int &j : nd.slices) j = internal[j];
+            std::sort(nd.slices.begin(), nd.slices.end());
+        }
+        for (int e = 0; e < P.net.n_edges; ++e)
+            if (slice_index[e] >= 0) slice_index[e] = internal[slice_index[e]];
+    }
+    B.slice_of = slice_index;
+    // slice batch: explicit, or the largest that fits the workspace limit
+    int lo = 0, hi = std::min(n_sliced, 20);
+    if (P.opt.slice_batch_log2 >= 0) lo = hi = std::min(P.opt.slice_batch_log2, n_sliced);
+    int chosen = -1;
+    for (int ml = hi; ml >= lo; --ml) {
+        if (!B.schedule(ml)) return false;
+        const int64_t ws = B.layout_workspace(false);
+        if (ws <= P.opt.workspace_limit || ml == lo) {
+            chosen = ml;
+            if (ws > P.opt.workspace_limit && P.opt.slice_batch_log2 < 0) {
+                code = TN_ENOMEM;
+                err = "plan needs " + std::to_string(ws) + " workspace bytes even with one slice per pass";
+                return false;
+            }
+            break;
+        }
+    }
+    if (!B.schedule(chosen)) return false;
+    for (Node &nd : P.nodes) { nd.buf = NodeBuf(); }
+    P.peak_tensor_bytes = 0;
+    P.ws_bytes = B.layout_workspace(true);
+    // costs
+    P.flops_exec = P.flops_ma = P.flops_sa = P.bytes_min = 0;
+    for (const Step &st : P.steps) {
+        const Node &nd = P.nodes[st.node];
+        P.flops_exec += st.flops * st.runs;
+        P.bytes_min += st.bytes * st.runs;
+        const double macs = std::ldexp(1.0, st.mb + st.kb + st.nb);
+        P.flops_ma += 8.0 * macs * std::ldexp(1.0, (int)nd.slices.size()) * nd.n_out;
+        P.flops_sa += 8.0 * macs * std::ldexp(1.0, n_sliced) * double(P.k_unique);
+    }
+    code = TN_OK;
+    return true;
+}
+
+}  // namespace tnp

@@ -1,0 +1,152 @@
+// Host-side plan of a multiple-amplitude contraction (no CUDA calls here).
+//
+// The plan turns (circuit, bitstrings, contraction tree, sliced edges) into
+//   * the fused tensor network (SM Sec. II: one tensor per two-qubit gate),
+//   * the static reuse-instance DAG: for every tree node, the distinct
+//     projections of the bitstrings onto the node's output qubits (the width
+//     w of the paper's reuse tree, main text Eq. (1) and SM Sec. III),
+//     times the values of the sliced edges inside the node that run side by
+//     side in one pass,
+//   * a step list (one pairwise contraction per internal node) in
+//     execution order, split into slice-independent steps (run once per
+//     call) and slice-dependent steps (run once per slice batch),
+//   * a workspace layout (byte offsets into one caller-owned device buffer).
+#pragma once
+
+#include <array>
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tn.h"
+
+namespace tnp {
+
+using cd = std::complex<double>;
+
+enum LegKind { LEG_BOND = 0, LEG_OUT = 1, LEG_FIXED = 2 };
+
+struct Leg {
+    int kind;
+    int id;  // bond edge id, or qubit for an output leg
+};
+
+// Fused tensor of one two-qubit gate; t[((oa*2+ob)*2+ia)*2+ib], the legs
+// in that order.  A LEG_FIXED input leg is |0>: only ia = 0 (ib = 0) holds
+// the absorbed input vector.
+struct LeafTensor {
+    int gate;
+    int qa, qb;
+    Leg legs[4];  // oa, ob, ia, ib
+    cd t[16];
+};
+
+struct Network {
+    int n_qubits = 0, n_tensors = 0, n_edges = 0;
+    std::vector<LeafTensor> leaves;
+    std::vector<std::array<int, 2>> edge_ends;
+    std::vector<int> out_tensor;  // per qubit
+};
+
+bool build_network(const tn_circuit *circ, Network &net, std::string &err);
+
+// Device-side workspace offsets (bytes) of one node's data.
+struct NodeBuf {
+    int64_t data = -1;  // complex64 [n_inst][2^rank]
+    int64_t E = -1;     // int32 [n_inst] accumulated power-of-two exponent
+    int64_t mx = -1;    // uint32 [n_inst] max |component| float bits (rescale)
+    int64_t sig = -1;   // int32 [n_sig] -> (sigL, sigR) packed as 2 arrays
+    int64_t out = -1;   // int32 [n_out] -> (outL, outR) packed as 2 arrays
+};
+
+struct Node {
+    int left = -1, right = -1;   // children (-1 for leaves)
+    int parent = -1;
+    std::vector<int> layout;     // open bond edges, bit 0 first
+    std::vector<int> outs;       // output qubits in the subtree (sorted)
+    std::vector<int> slices;     // internal sliced-edge indices t in the subtree (sorted)
+    std::vector<int> slices_low; // those batched in one pass (t < m_low)
+    uint64_t hmask = 0;          // looped sliced edges in the subtree (bit t - m_low)
+    int level = 64;              // lowest bit of hmask; 64 = computed once per call
+    bool persistent = false;     // buffer kept across slice batches
+    int n_out = 1;               // distinct projections of the bitstrings on outs
+    int64_t n_sig = 1;           // 2^{|slices_low|}
+    int64_t n_inst = 1;          // n_sig * n_out
+    int rank = 0;
+    // instance maps (internal nodes): out-instance -> child out-instances,
+    // slice-instance -> child slice-instances
+    std::vector<int32_t> outL, outR, sigL, sigR;
+    // leaves: the projection value (2 bits: oa, ob order) of each out-instance
+    std::vector<int32_t> leaf_outval;
+    NodeBuf buf;
+    int step = -1;               // step producing this node
+    int last_use = -1;           // last step reading it
+};
+
+// One pairwise contraction C = A (x) B over K = I_A n I_B.
+// A is the operand with more entries per instance.  Output layout: the free
+// bits of B (in B's order) at the bottom, then the free bits of A.
+struct Step {
+    int node = -1, a = -1, b = -1;
+    int mb = 0, kb = 0, nb = 0;
+    std::vector<int8_t> pAm, pAk, pBk, pBn;  // bit positions in A / B
+    int level = 64;          // recomputed in batch b > first iff level <= ctz(b)
+    double runs = 1;         // passes over all 2^h batches
+    int kernel = 0;          // 0 = per-row SIMT, 1 = tiled SIMT GEMM, 2 = tensor-core GEMM
+    double flops = 0;        // executed per pass: 8 * n_inst * 2^{mb+kb+nb}
+    double bytes = 0;        // A + B reads and C write per pass
+};
+
+struct Plan {
+    Network net;
+    tn_options opt{};
+    int n_qubits = 0;
+    int64_t k = 0;                    // input rows
+    std::vector<int32_t> uniq_of;     // input row -> distinct bitstring id
+    int64_t k_unique = 0;
+    std::vector<std::vector<uint8_t>> ubits;  // distinct bitstrings
+    std::vector<int> sliced;          // sliced edge ids, external order (j-th takes bit j of s)
+    std::vector<int> perm;            // internal slice index t -> external j
+    int m_low = 0;                    // sliced edges batched in one pass
+    int64_t n_batches = 1;
+    std::vector<Node> nodes;          // 2T-1
+    std::vector<Step> steps;          // SSA order
+    int n_static_steps = 0;
+    int root = -1;
+    int max_rank = 0;
+    double flops_ma = 0, flops_sa = 0, flops_exec = 0, bytes_min = 0;
+    int64_t peak_tensor_bytes = 0;
+
+    // workspace layout
+    int64_t ws_bytes = 0;
+    int64_t off_leaf_full = -1;       // complex64 full leaf tensors
+    int64_t off_fill_jobs = -1;       // FillJob table
+    int64_t n_fill_jobs = 0;
+    int64_t off_leaf_high = -1;       // LeafHigh table
+    int64_t off_uniq = -1;            // int32 [k] input row -> root out-instance
+    int64_t off_emax = -1, emax_bytes = 0;  // max words of every node, by level
+    std::vector<int64_t> emax_prefix;       // [lv]: bytes covering the nodes of level <= lv
+    int64_t off_scratch = -1;               // 256 bytes of device scratch (error word)
+    // host images uploaded at bind time: (offset, bytes)
+    std::vector<std::pair<int64_t, std::vector<uint8_t>>> uploads;
+};
+
+struct FillJob {          // one leaf instance block
+    int64_t dst;          // complex64 element offset of the block in the workspace
+    int64_t src;          // element offset in the full-leaf region, high-slice bits = 0
+    int32_t leaf_high;    // index into the LeafHigh table
+    int32_t n;            // elements
+};
+
+struct LeafHigh {         // sliced legs of a leaf that vary across batches
+    int32_t cnt;
+    int32_t j[4];         // high sliced index (j - m_low)
+    int32_t stride[4];    // element stride of that leg in the full-leaf block
+};
+
+bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int32_t *ssa,
+               const int32_t *sliced, int32_t n_sliced, const tn_options *opt, Plan &plan,
+               std::string &err, int &code);
+
+}  // namespace tnp

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of the C ABI in ``include/tn.h`` (same names).
+
+Argument marshalling only: every step of the contraction runs in the
+library's CUDA kernels.  Device buffers are anything with ``data_ptr()``
+(torch tensors) or raw integer addresses; streams are ``torch.cuda.Stream``
+objects, raw ``cudaStream_t`` integers, or None (the legacy default stream).
+If the shared library is missing or fails to load, every entry point raises:
+there is no fallback path.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import builder as _build
+
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED, TN_ESTATE = 0, -1, -2, -3, -4, -5, -6
+TN_FP32, TN_TF32, TN_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp32": TN_FP32, "tf32": TN_TF32, "bf16x3": TN_BF16X3}
+
+EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_plan_widths", "tn_plan_steps",
+           "tn_plan_bind", "tn_contract", "tn_contract_slices", "tn_xeb", "tn_plan_profile",
+           "tn_plan_step_times", "tn_destroy", "tn_last_error")
+
+
+class TnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class tn_gate(ctypes.Structure):
+    _fields_ = [("q0", ctypes.c_int32), ("q1", ctypes.c_int32), ("layer", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("m", ctypes.c_double * 32)]
+
+
+class tn_circuit(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32),
+                ("gates", ctypes.POINTER(tn_gate))]
+
+
+class tn_options(ctypes.Structure):
+    _fields_ = [("workspace_limit", ctypes.c_int64), ("slice_batch_log2", ctypes.c_int32),
+                ("rescale", ctypes.c_int32), ("fuse", ctypes.c_int32), ("fuse_max_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
+
+
+class tn_plan_info(ctypes.Structure):
+    _fields_ = [("n_tensors", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("n_steps", ctypes.c_int32), ("n_unique", ctypes.c_int32), ("n_sliced", ctypes.c_int32),
+                ("slice_batch_log2", ctypes.c_int32), ("n_batches", ctypes.c_int32),
+                ("max_rank", ctypes.c_int32), ("n_static_steps", ctypes.c_int32),
+                ("flops_ma", ctypes.c_double), ("flops_sa", ctypes.c_double), ("flops_exec", ctypes.c_double),
+                ("bytes_min", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
+                ("peak_tensor_bytes", ctypes.c_int64)]
+
+
+class tn_step_info(ctypes.Structure):
+    _fields_ = [("node", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32), ("mb", ctypes.c_int32),
+                ("kb", ctypes.c_int32), ("nb", ctypes.c_int32), ("rank_a", ctypes.c_int32),
+                ("rank_b", ctypes.c_int32), ("level", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("n_inst", ctypes.c_int64), ("n_inst_a", ctypes.c_int64), ("n_inst_b", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("runs", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the in-tree shared library (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path} is missing (run build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "tn_options_default": (None, [ctypes.POINTER(tn_options)]),
+        "tn_network": (ctypes.c_int, [ctypes.POINTER(tn_circuit), vp, vp, vp, vp]),
+        "tn_plan": (ctypes.c_int, [ctypes.POINTER(tn_circuit), vp, i64, vp, vp, i32,
+                                   ctypes.POINTER(tn_options), ctypes.POINTER(vp)]),
+        "tn_plan_query": (ctypes.c_int, [vp, ctypes.POINTER(tn_plan_info)]),
+        "tn_plan_widths": (ctypes.c_int, [vp, vp, vp, vp]),
+        "tn_plan_bind": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
+        "tn_plan_steps": (ctypes.c_int, [vp, vp, i32]),
+        "tn_contract": (ctypes.c_int, [vp, ctypes.c_int, i64, i64, vp, vp]),
+        "tn_contract_slices": (ctypes.c_int, [vp, ctypes.c_int, vp, i32, vp, vp]),
+        "tn_xeb": (ctypes.c_int, [vp, i64, i32, vp, vp]),
+        "tn_plan_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "tn_plan_step_times": (ctypes.c_int, [vp, vp, i32]),
+        "tn_destroy": (None, [vp]),
+        "tn_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != TN_OK:
+        raise TnError(rc, load().tn_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def circuit_struct(circ):
+    """Marshal an ``rqc.Circuit`` into a ``tn_circuit`` (keeps the arrays alive)."""
+    q0, q1, layer, m = circ.to_arrays()
+    arr = (tn_gate * len(q0))()
+    for i in range(len(q0)):
+        arr[i].q0, arr[i].q1, arr[i].layer = int(q0[i]), int(q1[i]), int(layer[i])
+        ctypes.memmove(arr[i].m, m[i].ctypes.data, 32 * 8)
+    c = tn_circuit(circ.n_qubits, len(q0), arr)
+    c._keep = arr
+    return c
+
+
+def options(**kw) -> tn_options:
+    o = tn_options()
+    load().tn_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def tn_network(circ):
+    lib = load()
+    c = circuit_struct(circ)
+    nt, ne = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.tn_network(ctypes.byref(c), ctypes.byref(nt), ctypes.byref(ne), None, None))
+    ends = np.zeros((ne.value, 2), np.int32)
+    outs = np.zeros(circ.n_qubits, np.int32)
+    _check(lib.tn_network(ctypes.byref(c), None, None, ends.ctypes.data, outs.ctypes.data))
+    return nt.value, ne.value, ends, outs
+
+
+class Plan:
+    """A tn_plan handle: host planning in the constructor, device work after
+    :meth:`tn_plan_bind`."""
+
+    def __init__(self, circ, bits, tree_ssa, sliced=(), **opts):
+        lib = load()
+        self._lib = lib
+        self.n_qubits = circ.n_qubits
+        c = circuit_struct(circ)
+        self._bits = np.ascontiguousarray(bits, np.uint8)
+        self.k = self._bits.shape[0]
+        ssa = np.ascontiguousarray(np.asarray(tree_ssa, np.int32).reshape(-1, 2))
+        sl = np.ascontiguousarray(np.asarray(list(sliced), np.int32))
+        o = options(**opts)
+        h = ctypes.c_void_p()
+        _check(lib.tn_plan(ctypes.byref(c), self._bits.ctypes.data if self.k else None, self.k,
+                           ssa.ctypes.data if ssa.size else None, sl.ctypes.data if sl.size else None,
+                           len(sl), ctypes.byref(o), ctypes.byref(h)))
+        self.h = h.value
+        self.n_sliced = len(sl)
+        self._ws = None
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._lib.tn_destroy(self.h)
+            self.h = None
+
+    def tn_plan_query(self) -> dict:
+        info = tn_plan_info()
+        _check(self._lib.tn_plan_query(self.h, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in tn_plan_info._fields_}
+
+    info = property(tn_plan_query)
+
+    def tn_plan_widths(self):
+        n = self.info["n_nodes"]
+        w = np.zeros(n, np.int64)
+        r = np.zeros(n, np.int32)
+        s = np.zeros(n, np.int32)
+        _check(self._lib.tn_plan_widths(self.h, w.ctypes.data, r.ctypes.data, s.ctypes.data))
+        return w, r, s
+
+    def tn_plan_steps(self):
+        """Per-step features as a list of dicts (execution order)."""
+        n = self.info["n_steps"]
+        arr = (tn_step_info * max(n, 1))()
+        _check(self._lib.tn_plan_steps(self.h, arr, n))
+        return [{f: getattr(arr[i], f) for f, _ in tn_step_info._fields_} for i in range(n)]
+
+    def tn_plan_bind(self, workspace, nbytes=None, stream=None):
+        if nbytes is None:
+            nbytes = workspace.numel() * workspace.element_size()
+        self._ws = workspace  # keep it alive while bound
+        _check(self._lib.tn_plan_bind(self.h, _ptr(workspace), int(nbytes), _stream(stream)))
+
+    def tn_contract(self, amps, precision=TN_FP32, batch_lo=0, batch_hi=None, stream=None):
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        if batch_hi is None:
+            batch_hi = self.info["n_batches"]
+        _check(self._lib.tn_contract(self.h, int(precision), int(batch_lo), int(batch_hi), _ptr(amps),
+                                     _stream(stream)))
+
+    def tn_contract_slices(self, slice_ids, partials, precision=TN_FP32, stream=None):
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        ids = np.ascontiguousarray(np.asarray(slice_ids, np.int64))
+        _check(self._lib.tn_contract_slices(self.h, int(precision), ids.ctypes.data, len(ids), _ptr(partials),
+                                            _stream(stream)))
+
+    def tn_plan_profile(self, enable=True):
+        _check(self._lib.tn_plan_profile(self.h, 1 if enable else 0))
+
+    def tn_plan_step_times(self):
+        n = self.info["n_steps"]
+        ms = np.zeros(n, np.float64)
+        _check(self._lib.tn_plan_step_times(self.h, ms.ctypes.data, n))
+        return ms
+
+
+def tn_xeb(amps, k, n_qubits, out, stream=None):
+    _check(load().tn_xeb(_ptr(amps), int(k), int(n_qubits), _ptr(out), _stream(stream)))

@@ -1,0 +1,182 @@
+"""Host-side checks of the CUDA library: it loads, exports every entry point
+declared in include/tn.h, builds the same network as the input generators,
+and its reuse-instance DAG has the widths of Eq. (1) (brute-force counts,
+the paper's bounds, and the uniform-bitstring law behind Table S2).  No
+GPU is touched: tn_plan is host-only.
+"""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from rqc import make_workload, network_structure, random_circuit, grid_layout
+from rqc.bitstrings import uniform_bitstrings
+from rqc.tree import candidate_trees, expected_width
+
+
+@pytest.fixture(scope="module")
+def tn():
+    from paper_2212_04749_gb300 import builder
+    builder.build()
+    from paper_2212_04749_gb300 import tn as mod
+    mod.load()
+    return mod
+
+
+def test_library_exports_every_declared_entry_point(tn, root):
+    hdr = open(os.path.join(root, "include", "tn.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char \*)\s*(tn_\w+)\s*\(", hdr, re.M))
+    assert declared, "no declarations parsed"
+    lib = tn.load()
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared == set(tn.EXPORTS)
+
+
+@pytest.mark.parametrize("name", ["grid3x4_m8", "grid5x6_m14", "diamond53_m12"])
+def test_network_matches_generator_structure(tn, name):
+    w = make_workload(name)
+    nt, ne, ends, outs = tn.tn_network(w.circuit)
+    assert nt == w.struct.n_tensors and ne == w.struct.n_edges
+    assert np.array_equal(ends, w.struct.edge_ends)
+    for q in range(w.circuit.n_qubits):
+        assert q in w.struct.tensor_outputs[outs[q]]
+
+
+def _subtree_outs(struct, ssa):
+    T = struct.n_tensors
+    outs = [set(struct.tensor_outputs[t]) for t in range(T)]
+    for a, b in ssa:
+        outs.append(outs[a] | outs[b])
+    return outs
+
+
+@pytest.mark.parametrize("name", ["grid3x4_m8", "grid5x6_m14"])
+def test_widths_are_distinct_projection_counts(tn, name):
+    w = make_workload(name)
+    p = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced)
+    width, rank, nsl = p.tn_plan_widths()
+    outs = _subtree_outs(w.struct, w.tree.ssa)
+    ku = len({b.tobytes() for b in w.bits})
+    for v, o in enumerate(outs):
+        cols = sorted(o)
+        brute = len({row.tobytes() for row in w.bits[:, cols]}) if cols else 1
+        assert width[v] == brute, v
+    # Eq. (1) bounds: the root carries every bitstring, widths never shrink
+    # towards the root, a leaf carries at most its 2 output legs' 4 values
+    assert width[-1] == ku
+    T = w.struct.n_tensors
+    for i, (a, b) in enumerate(w.tree.ssa):
+        assert width[T + i] >= max(width[a], width[b])
+        assert width[T + i] <= width[a] * width[b]
+    assert width[:T].max() <= 4
+
+
+def test_widths_follow_the_uniform_occupancy_law(tn):
+    # the law the paper's Table S2 widths obey (2^j (1-(1-2^-j)^k)); for
+    # k = 3e6 it gives 988,587 at j = 20 against the printed 981,285
+    c = random_circuit(grid_layout(4, 5), 6, seed=12)
+    s = network_structure(c)
+    k = 3000
+    bits = uniform_bitstrings(20, k, seed=99)
+    ssa = candidate_trees(s, k, seed=1, trials=1)[0]
+    p = tn.Plan(c, bits, ssa, [])
+    width, _, _ = p.tn_plan_widths()
+    outs = _subtree_outs(s, ssa)
+    for v, o in enumerate(outs):
+        j = len(o)
+        mu = expected_width(j, k)
+        # variance of the occupied-bin count is below its mean
+        assert abs(width[v] - mu) <= 6 * np.sqrt(max(mu, 1.0)) + 1, (v, j, width[v], mu)
+    assert abs(expected_width(20, 3 * 10 ** 6) - 988587) < 1
+    assert abs(expected_width(16, 3 * 10 ** 6) - 65536) < 1
+
+
+def test_all_amplitudes_give_doubling_widths(tn):
+    # SM Sec. III.B: computing all 2^n amplitudes, every output leg met
+    # doubles the width (w_l = 2^{l-1})
+    w = make_workload("grid3x4_m8")
+    allbits = ((np.arange(4096)[:, None] >> np.arange(11, -1, -1)[None, :]) & 1).astype(np.uint8)
+    p = tn.Plan(w.circuit, allbits, w.tree.ssa, [])
+    width, _, _ = p.tn_plan_widths()
+    outs = _subtree_outs(w.struct, w.tree.ssa)
+    for v, o in enumerate(outs):
+        assert width[v] == 2 ** len(o)
+
+
+def _eq1_flops(w, p):
+    width, rank, nsl = p.tn_plan_widths()
+    T = w.struct.n_tensors
+    total = 0.0
+    for i, (a, b) in enumerate(w.tree.ssa):
+        v = T + i
+        union = (rank[a] + rank[b] + rank[v]) // 2
+        total += 8.0 * (2.0 ** union) * (2.0 ** nsl[v]) * width[v]
+    return total
+
+
+@pytest.mark.parametrize("name", ["grid3x4_m8", "grid5x6_m14"])
+def test_plan_cost_is_eq1_and_executed_without_recomputation(tn, name):
+    w = make_workload(name)
+    p = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced)
+    info = p.info
+    assert info["flops_ma"] == pytest.approx(_eq1_flops(w, p), rel=1e-12)
+    # the slice loop recomputes a node only when one of its sliced values
+    # changes; with the plan's slice order that is (nearly) never more often
+    # than Eq. (1) counts
+    assert info["flops_ma"] <= info["flops_exec"] <= info["flops_ma"] * (1 + 1e-4)
+    assert info["flops_ma"] < info["flops_sa"]
+    steps = p.tn_plan_steps()
+    assert len(steps) == w.struct.n_tensors - 1
+    assert sum(s["flops"] * s["runs"] for s in steps) == pytest.approx(info["flops_exec"], rel=1e-12)
+
+
+def test_slice_batch_trades_memory_for_passes(tn):
+    w = make_workload("grid5x6_m14")
+    infos = [tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, slice_batch_log2=b).info for b in (2, 5)]
+    assert infos[0]["n_batches"] == 2 ** 8 and infos[1]["n_batches"] == 2 ** 5
+    assert infos[0]["workspace_bytes"] < infos[1]["workspace_bytes"]
+    assert infos[0]["flops_exec"] == pytest.approx(infos[1]["flops_exec"], rel=1e-4)
+
+
+def test_duplicate_bitstrings_are_planned_once(tn):
+    w = make_workload("grid3x4_m8")
+    bits = np.concatenate([w.bits, w.bits[:10]])
+    p = tn.Plan(w.circuit, bits, w.tree.ssa, [])
+    assert p.info["n_unique"] == 64
+
+
+@pytest.mark.parametrize("case", ["tree_reuse", "tree_forward", "bits_value", "slice_range", "slice_dup"])
+def test_invalid_inputs_are_rejected(tn, case):
+    w = make_workload("grid3x4_m8")
+    ssa, bits, sl = w.tree.ssa.copy(), w.bits.copy(), [0, 1]
+    if case == "tree_reuse":
+        ssa[5] = ssa[4]
+    elif case == "tree_forward":
+        ssa[0, 0] = 60
+    elif case == "bits_value":
+        bits[3, 4] = 2
+    elif case == "slice_range":
+        sl = [10 ** 6]
+    else:
+        sl = [3, 3]
+    with pytest.raises(tn.TnError) as ei:
+        tn.Plan(w.circuit, bits, ssa, sl)
+    assert ei.value.code == tn.TN_EINVAL
+    assert str(ei.value)
+
+
+def test_qubit_without_two_qubit_gate_is_rejected(tn):
+    from rqc.circuit import product_circuit
+    with pytest.raises(tn.TnError):
+        tn.tn_network(product_circuit(3, 2, seed=1))
+
+
+def test_contract_before_bind_is_a_state_error(tn):
+    w = make_workload("grid3x4_m8")
+    p = tn.Plan(w.circuit, w.bits, w.tree.ssa, [])
+    with pytest.raises(tn.TnError) as ei:
+        p.tn_contract(12345, "fp32")
+    assert ei.value.code == tn.TN_ESTATE
