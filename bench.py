@@ -1,0 +1,387 @@
+"""Throughput of the multiple-amplitude contraction on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload grid5x6_m14] [--precision fp32|tf32|bf16x3]
+
+One step = one full tn_contract over every slice batch of the workload's
+plan: the amplitudes of all its bitstrings (30 qubits, 14 cycles, 4096
+bitstrings, 2^10 slices by default).  Prints one JSON line (rank 0).
+
+value      amplitudes/s over all ranks: bitstrings x ranks / max-over-ranks
+           device time (CUDA events around each tn_contract; inputs and
+           plan resident in HBM; a 512 MiB write flushes L2 between steps).
+e2e        the same metric through the public API from host data: tn_plan
+           (host), tn_plan_bind (tables up), tn_contract, amplitudes down,
+           timed on the host clock.
+roofline   the kernel family with the largest share of device time,
+           algorithmic bytes or flops / its measured launch time, against
+           the measured peak.
+cpu_baseline  the CPU oracle (state vector, complex128) on this host's
+           cores, timed on a bounded sample of its gate passes.
+--impl reference times that oracle as the reference arm.
+Multi-GPU (torchrun): each rank contracts its own seeded bitstrings (weak
+scaling, no collective on the data path).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "amplitudes/sec & TFLOP/s (frac of peak), mixed vs FP32 at stated amp error"
+UNIT = "amplitudes/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _bits_for_rank(w, rank):
+    from rqc.bitstrings import uniform_bitstrings
+    if rank == 0:
+        return w.bits
+    return uniform_bitstrings(w.circuit.n_qubits, w.bits.shape[0], seed=2000 + w.spec.index + 1000 * rank)
+
+
+def _golden(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_sv.txt")
+    if not os.path.exists(path):
+        return None
+    vals = []
+    for line in open(path):
+        if not line.startswith("#"):
+            re_, im_ = line.split()
+            vals.append(complex(float(re_), float(im_)))
+    return np.asarray(vals, np.complex128)
+
+
+def cpu_oracle_sample(w, budget_s=20.0):
+    """The complex128 state-vector oracle on a bounded sample: the state is
+    evolved through the first g gates (g grown until ~budget_s of CPU work),
+    and the full run's time is extrapolated per gate pass."""
+    from oracle import sv as osv
+    from rqc.circuit import Circuit
+    total = len(w.circuit.gates)
+    g = 8
+    while True:
+        c = Circuit(n_qubits=w.circuit.n_qubits, gates=w.circuit.gates[:g])
+        t0 = time.perf_counter()
+        osv.state(c)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 3 or g >= total:
+            break
+        g = min(total, max(g + 1, int(g * min(8.0, budget_s / 3 / max(dt, 1e-3)))))
+    t_full = dt * (total + 1) / (g + 1)
+    k = w.bits.shape[0]
+    return {"value": k / t_full, "unit": UNIT, "cores": osv.threads(), "kind": "oracle",
+            "sample": f"state-vector oracle (complex128, 2^{w.circuit.n_qubits} amplitudes) through the first "
+                      f"{g} of {total} gates in {dt:.2f} s, extrapolated per gate pass to {t_full:.1f} s "
+                      f"for the {k} bitstrings"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from rqc import make_workload
+    w = make_workload(args.workload)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, budget_s=3.0)
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(w, budget_s=args.ref_budget))
+    v = statistics.median(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.bits.shape[0] / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[-1]["cores"], "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2212_04749_gb300 import builder, tn
+    from rqc import make_workload
+
+    builder.build()
+    tn.load()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = make_workload(args.workload)
+    bits = _bits_for_rank(w, rank)
+    k = bits.shape[0]
+    stream = torch.cuda.current_stream()
+    free, _ = torch.cuda.mem_get_info()
+    limit = min(int(args.ws_gib * 2 ** 30), int(free * 0.8))
+    t0 = time.perf_counter()
+    plan = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit)
+    t_plan = time.perf_counter() - t0
+    info = plan.info
+    ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
+    plan.tn_plan_bind(ws, stream=stream)
+    amps = torch.zeros(2 * k, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+
+    def one_step(prec, profile=False):
+        amps.zero_()
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        plan.tn_plan_profile(profile)
+        e0.record(stream)
+        plan.tn_contract(amps, prec, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        one_step(args.precision)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    step_ms = np.zeros(info["n_steps"])
+    kernels = None
+    with Clocks(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            times.append(one_step(args.precision, profile=True))
+            ms, kernels = plan.tn_plan_step_times()
+            step_ms += ms
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = clk.summary()
+    mean_ms = sum(times) / len(times)
+    t_max = mean_ms
+    if dist is not None:
+        tt = torch.tensor([mean_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = tt.item()
+    value = k * world / (t_max / 1000.0)
+    plan.tn_plan_profile(False)
+
+    # accuracy of this run against the stored oracle values
+    got = amps.cpu().numpy().view(np.complex128)
+    ref = _golden(args.workload) if rank == 0 else None
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref)) if ref is not None and len(ref) == k else None
+
+    # mixed-precision forms on the same workload
+    mixed = {}
+    if args.mixed and rank == 0:
+        for prec in ("bf16x3", "tf32"):
+            if prec == args.precision:
+                continue
+            one_step(prec)
+            ts = [one_step(prec) for _ in range(max(2, args.steps // 2))]
+            g2 = amps.cpu().numpy().view(np.complex128)
+            e2 = float(np.linalg.norm(g2 - ref) / np.linalg.norm(ref)) if ref is not None else None
+            mixed[prec] = {"amplitudes_per_s": k / (statistics.mean(ts) / 1000.0), "ms_per_step": statistics.mean(ts),
+                           "rel_l2_vs_oracle": e2}
+
+    # roofline of the dominant kernel family
+    peaks, peak_src = _peaks()
+    steps = plan.tn_plan_steps()
+    fam_names = {0: "k_step_row", 1: "k_step_gemm_simt", 2: "k_step_gemm_tc"}
+    fam_ms, fam_bytes, fam_flops, fam_launch = {}, {}, {}, {}
+    for s, st in enumerate(steps):
+        f = int(kernels[s]) if kernels is not None else 0
+        fam_ms[f] = fam_ms.get(f, 0.0) + step_ms[s] / args.steps
+        fam_bytes[f] = fam_bytes.get(f, 0.0) + st["bytes"] * st["runs"]
+        fam_flops[f] = fam_flops.get(f, 0.0) + st["flops"] * st["runs"]
+        fam_launch[f] = fam_launch.get(f, 0) + int(st["runs"])
+    dom = max(fam_ms, key=fam_ms.get)
+    sec = fam_ms[dom] / 1000.0
+    if dom == 0:
+        ach = fam_bytes[dom] / sec / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    elif dom == 1:
+        pk = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = fam_flops[dom] / sec / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
+    else:
+        base = peaks["bf16_tflops_sustained"]
+        pk = base / 3.0 if args.precision == "bf16x3" else base * (1.1 / 2.25)
+        ach = fam_flops[dom] / sec / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = fam_names[dom]
+    roof["launches_per_step"] = fam_launch[dom]
+    roof["share_of_step_time"] = fam_ms[dom] / max(sum(fam_ms.values()), 1e-12)
+    roof["peak_source"] = peak_src
+    roof["per_kernel_ms"] = {fam_names[f]: fam_ms[f] for f in fam_ms}
+
+    # end to end through the public API from host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned_out = torch.empty(2 * k, dtype=torch.float64, pin_memory=True)
+        ws2 = ws
+        tw = []
+        for _ in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p2 = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit)
+            p2.tn_plan_bind(ws2, stream=stream)
+            amps.zero_()
+            p2.tn_contract(amps, args.precision, stream=stream)
+            pinned_out.copy_(amps, non_blocking=True)
+            stream.synchronize()
+            tw.append(time.perf_counter() - t0)
+            del p2
+        plan.tn_plan_bind(ws, stream=stream)
+        e2e_s = statistics.mean(tw[1:])
+        e2e = {"value": k * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(info["upload_bytes"]),
+               "d2h_bytes_per_step": int(16 * k), "host_plan_s": t_plan}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(w, budget_s=args.ref_budget)
+
+    tflops = info["flops_ma"] / (t_max / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "fp32", "tf32": "tf32", "bf16x3": "bf16x3"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "qubits": w.circuit.n_qubits, "cycles": w.spec.cycles,
+                   "bitstrings": k, "sliced_edges": len(w.tree.sliced), "slices": 2 ** len(w.tree.sliced),
+                   "slice_batch": 2 ** info["slice_batch_log2"], "precision": args.precision,
+                   "l2": "512 MiB write between steps; intermediates exceed L2",
+                   "flops_eq1": info["flops_ma"], "flops_single_amplitude_x_k": info["flops_sa"],
+                   "bytes_algorithmic": info["bytes_min"], "max_rank": info["max_rank"],
+                   "workspace_gib": info["workspace_bytes"] / 2 ** 30},
+        "tflops_algorithmic": tflops,
+        "rel_l2_vs_oracle": err,
+        "mixed": mixed or None,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(info["launches_per_call"]) * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="grid5x6_m14")
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16x3"], default="fp32")
+    ap.add_argument("--ws-gib", type=float, default=64.0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

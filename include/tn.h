@@ -103,6 +103,8 @@ typedef struct {
                                      intermediate written once, read once per use */
     int64_t workspace_bytes;      /* device bytes tn_plan_bind needs */
     int64_t peak_tensor_bytes;    /* largest intermediate set (all instances) */
+    int64_t upload_bytes;         /* host-to-device bytes tn_plan_bind copies */
+    int64_t launches_per_call;    /* kernels one full tn_contract launches */
 } tn_plan_info;
 
 typedef struct tn_plan_s *tn_plan_t;
@@ -142,6 +144,10 @@ typedef struct {
     int64_t n_inst, n_inst_a, n_inst_b;  /* instances of the output and operands */
     double flops, bytes;      /* per pass: 8 * n_inst * 2^(mb+kb+nb); A + B reads + C write */
     double runs;              /* passes over all slice batches */
+    int32_t a_run_m, a_run_k; /* lowest address bits of an A instance that are
+                                 consecutive m (resp. k) bits: contiguous runs */
+    int32_t b_run_k, b_run_n;
+    int64_t n_groups;         /* runs of output instances sharing one A instance */
 } tn_step_info;
 
 int tn_plan_steps(tn_plan_t plan, tn_step_info *steps, int32_t n);
@@ -176,10 +182,14 @@ int tn_contract_slices(tn_plan_t plan, int precision, const int64_t *slice_ids, 
  * asynchronous on `stream`. */
 int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, void *stream);
 
-/* Device time of each step of the last tn_contract* call, when profiling is
- * on (tn_plan_profile(plan, 1)); ms has n_steps entries. */
+/* Device time of each step summed over the slice batches of the last
+ * tn_contract* call, when profiling is on (tn_plan_profile(plan, 1): CUDA
+ * events around every launch, read back by tn_plan_step_times, which
+ * synchronises the events); ms has n_steps entries.  kernel (may be NULL)
+ * receives the kernel family each step last ran: 0 per-row SIMT, 1 tiled
+ * SIMT GEMM, 2 tensor-core GEMM. */
 int tn_plan_profile(tn_plan_t plan, int enable);
-int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t n);
+int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t *kernel, int32_t n);
 
 void tn_destroy(tn_plan_t plan);
 

@@ -36,8 +36,10 @@ struct PlanObj {
     std::vector<tnk::StepDesc> desc;  // per step
     int32_t *err_flag = nullptr;      // device word for bounded waits
     bool profile = false;
-    std::vector<cudaEvent_t> ev;
-    std::vector<double> step_ms;
+    std::vector<cudaEvent_t> ev;          // pool, two per profiled launch
+    std::vector<int> ev_step;             // step of each recorded pair
+    size_t ev_used = 0;
+    std::vector<int32_t> step_kernel;     // kernel family each step ran last (0 row, 1 SIMT GEMM, 2 TC GEMM)
     int64_t last_batches = 0;
 };
 
@@ -81,12 +83,19 @@ void build_descs(PlanObj *o) {
         d.mb = st.mb;
         d.kb = st.kb;
         d.nb = st.nb;
-        for (int j = 0; j < st.mb; ++j) d.pAm[j] = st.pAm[j];
-        for (int j = 0; j < st.kb; ++j) {
-            d.pAk[j] = st.pAk[j];
-            d.pBk[j] = st.pBk[j];
+        for (int j = 0; j < st.mb; ++j) {
+            d.pAm[j] = st.pAm[j];
+            d.pCm[j] = st.pCm[j];
         }
-        for (int j = 0; j < st.nb; ++j) d.pBn[j] = st.pBn[j];
+        for (int j = 0; j < st.nb; ++j) {
+            d.pBn[j] = st.pBn[j];
+            d.pCn[j] = st.pCn[j];
+        }
+        d.gfirst = at<const int64_t>(o, st.off_groups);
+        d.n_groups = st.n_groups;
+        int64_t mg = 0;
+        for (int64_t g = 0; g < st.n_groups; ++g) mg = std::max(mg, st.group_first[g + 1] - st.group_first[g]);
+        d.max_group = (int32_t)mg;
         o->desc.push_back(d);
     }
 }
@@ -95,13 +104,19 @@ int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
     const tnp::Step &S = o->P.steps[s];
     const tnk::StepDesc &d = o->desc[s];
     cudaError_t e;
+    int fam;
     if (S.kernel == 0) {
+        fam = 0;
         e = tnk::launch_step_row(d, st);
     } else if (precision != TN_FP32 && tnk::gemm_tc_supports(d)) {
+        fam = 2;
         e = tnk::launch_step_gemm_tc(d, precision, o->err_flag, st);
     } else {
+        fam = 1;
         e = tnk::launch_step_gemm_simt(d, st);
     }
+    if ((int)o->step_kernel.size() <= s) o->step_kernel.resize(o->P.steps.size(), -1);
+    o->step_kernel[s] = fam;
     if (e != cudaSuccess)
         return set_err(TN_ECUDA, "step " + std::to_string(s) + ": " + cudaGetErrorString(e));
     return TN_OK;
@@ -114,42 +129,37 @@ template <class F>
 int run_batches(PlanObj *o, int precision, int64_t b_lo, int64_t b_hi, cudaStream_t st, F per_batch) {
     tnp::Plan &P = o->P;
     const int nst = (int)P.steps.size();
-    if (o->profile) {
-        for (int i = (int)o->ev.size(); i < 2 * nst; ++i) {
-            cudaEvent_t e;
-            CU(cudaEventCreate(&e));
-            o->ev.push_back(e);
-        }
-        o->step_ms.assign(nst, 0.0);
-    }
+    o->ev_used = 0;
+    o->ev_step.clear();
     const auto *jobs = at<const tnk::FillJobD>(o, P.off_fill_jobs);
     const auto *highs = at<const tnk::LeafHighD>(o, P.off_leaf_high);
-    std::vector<int> ran;
     for (int64_t b = b_lo; b < b_hi; ++b) {
         const int lv = (b == b_lo) ? 64 : __builtin_ctzll((unsigned long long)b);
         const int64_t clear = (b == b_lo) ? P.emax_bytes : P.emax_prefix[lv];
         if (clear) CU(cudaMemsetAsync(o->ws + P.off_emax, 0, clear, st));
         cudaError_t e = tnk::launch_fill(jobs, P.n_fill_jobs, highs, b, at<float2>(o, 0), st);
         if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("leaf fill: ") + cudaGetErrorString(e));
-        ran.clear();
         for (int s = 0; s < nst; ++s) {
             if (b != b_lo && P.steps[s].level > lv) continue;
-            if (o->profile) CU(cudaEventRecord(o->ev[2 * s], st));
+            if (o->profile) {
+                while (o->ev.size() < 2 * (o->ev_used + 1)) {
+                    cudaEvent_t ev;
+                    CU(cudaEventCreate(&ev));
+                    o->ev.push_back(ev);
+                }
+                CU(cudaEventRecord(o->ev[2 * o->ev_used], st));
+            }
             if (int rc = run_step(o, s, precision, st)) return rc;
-            if (o->profile) CU(cudaEventRecord(o->ev[2 * s + 1], st));
-            ran.push_back(s);
-        }
-        if (o->profile) {
-            CU(cudaStreamSynchronize(st));
-            for (int s : ran) {
-                float ms = 0.f;
-                CU(cudaEventElapsedTime(&ms, o->ev[2 * s], o->ev[2 * s + 1]));
-                o->step_ms[s] += ms;
+            if (o->profile) {
+                CU(cudaEventRecord(o->ev[2 * o->ev_used + 1], st));
+                o->ev_step.push_back(s);
+                o->ev_used++;
             }
         }
         if (int rc = per_batch(b)) return rc;
     }
     o->last_batches = b_hi - b_lo;
+    (void)nst;
     return TN_OK;
 }
 
@@ -215,6 +225,12 @@ int tn_plan_query(tn_plan_t plan, tn_plan_info *info) {
     info->bytes_min = P.bytes_min;
     info->workspace_bytes = P.ws_bytes;
     info->peak_tensor_bytes = P.peak_tensor_bytes;
+    int64_t up = 0;
+    for (const auto &u : P.uploads) up += (int64_t)u.second.size();
+    info->upload_bytes = up;
+    double steps_run = 0;
+    for (const tnp::Step &st : P.steps) steps_run += st.runs;
+    info->launches_per_call = (int64_t)steps_run + 2 * P.n_batches;  // + leaf fill and accumulate per batch
     return TN_OK;
 }
 
@@ -251,6 +267,16 @@ int tn_plan_steps(tn_plan_t plan, tn_step_info *out, int32_t n) {
         r.flops = st.flops;
         r.bytes = st.bytes;
         r.runs = st.runs;
+        auto run = [](const std::vector<int8_t> &pos) {
+            int j = 0;
+            while (j < (int)pos.size() && pos[j] == j) ++j;
+            return j;
+        };
+        r.a_run_m = run(st.pAm);
+        r.a_run_k = run(st.pAk);
+        r.b_run_k = run(st.pBk);
+        r.b_run_n = run(st.pBn);
+        r.n_groups = st.n_groups;
     }
     return TN_OK;
 }
@@ -359,10 +385,19 @@ int tn_plan_profile(tn_plan_t plan, int enable) {
     return TN_OK;
 }
 
-int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t n) {
+int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t *kernel, int32_t n) {
     if (!plan || !ms) return set_err(TN_EINVAL, "tn_plan_step_times: null argument");
     PlanObj *o = reinterpret_cast<PlanObj *>(plan);
-    for (int32_t i = 0; i < n && i < (int32_t)o->step_ms.size(); ++i) ms[i] = o->step_ms[i];
+    for (int32_t i = 0; i < n; ++i) {
+        ms[i] = 0.0;
+        if (kernel) kernel[i] = i < (int32_t)o->step_kernel.size() ? o->step_kernel[i] : -1;
+    }
+    for (size_t q = 0; q < o->ev_used; ++q) {
+        CU(cudaEventSynchronize(o->ev[2 * q + 1]));
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, o->ev[2 * q], o->ev[2 * q + 1]));
+        if (o->ev_step[q] < n) ms[o->ev_step[q]] += t;
+    }
     return TN_OK;
 }
 

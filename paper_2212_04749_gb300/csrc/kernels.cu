@@ -73,123 +73,107 @@ __global__ void k_fill(const FillJobD *__restrict__ jobs, int64_t njobs, const L
 
 constexpr int ROW_THREADS = 256;
 
-// K*N <= 64; NB = log2 N (0..4).
+// One thread per row m of an A instance; B (K x N <= 256 entries) of the
+// instance in shared memory when the block lies inside one instance.
+// N = 2^NB <= 16, K <= 128.  A rows are K-contiguous (K-major operands).
 template <int NB>
 __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d) {
     constexpr int N = 1 << NB;
-    __shared__ int8_t s_pos[4][40];
-    __shared__ int64_t s_offAk[64];
-    __shared__ int64_t s_offB[64];
-    __shared__ int64_t s_mlo[ROW_THREADS];
-    __shared__ float2 s_B[64];
-    __shared__ int64_t s_hi;
-    __shared__ int64_t s_ia, s_ib;
-    __shared__ float s_sa;
+    __shared__ int8_t s_pAm[40], s_pCm[40];
+    __shared__ int64_t s_offBn[16], s_offCn[16];
+    __shared__ int64_t s_mloA[ROW_THREADS], s_mloC[ROW_THREADS];
+    __shared__ float2 s_B[256];
+    __shared__ int64_t s_hiA, s_hiC, s_ia, s_ib;
+    __shared__ int s_ea, s_eb;
     const int tid = threadIdx.x;
     const int K = 1 << d.kb;
     const int mb = d.mb;
     const int64_t M = int64_t(1) << mb;
+    const int64_t total = d.nInst << mb;
     if (tid < 40) {
-        s_pos[0][tid] = d.pAm[tid];
-        s_pos[1][tid] = tid < 24 ? d.pAk[tid] : 0;
-        s_pos[2][tid] = tid < 24 ? d.pBk[tid] : 0;
-        s_pos[3][tid] = tid < 24 ? d.pBn[tid] : 0;
+        s_pAm[tid] = d.pAm[tid];
+        s_pCm[tid] = d.pCm[tid];
+    }
+    if (tid < N) {
+        s_offBn[tid] = dep(tid, d.pBn, NB);
+        s_offCn[tid] = dep(tid, d.pCn, NB);
     }
     __syncthreads();
-    if (tid < K) s_offAk[tid] = dep(tid, s_pos[1], d.kb);
-    if (tid < K * N) {
-        const int k = tid >> NB, n = tid & (N - 1);
-        s_offB[tid] = dep(k, s_pos[2], d.kb) + dep(n, s_pos[3], NB);
-    }
     const int lob = mb < 8 ? mb : 8;
-    s_mlo[tid] = dep(tid & ((1 << lob) - 1), s_pos[0], lob);
+    const int lo = tid & ((1 << lob) - 1);
+    s_mloA[tid] = dep(lo, s_pAm, lob);
+    s_mloC[tid] = dep(lo, s_pCm, lob);
     const int64_t gid0 = int64_t(blockIdx.x) * ROW_THREADS;
-    const bool uniform = M >= ROW_THREADS;  // whole block inside one instance
-    if (uniform && tid == 0 && gid0 < (d.nInst << mb)) {
+    const bool uniform = M >= ROW_THREADS;  // the whole block inside one instance
+    if (uniform && tid == 0 && gid0 < total) {
         const int64_t i = gid0 >> mb;
         const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
         s_ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
         s_ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
-        s_hi = mb > 8 ? dep((gid0 & (M - 1)) >> 8, s_pos[0] + 8, mb - 8) : 0;
+        const int64_t mh = (gid0 & (M - 1)) >> 8;
+        s_hiA = mb > 8 ? dep(mh, s_pAm + 8, mb - 8) : 0;
+        s_hiC = mb > 8 ? dep(mh, s_pCm + 8, mb - 8) : 0;
+        s_ea = d.mxA ? exp_of(d.mxA[s_ia]) : 0;
+        s_eb = d.mxB ? exp_of(d.mxB[s_ib]) : 0;
     }
     __syncthreads();
-    if (uniform && gid0 < (d.nInst << mb)) {
-        if (tid < K * N) {
-            const float sb = pow2f(-(d.mxB ? exp_of(d.mxB[s_ib]) : 0));
-            const float2 b = d.B[s_ib * d.sB + s_offB[tid]];
-            s_B[tid] = make_float2(b.x * sb, b.y * sb);
+    if (uniform && gid0 < total) {
+        for (int e = tid; e < K * N; e += ROW_THREADS) {
+            const int k = e >> NB, n = e & (N - 1);
+            s_B[e] = d.B[s_ib * d.sB + k + s_offBn[n]];
         }
-        if (tid == 0) s_sa = pow2f(-(d.mxA ? exp_of(d.mxA[s_ia]) : 0));
         __syncthreads();
     }
     const int64_t gid = gid0 + tid;
-    if (gid >= (d.nInst << mb)) return;
+    if (gid >= total) return;
     const int64_t i = gid >> mb;
     const int64_t m = gid & (M - 1);
-    int64_t ia, ib, offm;
-    float sa;
-    int ea = 0, eb = 0;
+    int64_t ia, ib, offA, offC;
+    int ea, eb;
     if (uniform) {
         ia = s_ia;
         ib = s_ib;
-        offm = s_hi + s_mlo[tid];
-        sa = s_sa;
+        offA = s_hiA + s_mloA[tid];
+        offC = s_hiC + s_mloC[tid];
+        ea = s_ea;
+        eb = s_eb;
     } else {
         const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
         ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
         ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
-        offm = s_mlo[m & 255];
+        offA = s_mloA[m & 255];
+        offC = s_mloC[m & 255];
         ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
-        sa = pow2f(-ea);
+        eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
     }
-    const float2 *A = d.A + ia * d.sA + offm;
+    const float2 *A = d.A + ia * d.sA + offA;
     float2 acc[N];
 #pragma unroll
     for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
     if (uniform) {
         for (int k = 0; k < K; ++k) {
-            float2 a = __ldg(A + s_offAk[k]);
-            a.x *= sa;
-            a.y *= sa;
+            const float2 a = __ldg(A + k);
 #pragma unroll
             for (int n = 0; n < N; ++n) cfma(acc[n], a, s_B[k * N + n]);
         }
     } else {
-        eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
-        const float sb = pow2f(-eb);
         const float2 *B = d.B + ib * d.sB;
         for (int k = 0; k < K; ++k) {
-            float2 a = __ldg(A + s_offAk[k]);
-            a.x *= sa;
-            a.y *= sa;
+            const float2 a = __ldg(A + k);
 #pragma unroll
-            for (int n = 0; n < N; ++n) {
-                float2 b = __ldg(B + s_offB[k * N + n]);
-                b.x *= sb;
-                b.y *= sb;
-                cfma(acc[n], a, b);
-            }
+            for (int n = 0; n < N; ++n) cfma(acc[n], a, __ldg(B + k + s_offBn[n]));
         }
     }
-    float2 *C = d.C + i * d.sC + m * N;
+    const float sc = pow2f(-(ea + eb));
+    float2 *C = d.C + i * d.sC + offC;
     uint32_t mx = 0;
-    if constexpr (N >= 2) {
 #pragma unroll
-        for (int n = 0; n < N; n += 2) {
-            reinterpret_cast<float4 *>(C)[n / 2] = make_float4(acc[n].x, acc[n].y, acc[n + 1].x, acc[n + 1].y);
-            mx = max(mx, max(absmax_bits(acc[n]), absmax_bits(acc[n + 1])));
-        }
-    } else {
-        C[0] = acc[0];
-        mx = absmax_bits(acc[0]);
+    for (int n = 0; n < N; ++n) {
+        const float2 v = make_float2(acc[n].x * sc, acc[n].y * sc);
+        C[s_offCn[n]] = v;
+        mx = max(mx, absmax_bits(v));
     }
-    if (m == 0) {
-        if (uniform) {
-            ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
-            eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
-        }
-        d.EC[i] = d.EA[ia] + ea + d.EB[ib] + eb;
-    }
+    if (m == 0) d.EC[i] = d.EA[ia] + ea + d.EB[ib] + eb;
     if (d.mxC) {
         if (M >= 32) {
 #pragma unroll
@@ -201,116 +185,129 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d) {
     }
 }
 
-// Tiled FP32 complex GEMM with gathered operands: tile 64 (m) x 32 (n) x 8 (k),
-// 256 threads, 4 x 2 outputs per thread.
-constexpr int GBM = 64, GBN = 32, GBK = 8;
+// Grouped SIMT complex GEMM, FP32 FMA.  One CTA: BM rows of the group's A
+// instance times BN columns of the group's concatenated B instances (column
+// c -> instance gfirst[g] + c / N, column n = c % N), K in chunks of BK.
+// 256 threads, 8 x 4 outputs each (rows tm + 16 x, columns 4 tn + y).
+constexpr int GBM = 128, GBN = 64, GBK = 16;
 
-__global__ void __launch_bounds__(256) k_step_gemm_simt(const StepDesc d) {
-    __shared__ int8_t s_pos[4][40];
-    __shared__ int64_t s_offAm[GBM];
-    __shared__ int64_t s_offBn[GBN];
-    __shared__ float2 s_A[GBK][GBM + 1];
-    __shared__ float2 s_B[GBK][GBN + 1];
-    __shared__ int64_t s_ia, s_ib;
-    __shared__ float s_sa, s_sb;
-    __shared__ int s_ea, s_eb;
+__global__ void __launch_bounds__(256) k_step_gemm_simt(const StepDesc d, int ctiles, int mtiles) {
+    __shared__ int8_t s_pAm[40], s_pCm[40];
+    __shared__ int64_t s_offA[GBM], s_offC[GBM];
+    __shared__ int64_t s_bbase[GBN], s_cbase[GBN];
+    __shared__ int32_t s_eb[GBN];
+    __shared__ uint32_t s_mx[GBN];
+    __shared__ float2 s_A[GBK][GBM + 2];
+    __shared__ float2 s_B[GBK][GBN + 2];
+    __shared__ int64_t s_ia;
+    __shared__ int s_ea;
     const int tid = threadIdx.x;
-    const int64_t M = int64_t(1) << d.mb;
+    const int64_t bid = blockIdx.x;
+    const int mt = int(bid % mtiles);
+    const int64_t rest = bid / mtiles;
+    const int ct = int(rest % ctiles);
+    const int64_t g = rest / ctiles;
+    const int64_t i0 = d.gfirst[g];
+    const int64_t icount = d.gfirst[g + 1] - i0;
     const int N = 1 << d.nb;
-    const int64_t K = int64_t(1) << d.kb;
-    const int64_t tiles_m = (M + GBM - 1) / GBM;
-    const int64_t tiles_n = (N + GBN - 1) / GBN;
-    const int64_t per_inst = tiles_m * tiles_n;
-    const int64_t t = blockIdx.x;
-    const int64_t i = t / per_inst;
-    const int64_t r = t - i * per_inst;
-    const int64_t m0 = (r / tiles_n) * GBM;
-    const int64_t n0 = (r % tiles_n) * GBN;
+    const int64_t M = int64_t(1) << d.mb;
+    const int K = 1 << d.kb;
+    const int64_t cols = icount * N;
+    const int64_t c0 = int64_t(ct) * GBN;
+    if (c0 >= cols) return;  // uniform across the block
+    const int64_t m0 = int64_t(mt) * GBM;
     if (tid < 40) {
-        s_pos[0][tid] = d.pAm[tid];
-        s_pos[1][tid] = tid < 24 ? d.pAk[tid] : 0;
-        s_pos[2][tid] = tid < 24 ? d.pBk[tid] : 0;
-        s_pos[3][tid] = tid < 24 ? d.pBn[tid] : 0;
+        s_pAm[tid] = d.pAm[tid];
+        s_pCm[tid] = d.pCm[tid];
     }
     if (tid == 0) {
-        const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
+        const int64_t sig = i0 / d.nOut, beta = i0 - sig * d.nOut;
         s_ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
-        s_ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
         s_ea = d.mxA ? exp_of(d.mxA[s_ia]) : 0;
-        s_eb = d.mxB ? exp_of(d.mxB[s_ib]) : 0;
-        s_sa = pow2f(-s_ea);
-        s_sb = pow2f(-s_eb);
     }
     __syncthreads();
-    if (tid < GBM) s_offAm[tid] = (m0 + tid < M) ? dep(m0 + tid, s_pos[0], d.mb) : 0;
-    else if (tid < GBM + GBN) {
+    if (tid < GBM) {
+        const int64_t m = m0 + tid;
+        s_offA[tid] = m < M ? dep(m, s_pAm, d.mb) : 0;
+        s_offC[tid] = m < M ? dep(m, s_pCm, d.mb) : 0;
+    } else if (tid < GBM + GBN) {
         const int c = tid - GBM;
-        s_offBn[c] = (n0 + c < N) ? dep(n0 + c, s_pos[3], d.nb) : 0;
+        const int64_t gc = c0 + c;
+        s_mx[c] = 0;
+        if (gc < cols) {
+            const int64_t inst = i0 + gc / N;
+            const int n = int(gc % N);
+            const int64_t sig = inst / d.nOut, beta = inst - sig * d.nOut;
+            const int64_t ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
+            s_bbase[c] = ib * d.sB + dep(n, d.pBn, d.nb);
+            s_cbase[c] = inst * d.sC + dep(n, d.pCn, d.nb);
+            const int eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
+            s_eb[c] = eb;
+            if (n == 0 && mt == 0) d.EC[inst] = d.EA[s_ia] + s_ea + d.EB[ib] + eb;
+        } else {
+            s_bbase[c] = -1;
+            s_cbase[c] = -1;
+            s_eb[c] = 0;
+        }
     }
     __syncthreads();
     const float2 *A = d.A + s_ia * d.sA;
-    const float2 *B = d.B + s_ib * d.sB;
-    const float sa = s_sa, sb = s_sb;
-    const int tm = (tid % 16) * 4;  // 4 rows
-    const int tn = (tid / 16) * 2;  // 2 cols
-    float2 acc[4][2];
+    const int tm = tid & 15, tn = tid >> 4;
+    float2 acc[8][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 2; ++b) acc[a][b] = make_float2(0.f, 0.f);
-    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
-        // A tile: 8 x 64 entries, 2 per thread
-        for (int e = tid; e < GBK * GBM; e += 256) {
-            const int kk = e / GBM, mm = e % GBM;
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = make_float2(0.f, 0.f);
+    const int bk = K < GBK ? K : GBK;
+    for (int k0 = 0; k0 < K; k0 += bk) {
+        for (int e = tid; e < bk * GBM; e += 256) {
+            const int kk = e % bk, r = e / bk;
             float2 v = make_float2(0.f, 0.f);
-            if (k0 + kk < K && m0 + mm < M) {
-                v = __ldg(A + s_offAm[mm] + dep(k0 + kk, s_pos[1], d.kb));
-                v.x *= sa;
-                v.y *= sa;
-            }
-            s_A[kk][mm] = v;
+            if (m0 + r < M) v = __ldg(A + s_offA[r] + k0 + kk);
+            s_A[kk][r] = v;
         }
-        for (int e = tid; e < GBK * GBN; e += 256) {
-            const int kk = e / GBN, nn = e % GBN;
+        for (int e = tid; e < bk * GBN; e += 256) {
+            const int kk = e % bk, c = e / bk;
             float2 v = make_float2(0.f, 0.f);
-            if (k0 + kk < K && n0 + nn < N) {
-                v = __ldg(B + dep(k0 + kk, s_pos[2], d.kb) + s_offBn[nn]);
-                v.x *= sb;
-                v.y *= sb;
-            }
-            s_B[kk][nn] = v;
+            if (s_bbase[c] >= 0) v = __ldg(d.B + s_bbase[c] + k0 + kk);
+            s_B[kk][c] = v;
         }
         __syncthreads();
+        for (int kk = 0; kk < bk; ++kk) {
+            float2 a[8], b[4];
 #pragma unroll
-        for (int kk = 0; kk < GBK; ++kk) {
-            float2 a[4], b[2];
+            for (int x = 0; x < 8; ++x) a[x] = s_A[kk][tm + 16 * x];
 #pragma unroll
-            for (int x = 0; x < 4; ++x) a[x] = s_A[kk][tm + x];
+            for (int y = 0; y < 4; ++y) b[y] = s_B[kk][4 * tn + y];
 #pragma unroll
-            for (int y = 0; y < 2; ++y) b[y] = s_B[kk][tn + y];
+            for (int x = 0; x < 8; ++x)
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-                for (int y = 0; y < 2; ++y) cfma(acc[x][y], a[x], b[y]);
+                for (int y = 0; y < 4; ++y) cfma(acc[x][y], a[x], b[y]);
         }
         __syncthreads();
     }
-    uint32_t mx = 0;
-    float2 *C = d.C + i * d.sC;
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
+    for (int y = 0; y < 4; ++y) {
+        const int c = 4 * tn + y;
+        if (s_cbase[c] < 0) continue;
+        const float sc = pow2f(-(s_ea + s_eb[c]));
+        uint32_t mx = 0;
 #pragma unroll
-        for (int y = 0; y < 2; ++y) {
-            const int64_t m = m0 + tm + x, n = n0 + tn + y;
-            if (m < M && n < N) {
-                C[m * N + n] = acc[x][y];
-                mx = max(mx, absmax_bits(acc[x][y]));
-            }
+        for (int x = 0; x < 8; ++x) {
+            const int r = tm + 16 * x;
+            if (m0 + r >= M) continue;
+            const float2 v = make_float2(acc[x][y].x * sc, acc[x][y].y * sc);
+            d.C[s_cbase[c] + s_offC[r]] = v;
+            mx = max(mx, absmax_bits(v));
         }
-    if (m0 == 0 && n0 == 0 && tid == 0) d.EC[i] = d.EA[s_ia] + s_ea + d.EB[s_ib] + s_eb;
+        if (d.mxC) atomicMax(&s_mx[c], mx);
+    }
     if (d.mxC) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((tid & 31) == 0) record_max(d.mxC + i, mx);
+        __syncthreads();
+        if (tid < GBN && s_cbase[tid] >= 0) {
+            const int64_t inst = i0 + (c0 + tid) / N;
+            record_max(d.mxC + inst, s_mx[tid]);
+        }
     }
 }
 
@@ -373,7 +370,7 @@ cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *hi
 }
 
 cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
-    if (d.kb + d.nb > 6 || d.nb > 4 || d.mb > 40) return cudaErrorInvalidValue;
+    if (d.kb + d.nb > 8 || d.nb > 4 || d.mb > 40) return cudaErrorInvalidValue;
     const int64_t rows = d.nInst << d.mb;
     const int64_t blocks = (rows + ROW_THREADS - 1) / ROW_THREADS;
     if (blocks <= 0) return cudaSuccess;
@@ -392,10 +389,12 @@ cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
 cudaError_t launch_step_gemm_simt(const StepDesc &d, cudaStream_t s) {
     const int64_t M = int64_t(1) << d.mb;
     const int64_t N = int64_t(1) << d.nb;
-    const int64_t tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * d.nInst;
-    if (tiles <= 0) return cudaSuccess;
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_step_gemm_simt<<<dim3((unsigned)tiles), 256, 0, s>>>(d);
+    const int64_t ctiles = (int64_t(d.max_group) * N + GBN - 1) / GBN;
+    const int64_t mtiles = (M + GBM - 1) / GBM;
+    const int64_t blocks = d.n_groups * ctiles * mtiles;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL || ctiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_step_gemm_simt<<<dim3((unsigned)blocks), 256, 0, s>>>(d, (int)ctiles, (int)mtiles);
     return cudaGetLastError();
 }
 

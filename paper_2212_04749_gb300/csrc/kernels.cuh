@@ -10,9 +10,12 @@ namespace tnk {
 // One pairwise contraction step, passed by value to every step kernel.
 //   C[i](m, n) = sum_k  A[a(i)](m, k) * B[b(i)](k, n)       (complex)
 // Instance i = sigma * nOut + beta;  a(i) = sigA[sigma] * nOutA + outA[beta],
-// b(i) likewise.  Entry (m, k) of an A instance sits at element offset
-// dep(m, pAm) + dep(k, pAk), where dep scatters the bits of its first
-// argument to the listed bit positions.  C is row-major: C[i][m * N + n].
+// b(i) likewise.  Both operands are K-major: entry (m, k) of an A instance
+// sits at element offset k + dep(m, pAm), entry (k, n) of a B instance at
+// k + dep(n, pBn), where dep scatters the bits of its first argument to the
+// listed bit positions (all >= kb).  C(m, n) of instance i sits at
+// i * sC + dep(m, pCm) + dep(n, pCn).  Consecutive output instances
+// [gfirst[g], gfirst[g+1]) read the same A instance (group g).
 struct StepDesc {
     const float2 *A;
     const float2 *B;
@@ -28,11 +31,13 @@ struct StepDesc {
     const uint32_t *mxA, *mxB;    // max-|component| bits of the operands (null: no rescale)
     uint32_t *mxC;                // max-|component| bits of C (null: not tracked)
     int32_t mb, kb, nb;
-    int32_t pad1;
+    int32_t max_group;            // largest group (instances)
+    const int64_t *gfirst;        // [n_groups + 1]
+    int64_t n_groups;
     int8_t pAm[40];
-    int8_t pAk[24];
-    int8_t pBk[24];
     int8_t pBn[24];
+    int8_t pCm[40];
+    int8_t pCn[24];
 };
 
 struct FillJobD {

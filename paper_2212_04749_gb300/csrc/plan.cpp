@@ -198,6 +198,8 @@ struct Builder {
     int T = 0, NN = 0, m = 0;
     std::vector<std::vector<int32_t>> oi;  // node -> per distinct bitstring out-instance
     std::vector<int> slice_of;             // bond edge -> internal slice index (-1: not sliced)
+    bool bad_offsets = false;              // set by layout_workspace's self-check
+    std::vector<std::vector<int>> low_bits; // per node: bonds its consumer contracts (edge-id order)
 
     bool fail(int c, const std::string &msg) {
         code = c;
@@ -207,8 +209,9 @@ struct Builder {
 
     // Reuse-instance DAG over the distinct bitstrings (SM Sec. III): the
     // out-instances of a node are the distinct projections of the
-    // bitstrings onto its output qubits.  Ordered by (left, right) child
-    // instance so that instances sharing a child instance are adjacent.
+    // bitstrings onto its output qubits, ordered by (A-child instance,
+    // B-child instance) so that instances sharing their A operand are
+    // adjacent (one wide GEMM per shared A).
     void out_instances() {
         const int64_t ku = P.k_unique;
         oi.assign(NN, {});
@@ -232,7 +235,9 @@ struct Builder {
         }
         for (int v = T; v < NN; ++v) {
             Node &nd = P.nodes[v];
-            const int a = nd.left, b = nd.right;
+            // major key: the operand the step reads as A (the larger one)
+            const bool left_big = P.nodes[nd.left].rank >= P.nodes[nd.right].rank;
+            const int a = left_big ? nd.left : nd.right, b = left_big ? nd.right : nd.left;
             const int64_t nb = P.nodes[b].n_out;
             std::vector<int64_t> key(ku);
             for (int64_t u = 0; u < ku; ++u) key[u] = int64_t(oi[a][u]) * nb + oi[b][u];
@@ -241,11 +246,12 @@ struct Builder {
             vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
             if (vals.empty()) vals.push_back(0);
             nd.n_out = (int)vals.size();
-            nd.outL.resize(vals.size());
-            nd.outR.resize(vals.size());
+            std::vector<int32_t> &oa = left_big ? nd.outL : nd.outR, &ob = left_big ? nd.outR : nd.outL;
+            oa.resize(vals.size());
+            ob.resize(vals.size());
             for (size_t i = 0; i < vals.size(); ++i) {
-                nd.outL[i] = int32_t(vals[i] / nb);
-                nd.outR[i] = int32_t(vals[i] % nb);
+                oa[i] = int32_t(vals[i] / nb);
+                ob[i] = int32_t(vals[i] % nb);
             }
             oi[v].resize(ku);
             for (int64_t u = 0; u < ku; ++u)
@@ -317,32 +323,51 @@ struct Builder {
             P.n_static_steps += nd.level == 64;
             P.steps.push_back(st);
         }
-        // layouts and bit positions
+        // Layouts.  Every node is stored with the bonds its consumer contracts
+        // (L = its open bonds shared with its sibling, in edge-id order) as
+        // the lowest address bits, so that both operands of every step are
+        // K-major with the same k order; the producing step's epilogue writes
+        // that layout directly.  Leaves got theirs in make_plan.
         P.max_rank = 0;
         for (int v = 0; v < T; ++v) P.max_rank = std::max(P.max_rank, P.nodes[v].rank);
         for (Step &st : P.steps) {
             Node &nd = P.nodes[st.node];
             const Node &A = P.nodes[st.a], &B = P.nodes[st.b];
-            std::vector<int> fa, fb, kk;
+            auto in = [](const std::vector<int> &v, int e) { return std::find(v.begin(), v.end(), e) != v.end(); };
+            const std::vector<int> &Lv = low_bits[st.node];
+            std::vector<int> kk, fa_l, fa_r, fb_l, fb_r;
             for (int e : A.layout) {
-                if (std::find(B.layout.begin(), B.layout.end(), e) != B.layout.end()) kk.push_back(e);
-                else fa.push_back(e);
+                if (in(B.layout, e)) kk.push_back(e);
+                else if (in(Lv, e)) fa_l.push_back(e);
+                else fa_r.push_back(e);
             }
-            for (int e : B.layout)
-                if (std::find(A.layout.begin(), A.layout.end(), e) == A.layout.end()) fb.push_back(e);
+            for (int e : B.layout) {
+                if (in(A.layout, e)) continue;
+                if (in(Lv, e)) fb_l.push_back(e);
+                else fb_r.push_back(e);
+            }
+            std::sort(fa_l.begin(), fa_l.end());
+            std::sort(fb_l.begin(), fb_l.end());
+            std::vector<int> mord(fa_l), nord(fb_l);
+            mord.insert(mord.end(), fa_r.begin(), fa_r.end());
+            nord.insert(nord.end(), fb_r.begin(), fb_r.end());
+            nd.layout = Lv;
+            nd.layout.insert(nd.layout.end(), fb_r.begin(), fb_r.end());
+            nd.layout.insert(nd.layout.end(), fa_r.begin(), fa_r.end());
             auto pos = [](const std::vector<int> &lay, int e) {
                 return int8_t(std::find(lay.begin(), lay.end(), e) - lay.begin());
             };
-            st.mb = (int)fa.size();
+            st.mb = (int)mord.size();
             st.kb = (int)kk.size();
-            st.nb = (int)fb.size();
-            st.pAm.clear(); st.pAk.clear(); st.pBk.clear(); st.pBn.clear();
-            for (int e : fa) st.pAm.push_back(pos(A.layout, e));
+            st.nb = (int)nord.size();
+            st.pAm.clear(); st.pAk.clear(); st.pBk.clear(); st.pBn.clear(); st.pCm.clear(); st.pCn.clear();
+            for (int e : mord) { st.pAm.push_back(pos(A.layout, e)); st.pCm.push_back(pos(nd.layout, e)); }
             for (int e : kk) { st.pAk.push_back(pos(A.layout, e)); st.pBk.push_back(pos(B.layout, e)); }
-            for (int e : fb) st.pBn.push_back(pos(B.layout, e));
-            nd.layout = fb;
-            nd.layout.insert(nd.layout.end(), fa.begin(), fa.end());
+            for (int e : nord) { st.pBn.push_back(pos(B.layout, e)); st.pCn.push_back(pos(nd.layout, e)); }
             nd.rank = (int)nd.layout.size();
+            for (int j = 0; j < st.kb; ++j)
+                if (st.pAk[j] != j || st.pBk[j] != j)
+                    return fail(TN_EUNSUPPORTED, "internal error: operand not K-major");
             P.max_rank = std::max(P.max_rank, nd.rank);
             if (nd.rank > 40 || st.mb > 40 || st.kb > 24 || st.nb > 24)
                 return fail(TN_EUNSUPPORTED, "intermediate rank above 40 (or contracted/free bits above 24)");
@@ -352,7 +377,25 @@ struct Builder {
                               double(B.n_inst) * std::ldexp(1.0, B.rank) +
                               double(nd.n_inst) * std::ldexp(1.0, nd.rank));
             st.runs = st.level >= h ? 1.0 : std::ldexp(1.0, h - st.level);
-            st.kernel = (st.kb + st.nb <= 6 && st.nb <= 4) ? 0 : 1;
+            // groups: runs of consecutive output instances reading one A instance
+            const bool a_left = st.a == nd.left;
+            const std::vector<int32_t> &sgA = a_left ? nd.sigL : nd.sigR;
+            const std::vector<int32_t> &otA = a_left ? nd.outL : nd.outR;
+            st.group_first.clear();
+            int64_t prev = -1;
+            for (int64_t i = 0; i < nd.n_inst; ++i) {
+                const int64_t sg = i / nd.n_out, bt = i % nd.n_out;
+                const int64_t ai = int64_t(sgA[sg]) * A.n_out + otA[bt];
+                if (ai != prev) st.group_first.push_back(i);
+                prev = ai;
+            }
+            st.group_first.push_back(nd.n_inst);
+            st.n_groups = (int64_t)st.group_first.size() - 1;
+            // kernel family: the per-row kernel takes a small B (N <= 16,
+            // K*N <= 256) when few instances share an A (under 16 columns per
+            // A on average); everything else is a GEMM over instance groups
+            const double cols_per_a = std::ldexp(double(nd.n_inst) / double(st.n_groups), st.nb);
+            st.kernel = (st.nb <= 4 && st.kb + st.nb <= 8 && cols_per_a < 16.0) ? 0 : 1;
         }
         for (int s = 0; s < (int)P.steps.size(); ++s) {
             P.nodes[P.steps[s].a].last_use = s;
@@ -495,6 +538,16 @@ struct Builder {
                 }
             }
         }
+        // every fill job copies inside its leaf's instance buffer, from inside
+        // the full-leaf region, for every value of the looped sliced legs
+        for (size_t q = 0; q < jobs.size(); ++q) {
+            const FillJob &j = jobs[q];
+            const LeafHigh &hh = highs[j.leaf_high];
+            int64_t hmax = 0;
+            for (int c = 0; c < hh.cnt; ++c) hmax += hh.stride[c];
+            if (j.src < p.off_leaf_full / 8 || j.src + hmax + j.n > p.off_leaf_full / 8 + full_elems)
+                bad_offsets = true;
+        }
         p.n_fill_jobs = (int64_t)jobs.size();
         p.off_fill_jobs = take(int64_t(jobs.size()) * sizeof(FillJob));
         p.off_leaf_high = take(int64_t(highs.size()) * sizeof(LeafHigh));
@@ -509,6 +562,10 @@ struct Builder {
             push_upload(p, p.off_uniq, r);
         }
         p.off_scratch = take(256);
+        for (Step &st : p.steps) {
+            st.off_groups = take(int64_t(st.group_first.size()) * 8);
+            if (emit) push_upload(p, st.off_groups, st.group_first);
+        }
         // transient intermediates: first-fit over one full pass of the steps
         Arena ar;
         ar.base = ar.top = ar.high = off;
@@ -526,7 +583,23 @@ struct Builder {
             }
             p.peak_tensor_bytes = std::max(p.peak_tensor_bytes, bytes);
         }
-        return Arena::align(ar.high);
+        const int64_t total = Arena::align(ar.high);
+        // every node buffer inside the workspace; every job destination inside its leaf
+        for (int v = 0; v < NN; ++v) {
+            const Node &nd = p.nodes[v];
+            if (nd.buf.data < 0 || nd.buf.data + nd.n_inst * (int64_t(8) << nd.rank) > total) bad_offsets = true;
+            if (nd.buf.E < 0 || nd.buf.mx < 0) bad_offsets = true;
+        }
+        for (const FillJob &j : jobs) {
+            bool inside = false;
+            for (int v = 0; v < T && !inside; ++v) {
+                const Node &nd = p.nodes[v];
+                const int64_t b0 = nd.buf.data / 8, b1 = b0 + nd.n_inst * (int64_t(1) << nd.rank);
+                inside = j.dst >= b0 && j.dst + j.n <= b1;
+            }
+            if (!inside) bad_offsets = true;
+        }
+        return total;
     }
 };
 
@@ -629,11 +702,30 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
                        std::back_inserter(nd.slices));
     }
     if ((int)P.nodes[P.root].outs.size() != n) { err = "tree: root does not hold every output leg"; return false; }
+    // bonds each node shares with its sibling (contracted by its consumer)
+    std::vector<std::vector<int>> low_bits(NN);
+    for (int v = T; v < NN; ++v) {
+        const int a = P.nodes[v].left, b = P.nodes[v].right;
+        std::vector<int> kset;
+        std::set_intersection(open[a].begin(), open[a].end(), open[b].begin(), open[b].end(),
+                              std::back_inserter(kset));
+        low_bits[a] = kset;
+        low_bits[b] = kset;
+    }
+    // leaf layouts: the contracted bonds first (edge-id order), then the rest
+    for (int v = 0; v < T; ++v) {
+        Node &nd = P.nodes[v];
+        std::vector<int> lay = low_bits[v];
+        for (int e : nd.layout)
+            if (std::find(lay.begin(), lay.end(), e) == lay.end()) lay.push_back(e);
+        nd.layout = lay;
+    }
 
-    Builder B{P, err, code, 0, 0, 0, {}, {}};
+    Builder B{P, err, code, 0, 0, 0, {}, {}, false, {}};
     B.T = T;
     B.NN = NN;
     B.m = n_sliced;
+    B.low_bits = low_bits;
     B.out_instances();
     // Internal slice order.  The first m_low sliced edges run side by side in
     // one pass; the rest are looped over, bit t - m_low of the batch index,
@@ -718,6 +810,11 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
     for (Node &nd : P.nodes) { nd.buf = NodeBuf(); }
     P.peak_tensor_bytes = 0;
     P.ws_bytes = B.layout_workspace(true);
+    if (B.bad_offsets) {
+        code = TN_EUNSUPPORTED;
+        err = "internal error: workspace layout self-check failed";
+        return false;
+    }
     // costs
     P.flops_exec = P.flops_ma = P.flops_sa = P.bytes_min = 0;
     for (const Step &st : P.steps) {

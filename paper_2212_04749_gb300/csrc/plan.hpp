@@ -91,8 +91,12 @@ struct Step {
     int node = -1, a = -1, b = -1;
     int mb = 0, kb = 0, nb = 0;
     std::vector<int8_t> pAm, pAk, pBk, pBn;  // bit positions in A / B
+    std::vector<int8_t> pCm, pCn;            // positions of the m / n bits in C
     int level = 64;          // recomputed in batch b > first iff level <= ctz(b)
     double runs = 1;         // passes over all 2^h batches
+    int64_t n_groups = 0;    // runs of consecutive output instances sharing an A instance
+    std::vector<int64_t> group_first;  // n_groups + 1 boundaries
+    int64_t off_groups = -1;           // workspace offset of group_first
     int kernel = 0;          // 0 = per-row SIMT, 1 = tiled SIMT GEMM, 2 = tensor-core GEMM
     double flops = 0;        // executed per pass: 8 * n_inst * 2^{mb+kb+nb}
     double bytes = 0;        // A + B reads and C write per pass

@@ -53,7 +53,8 @@ class tn_plan_info(ctypes.Structure):
                 ("max_rank", ctypes.c_int32), ("n_static_steps", ctypes.c_int32),
                 ("flops_ma", ctypes.c_double), ("flops_sa", ctypes.c_double), ("flops_exec", ctypes.c_double),
                 ("bytes_min", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
-                ("peak_tensor_bytes", ctypes.c_int64)]
+                ("peak_tensor_bytes", ctypes.c_int64), ("upload_bytes", ctypes.c_int64),
+                ("launches_per_call", ctypes.c_int64)]
 
 
 class tn_step_info(ctypes.Structure):
@@ -61,7 +62,9 @@ class tn_step_info(ctypes.Structure):
                 ("kb", ctypes.c_int32), ("nb", ctypes.c_int32), ("rank_a", ctypes.c_int32),
                 ("rank_b", ctypes.c_int32), ("level", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("n_inst", ctypes.c_int64), ("n_inst_a", ctypes.c_int64), ("n_inst_b", ctypes.c_int64),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("runs", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("runs", ctypes.c_double),
+                ("a_run_m", ctypes.c_int32), ("a_run_k", ctypes.c_int32), ("b_run_k", ctypes.c_int32),
+                ("b_run_n", ctypes.c_int32), ("n_groups", ctypes.c_int64)]
 
 
 _lib = None
@@ -96,7 +99,7 @@ def load(build_if_missing: bool = False):
         "tn_contract_slices": (ctypes.c_int, [vp, ctypes.c_int, vp, i32, vp, vp]),
         "tn_xeb": (ctypes.c_int, [vp, i64, i32, vp, vp]),
         "tn_plan_profile": (ctypes.c_int, [vp, ctypes.c_int]),
-        "tn_plan_step_times": (ctypes.c_int, [vp, vp, i32]),
+        "tn_plan_step_times": (ctypes.c_int, [vp, vp, vp, i32]),
         "tn_destroy": (None, [vp]),
         "tn_last_error": (ctypes.c_char_p, []),
     }
@@ -238,10 +241,12 @@ class Plan:
         _check(self._lib.tn_plan_profile(self.h, 1 if enable else 0))
 
     def tn_plan_step_times(self):
+        """(ms per step summed over the last call's batches, kernel family per step)."""
         n = self.info["n_steps"]
-        ms = np.zeros(n, np.float64)
-        _check(self._lib.tn_plan_step_times(self.h, ms.ctypes.data, n))
-        return ms
+        ms = np.zeros(max(n, 1), np.float64)
+        kern = np.zeros(max(n, 1), np.int32)
+        _check(self._lib.tn_plan_step_times(self.h, ms.ctypes.data, kern.ctypes.data, n))
+        return ms[:n], kern[:n]
 
 
 def tn_xeb(amps, k, n_qubits, out, stream=None):

@@ -35,10 +35,14 @@ def workload_inputs(name):
 
 
 def input_digest(circ, bits) -> str:
-    q0, q1, layer, m = circ.to_arrays()
+    """Digest of the discrete inputs (gate positions, gate names, bitstrings);
+    the gate entries follow from the names, and leaving the floats out keeps
+    the digest identical across host architectures."""
+    q0, q1, layer, _ = circ.to_arrays()
     h = hashlib.sha256()
-    for a in (q0, q1, layer, np.round(m, 15), np.ascontiguousarray(bits, np.uint8)):
+    for a in (q0, q1, layer, np.ascontiguousarray(bits, np.uint8)):
         h.update(np.ascontiguousarray(a).tobytes())
+    h.update(",".join(g.kind for g in circ.gates).encode())
     return h.hexdigest()
 
 

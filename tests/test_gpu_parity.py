@@ -118,3 +118,19 @@ def test_xeb_kernel_matches_definition():
     tn.tn_xeb(dev, 5000, 14, out)
     torch.cuda.synchronize()
     assert abs(out.item() - xeb.linear_xeb(a, 14)) < 1e-12
+
+
+def test_grid5x6_fp32_matches_stored_state_vector():
+    # 30 qubits, 14 cycles, 4096 bitstrings, 2^10 slices: every amplitude
+    # against the complex128 state vector written by tests/golden/make_golden.py
+    import importlib.util, os
+    spec = importlib.util.spec_from_file_location(
+        "make_golden", os.path.join(os.path.dirname(__file__), "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    digest, ref = mg.read("grid5x6_m14")
+    w = make_workload("grid5x6_m14")
+    assert digest == mg.input_digest(w.circuit, w.bits)
+    got, p = run_plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced)
+    assert p.info["n_sliced"] == 10
+    assert rel_l2(got, ref) <= FP32_TOL
