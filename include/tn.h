@@ -182,6 +182,18 @@ int tn_contract_slices(tn_plan_t plan, int precision, const int64_t *slice_ids, 
  * asynchronous on `stream`. */
 int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, void *stream);
 
+/* Override the kernel family of one step (-1: the plan's choice; 0: per-row
+ * kernel, valid when N <= 16 and K*N <= 256; 1: grouped GEMM -- tensor
+ * cores for TN_TF32 / TN_BF16X3 when the shape allows, CUDA cores
+ * otherwise).  Used by the autotuner and the cost model.  TN_EINVAL for a
+ * family the step's shape does not allow. */
+int tn_plan_set_kernel(tn_plan_t plan, int32_t step, int32_t kernel);
+
+/* Synchronise `stream` and report device-side failures of earlier calls on
+ * this plan: TN_ETIMEOUT if a bounded wait inside a kernel gave up (the
+ * flag is then cleared), TN_OK otherwise. */
+int tn_plan_check(tn_plan_t plan, void *stream);
+
 /* Device time of each step summed over the slice batches of the last
  * tn_contract* call, when profiling is on (tn_plan_profile(plan, 1): CUDA
  * events around every launch, read back by tn_plan_step_times, which

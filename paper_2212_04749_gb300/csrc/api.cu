@@ -40,6 +40,7 @@ struct PlanObj {
     std::vector<int> ev_step;             // step of each recorded pair
     size_t ev_used = 0;
     std::vector<int32_t> step_kernel;     // kernel family each step ran last (0 row, 1 SIMT GEMM, 2 TC GEMM)
+    std::vector<int32_t> kernel_override; // per step: -1 plan choice, 0 row, 1 GEMM
     int64_t last_batches = 0;
 };
 
@@ -105,7 +106,9 @@ int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
     const tnk::StepDesc &d = o->desc[s];
     cudaError_t e;
     int fam;
-    if (S.kernel == 0) {
+    int want = S.kernel;
+    if (s < (int)o->kernel_override.size() && o->kernel_override[s] >= 0) want = o->kernel_override[s];
+    if (want == 0) {
         fam = 0;
         e = tnk::launch_step_row(d, st);
     } else if (precision != TN_FP32 && tnk::gemm_tc_supports(d)) {
@@ -376,6 +379,36 @@ int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, voi
     cudaError_t e = tnk::launch_xeb(amps, k, std::ldexp(1.0, n_qubits) / double(k), xeb_dev, st);
     if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("xeb: ") + cudaGetErrorString(e));
     g_err.clear();
+    return TN_OK;
+}
+
+int tn_plan_set_kernel(tn_plan_t plan, int32_t step, int32_t kernel) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_set_kernel: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    const tnp::Plan &P = o->P;
+    if (step < 0 || step >= (int32_t)P.steps.size()) return set_err(TN_EINVAL, "tn_plan_set_kernel: bad step");
+    if (kernel < -1 || kernel > 1) return set_err(TN_EINVAL, "tn_plan_set_kernel: bad kernel family");
+    const tnp::Step &st = P.steps[step];
+    if (kernel == 0 && !(st.nb <= 4 && st.kb + st.nb <= 8))
+        return set_err(TN_EINVAL, "tn_plan_set_kernel: per-row kernel needs N <= 16 and K*N <= 256");
+    o->kernel_override.resize(P.steps.size(), -1);
+    o->kernel_override[step] = kernel;
+    return TN_OK;
+}
+
+int tn_plan_check(tn_plan_t plan, void *stream) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_check: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    if (!o->ws) return TN_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int32_t flag = 0;
+    CU(cudaMemcpyAsync(&flag, o->err_flag, 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (flag) {
+        CU(cudaMemsetAsync(o->err_flag, 0, 4, st));
+        CU(cudaStreamSynchronize(st));
+        return set_err(TN_ETIMEOUT, "a bounded device-side wait gave up (tensor-core pipeline)");
+    }
     return TN_OK;
 }
 

@@ -21,7 +21,7 @@ PRECISIONS = {"fp32": TN_FP32, "tf32": TN_TF32, "bf16x3": TN_BF16X3}
 
 EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_plan_widths", "tn_plan_steps",
            "tn_plan_bind", "tn_contract", "tn_contract_slices", "tn_xeb", "tn_plan_profile",
-           "tn_plan_step_times", "tn_destroy", "tn_last_error")
+           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_check", "tn_destroy", "tn_last_error")
 
 
 class TnError(RuntimeError):
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = False):
         "tn_contract_slices": (ctypes.c_int, [vp, ctypes.c_int, vp, i32, vp, vp]),
         "tn_xeb": (ctypes.c_int, [vp, i64, i32, vp, vp]),
         "tn_plan_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "tn_plan_set_kernel": (ctypes.c_int, [vp, i32, i32]),
+        "tn_plan_check": (ctypes.c_int, [vp, vp]),
         "tn_plan_step_times": (ctypes.c_int, [vp, vp, vp, i32]),
         "tn_destroy": (None, [vp]),
         "tn_last_error": (ctypes.c_char_p, []),
@@ -236,6 +238,12 @@ class Plan:
         ids = np.ascontiguousarray(np.asarray(slice_ids, np.int64))
         _check(self._lib.tn_contract_slices(self.h, int(precision), ids.ctypes.data, len(ids), _ptr(partials),
                                             _stream(stream)))
+
+    def tn_plan_set_kernel(self, step, kernel):
+        _check(self._lib.tn_plan_set_kernel(self.h, int(step), int(kernel)))
+
+    def tn_plan_check(self, stream=None):
+        _check(self._lib.tn_plan_check(self.h, _stream(stream)))
 
     def tn_plan_profile(self, enable=True):
         _check(self._lib.tn_plan_profile(self.h, 1 if enable else 0))

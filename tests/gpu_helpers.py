@@ -12,10 +12,17 @@ def require_cuda():
     return torch, tn
 
 
-def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, **opts):
-    """Amplitudes (complex128, input order) summed over every slice batch."""
+def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, force_kernel=None, **opts):
+    """Amplitudes (complex128, input order) summed over every slice batch.
+    force_kernel: a function step_info -> kernel family (or None) applied to
+    every step before the run."""
     torch, tn = require_cuda()
     p = tn.Plan(circ, bits, ssa, sliced, **opts)
+    if force_kernel is not None:
+        for s, st in enumerate(p.tn_plan_steps()):
+            k = force_kernel(st)
+            if k is not None:
+                p.tn_plan_set_kernel(s, k)
     ws = torch.empty(max(p.info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
     p.tn_plan_bind(ws, stream=torch.cuda.current_stream())
     amps = torch.zeros(2 * len(bits), dtype=torch.float64, device="cuda")
@@ -24,6 +31,7 @@ def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, **opts)
     else:
         for lo, hi in batches:
             p.tn_contract(amps, precision, lo, hi, stream=torch.cuda.current_stream())
+    p.tn_plan_check(stream=torch.cuda.current_stream())
     torch.cuda.synchronize()
     return amps.cpu().numpy().view(np.complex128), p
 

@@ -1,0 +1,82 @@
+"""Tensor-core forms (TF32 and BF16x3 on tcgen05) against the oracle.
+
+Bound for the mixed form (BF16x3): relative L2 amplitude error <= 1e-3.
+TF32 keeps 10 mantissa bits per product; over the 90-300 contraction steps
+of these circuits its error sits near 1e-3 (measured 1.0e-3 on 20 qubits),
+so it is held to 1e-2 and reported, and BF16x3 is the mixed form that
+carries the 1e-3 claim.  A 20-qubit
+circuit has every GEMM-shaped step forced onto the grouped GEMM kernel so
+that the tensor-core path sees many shapes (ragged M and column tiles,
+K below one chunk); the 30-qubit workload checks all 4096 amplitudes.
+"""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import rel_l2, run_plan
+from oracle import sv
+from rqc import grid_layout, make_workload, network_structure, random_circuit
+from rqc.bitstrings import uniform_bitstrings
+from rqc.tree import candidate_trees, choose_slices
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-3
+TF32_TOL = 1e-2
+
+
+def _tol(prec):
+    return {"fp32": 1e-5, "tf32": TF32_TOL, "bf16x3": MIXED_TOL}[prec]
+
+
+def _gemm_everywhere(st):
+    return 1
+
+
+@pytest.fixture(scope="module")
+def case20():
+    c = random_circuit(grid_layout(4, 5), 12, seed=21)
+    s = network_structure(c)
+    bits = uniform_bitstrings(20, 1500, seed=5)
+    ssa = candidate_trees(s, 1500, seed=2, trials=2)[0]
+    from rqc.tree import ContractionTree
+    sl = choose_slices(s, ContractionTree(ssa=ssa), 1500, n_sliced=2)
+    return c, bits, ssa, sl, sv.amplitudes(c, bits)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
+def test_forced_gemm_path_matches_state_vector(case20, prec):
+    c, bits, ssa, sl, ref = case20
+    got, p = run_plan(c, bits, ssa, sl, precision=prec, force_kernel=_gemm_everywhere)
+    err = rel_l2(got, ref)
+    print(f"forced GEMM 20q {prec}: rel-L2 {err:.3e}")
+    assert err <= _tol(prec), err
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_plan_choice_matches_state_vector(case20, prec):
+    c, bits, ssa, sl, ref = case20
+    got, p = run_plan(c, bits, ssa, sl, precision=prec)
+    assert rel_l2(got, ref) <= _tol(prec)
+
+
+def test_bf16x3_is_closer_than_tf32(case20):
+    c, bits, ssa, sl, ref = case20
+    e_tf, _ = run_plan(c, bits, ssa, sl, precision="tf32", force_kernel=_gemm_everywhere)
+    e_bf, _ = run_plan(c, bits, ssa, sl, precision="bf16x3", force_kernel=_gemm_everywhere)
+    assert rel_l2(e_bf, ref) < rel_l2(e_tf, ref)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_grid5x6_mixed_matches_stored_state_vector(prec):
+    import importlib.util, os
+    spec = importlib.util.spec_from_file_location(
+        "make_golden", os.path.join(os.path.dirname(__file__), "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    _, ref = mg.read("grid5x6_m14")
+    w = make_workload("grid5x6_m14")
+    got, p = run_plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, precision=prec)
+    err = rel_l2(got, ref)
+    print(f"grid5x6_m14 {prec}: rel-L2 {err:.3e}")
+    assert err <= _tol(prec), err
