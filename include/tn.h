@@ -203,6 +203,30 @@ int tn_plan_check(tn_plan_t plan, void *stream);
 int tn_plan_profile(tn_plan_t plan, int enable);
 int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t *kernel, int32_t n);
 
+/* Contraction for callers that cannot allocate device memory.  No
+ * counterpart in the paper.  Some callers cannot call cudaMalloc or take
+ * device memory from an allocator: code embedded in a host application
+ * whose memory pools are owned by another runtime, or a process whose
+ * device memory is fixed before it starts.  For them this entry point runs
+ * the same contraction as tn_plan_bind + tn_contract over every slice batch,
+ * with the workspace in a fixed device array inside the library
+ * (TN_STATIC_SCRATCH_BYTES, 64 MiB, reserved on every device that loads the
+ * library until the process exits).  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   amps: caller-owned device complex128 buffer of k entries, accumulated
+ *         into as in tn_contract.
+ *   Plans whose tn_plan_info.workspace_bytes exceed TN_STATIC_SCRATCH_BYTES
+ *   are rejected with TN_ENOMEM and a message giving both sizes.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call uploads the plan's tables into the array and clears
+ * what must start at zero, because the array keeps the last call's
+ * contents; calls that overlap on the GPU (other streams, other threads)
+ * share the array and race.  A plan's own tn_plan_bind binding is left as it
+ * was. */
+#define TN_STATIC_SCRATCH_BYTES (64ll << 20)
+int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream);
+
 void tn_destroy(tn_plan_t plan);
 
 /* Thread-local message of the last failing call ("" if none). */

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -163,6 +164,28 @@ int run_batches(PlanObj *o, int precision, int64_t b_lo, int64_t b_hi, cudaStrea
     }
     o->last_batches = b_hi - b_lo;
     (void)nst;
+    return TN_OK;
+}
+
+// Fixed device scratch for tn_contract_static.  In host code this name is a
+// host-side stand-in, not a device address: the address comes from
+// cudaGetSymbolAddress, looked up once per device.
+__device__ __align__(256) unsigned char g_static_scratch[TN_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+std::vector<void *> g_static_addr;  // per device ordinal; null until looked up
+
+int static_scratch_address(void **out) {
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if ((int)g_static_addr.size() <= dev) g_static_addr.resize(dev + 1, nullptr);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        CU(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
     return TN_OK;
 }
 
@@ -380,6 +403,32 @@ int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, voi
     if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("xeb: ") + cudaGetErrorString(e));
     g_err.clear();
     return TN_OK;
+}
+
+int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream) {
+    if (!plan) return set_err(TN_EINVAL, "tn_contract_static: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    if (o->P.ws_bytes > (int64_t)TN_STATIC_SCRATCH_BYTES)
+        return set_err(TN_ENOMEM, "tn_contract_static: plan needs " + std::to_string(o->P.ws_bytes) +
+                                      " workspace bytes; the fixed scratch holds " +
+                                      std::to_string((long long)TN_STATIC_SCRATCH_BYTES));
+    void *scratch = nullptr;
+    if (int rc = static_scratch_address(&scratch)) return rc;
+    // bind to the fixed scratch, run every batch, restore the caller's binding
+    uint8_t *prev_ws = o->ws;
+    const size_t prev_bytes = o->ws_bytes;
+    int32_t *prev_flag = o->err_flag;
+    int rc = tn_plan_bind(plan, scratch, (size_t)TN_STATIC_SCRATCH_BYTES, stream);
+    if (rc == TN_OK) rc = tn_contract(plan, precision, 0, o->P.n_batches, amps, stream);
+    if (rc == TN_OK) rc = tn_plan_check(plan, stream);
+    const std::string msg = g_err;
+    o->ws = prev_ws;
+    o->ws_bytes = prev_bytes;
+    o->err_flag = prev_flag;
+    if (prev_ws) build_descs(o);
+    else o->desc.clear();
+    g_err = msg;
+    return rc;
 }
 
 int tn_plan_set_kernel(tn_plan_t plan, int32_t step, int32_t kernel) {

@@ -21,7 +21,9 @@ PRECISIONS = {"fp32": TN_FP32, "tf32": TN_TF32, "bf16x3": TN_BF16X3}
 
 EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_plan_widths", "tn_plan_steps",
            "tn_plan_bind", "tn_contract", "tn_contract_slices", "tn_xeb", "tn_plan_profile",
-           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_check", "tn_destroy", "tn_last_error")
+           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_check", "tn_contract_static", "tn_destroy",
+           "tn_last_error")
+TN_STATIC_SCRATCH_BYTES = 64 << 20
 
 
 class TnError(RuntimeError):
@@ -101,6 +103,7 @@ def load(build_if_missing: bool = False):
         "tn_plan_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "tn_plan_set_kernel": (ctypes.c_int, [vp, i32, i32]),
         "tn_plan_check": (ctypes.c_int, [vp, vp]),
+        "tn_contract_static": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "tn_plan_step_times": (ctypes.c_int, [vp, vp, vp, i32]),
         "tn_destroy": (None, [vp]),
         "tn_last_error": (ctypes.c_char_p, []),
@@ -238,6 +241,14 @@ class Plan:
         ids = np.ascontiguousarray(np.asarray(slice_ids, np.int64))
         _check(self._lib.tn_contract_slices(self.h, int(precision), ids.ctypes.data, len(ids), _ptr(partials),
                                             _stream(stream)))
+
+    def tn_contract_static(self, amps, precision=TN_FP32, stream=None):
+        """Contract every slice batch into ``amps`` using the library's fixed
+        device scratch instead of a bound workspace (no device allocation;
+        plans above TN_STATIC_SCRATCH_BYTES are rejected)."""
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        _check(self._lib.tn_contract_static(self.h, int(precision), _ptr(amps), _stream(stream)))
 
     def tn_plan_set_kernel(self, step, kernel):
         _check(self._lib.tn_plan_set_kernel(self.h, int(step), int(kernel)))
