@@ -286,6 +286,15 @@ def run_ours(args, world, rank, local):
         fam_bytes[f] = fam_bytes.get(f, 0.0) + st["bytes"] * st["runs"]
         fam_flops[f] = fam_flops.get(f, 0.0) + st["flops"] * st["runs"]
         fam_launch[f] = fam_launch.get(f, 0) + int(st["runs"])
+    if args.dump_steps and rank == 0:
+        rows = []
+        for s_, st in enumerate(steps):
+            r = dict(st)
+            r["ms_per_call"] = float(step_ms[s_] / args.steps)
+            r["family"] = int(kernels[s_]) if kernels is not None else -1
+            rows.append(r)
+        with open(args.dump_steps, "w") as f:
+            json.dump({"precision": args.precision, "workload": args.workload, "steps": rows}, f)
     dom = max(fam_ms, key=fam_ms.get)
     sec = fam_ms[dom] / 1000.0
     if dom == 0:
@@ -376,6 +385,7 @@ def main():
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--dump-steps", default=None, help="write per-step features and times (JSON) here")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":

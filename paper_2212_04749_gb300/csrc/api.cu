@@ -95,6 +95,8 @@ void build_descs(PlanObj *o) {
         }
         d.gfirst = at<const int64_t>(o, st.off_groups);
         d.n_groups = st.n_groups;
+        d.ctab = at<const int64_t>(o, st.off_col_tiles);
+        d.n_ctab = (int64_t)st.col_tiles.size();
         int64_t mg = 0;
         for (int64_t g = 0; g < st.n_groups; ++g) mg = std::max(mg, st.group_first[g + 1] - st.group_first[g]);
         d.max_group = (int32_t)mg;

@@ -41,7 +41,6 @@ constexpr int TBN = 64;       // complex columns per tile
 constexpr int TBNR = 2 * TBN; // real columns (MMA N)
 constexpr int TBK = 16;       // complex k per chunk
 constexpr int TBKR = 2 * TBK; // real k per chunk
-constexpr int TMEM_COLS = 128;
 constexpr unsigned long long WAIT_NS = 200000000ull;  // 200 ms per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -164,248 +163,392 @@ __device__ __forceinline__ uint32_t kmaj_off(int row, int kr, int es) {
     return uint32_t((kb >> 4) * (TBM * 16) + (row >> 3) * 128 + (row & 7) * 16 + (kb & 15));
 }
 
-struct __align__(16) Smem {
-    // stage s: tf32 uses a[s] (16 KB) and b[s]; bf16 uses the halves
-    // a[s] = {hi (8 KB), lo (8 KB)}, b[s] likewise
-    uint8_t a[2][TBM * TBKR * 4];
-    uint8_t b[2][TBNR * TBKR * 4];
-    uint64_t bar[2];
-    uint32_t tmem_base;
-    int64_t offA[TBM];
-    int64_t offC[TBM];
-    int64_t bbase[TBN];
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait(int pending) {
+    switch (pending) {
+        case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    }
+}
+
+__device__ __forceinline__ void named_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Persistent warp-specialised kernel.
+//   warps 0-3 : producers.  cp.async of A rows several chunks ahead (TF32:
+//               straight into the MMA layout; BF16x3: into a raw FP32 ring,
+//               then split into hi/lo), B expanded from L2-resident rows.
+//   warp 4    : TMEM allocation; lane 0 issues tcgen05.mma and commits.
+//   warps 5-8 : epilogue (TMEM lanes 32*(warp%4) ...), two accumulators so
+//               that a tile's epilogue overlaps the next tile's MMAs.
+constexpr int NPROD = 128;
+constexpr int MMA_WARP = 4;
+constexpr int EPI_WARP0 = 5;
+constexpr int NTHREADS = 288;
+constexpr int ACC_COLS = 128;
+constexpr int TMEM_COLS2 = 256;
+
+template <int PREC>
+struct Cfg {
+    static constexpr int STAGES = PREC == 1 ? 4 : 3;
+    static constexpr int LOOK = STAGES - 1;
+    static constexpr int SLOT_A = TBM * TBKR * 4;
+    static constexpr int SLOT_B = TBNR * TBKR * 4;
+    static constexpr int SLOT_RAW = PREC == 2 ? TBM * TBK * 8 : 0;
+    static constexpr int OFF_B = STAGES * SLOT_A;
+    static constexpr int OFF_RAW = OFF_B + STAGES * SLOT_B;
+    static constexpr int OFF_CTRL = OFF_RAW + STAGES * SLOT_RAW;
+};
+
+struct EpiMeta {
     int64_t cbase[TBN];
     int32_t eb[TBN];
     uint32_t mx[TBN];
-    int64_t ia;
-    int ea;
-    int abort_;
+    int32_t ea;
+    int32_t pad;
 };
 
-template <int PREC>  // 1 = TF32, 2 = BF16x3
-__global__ void __launch_bounds__(128) k_step_gemm_tc(const StepDesc d, int ctiles, int mtiles, int32_t *err) {
+struct Ctrl {
+    uint64_t full[4], empty[4], tfull[2], tempty[2];
+    uint32_t tmem_base;
+    int32_t abort_;
+    int32_t epi_stop, epi_fail;  // epilogue-uniform abort decisions
+    EpiMeta epi[2];
+};
+
+template <int PREC>
+constexpr size_t smem_bytes() {
+    return size_t(Cfg<PREC>::OFF_CTRL) + sizeof(Ctrl) + 128;
+}
+
+struct TileInfo {
+    int64_t i0, icount, c0, m0;
+    int mt;
+};
+
+__device__ __forceinline__ TileInfo decode_tile(const StepDesc &d, int64_t T, int64_t mtiles) {
+    TileInfo t;
+    const int64_t e = T / mtiles;
+    t.mt = int(T - e * mtiles);
+    const int64_t packed = d.ctab[e];
+    const int64_t g = packed >> 20;
+    t.i0 = d.gfirst[g];
+    t.icount = d.gfirst[g + 1] - t.i0;
+    t.c0 = (packed & 0xfffff) * TBN;
+    t.m0 = int64_t(t.mt) * TBM;
+    return t;
+}
+
+__device__ __forceinline__ int64_t a_instance(const StepDesc &d, int64_t i) {
+    const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
+    return int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
+}
+
+__device__ __forceinline__ int64_t b_instance(const StepDesc &d, int64_t i) {
+    const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
+    return int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err) {
+    using C = Cfg<PREC>;
     extern __shared__ uint8_t smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    Ctrl &X = *reinterpret_cast<Ctrl *>(sm + C::OFF_CTRL);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t bid = blockIdx.x;
-    const int mt = int(bid % mtiles);
-    const int64_t rest = bid / mtiles;
-    const int ct = int(rest % ctiles);
-    const int64_t g = rest / ctiles;
-    const int64_t i0 = d.gfirst[g];
-    const int64_t icount = d.gfirst[g + 1] - i0;
+    const int64_t n_tiles = d.n_ctab * mtiles;
     const int N = 1 << d.nb;
     const int64_t M = int64_t(1) << d.mb;
     const int K = 1 << d.kb;
-    const int64_t cols = icount * N;
-    const int64_t c0 = int64_t(ct) * TBN;
-    if (c0 >= cols) return;  // uniform
-    if (*reinterpret_cast<volatile int32_t *>(err) != 0) return;  // an earlier CTA gave up
-    const int64_t m0 = int64_t(mt) * TBM;
+    const int nch = (K + TBK - 1) / TBK;
+    const int64_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total_chunks = my_tiles * nch;
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&S.tmem_base)),
-                     "r"(TMEM_COLS)
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&X.tmem_base)),
+                     "r"(TMEM_COLS2)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const int64_t sig = i0 / d.nOut, beta = i0 - sig * d.nOut;
-        S.ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
-        S.ea = d.mxA ? exp_of(d.mxA[S.ia]) : 0;
-        S.abort_ = 0;
-    }
-    {
-        const int64_t m = m0 + tid;
-        S.offA[tid] = m < M ? dep(m, d.pAm, d.mb) : -1;
-        S.offC[tid] = m < M ? dep(m, d.pCm, d.mb) : -1;
-    }
-    if (tid < TBN) {
-        const int c = tid;
-        const int64_t gc = c0 + c;
-        S.mx[c] = 0;
-        if (gc < cols) {
-            const int64_t inst = i0 + gc / N;
-            const int n = int(gc % N);
-            const int64_t sig = inst / d.nOut, beta = inst - sig * d.nOut;
-            const int64_t ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
-            S.bbase[c] = ib * d.sB + dep(n, d.pBn, d.nb);
-            S.cbase[c] = inst * d.sC + dep(n, d.pCn, d.nb);
-            S.eb[c] = d.mxB ? exp_of(d.mxB[ib]) : 0;
-        } else {
-            S.bbase[c] = -1;
-            S.cbase[c] = -1;
-            S.eb[c] = 0;
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&X.full[s], NPROD);
+            mbar_init(&X.empty[s], 1);
         }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&X.tfull[a], 1);
+            mbar_init(&X.tempty[a], 128);
+        }
+        X.abort_ = *reinterpret_cast<volatile int32_t *>(err);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid < TBN && S.cbase[tid] >= 0 && mt == 0) {
-        const int64_t gc = c0 + tid;
-        if (gc % N == 0) {
-            const int64_t inst = i0 + gc / N;
-            const int64_t sig = inst / d.nOut, beta = inst - sig * d.nOut;
-            const int64_t ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
-            d.EC[inst] = d.EA[S.ia] + S.ea + d.EB[ib] + S.eb[tid];
-        }
-    }
-    const uint32_t tmem = S.tmem_base;
-    const float2 *A = d.A + S.ia * d.sA;
-    const int nchunks = (K + TBK - 1) / TBK;
-    const int kc = K < TBK ? K : TBK;  // valid complex k in a chunk
-    constexpr uint32_t LBO = TBM * 16, SBO = 128;
-    bool ok = true;
+    const uint32_t tmem = X.tmem_base;
+    volatile int32_t *abort_flag = &X.abort_;
+    auto give_up = [&]() {
+        atomicExch(err, 1);
+        *abort_flag = 1;
+    };
 
-    for (int c = 0; c < nchunks && ok; ++c) {
-        const int s = c & 1;
-        if (c >= 2) {
-            if (!mbar_wait(&S.bar[s], uint32_t((c - 2) >> 1) & 1u)) {
-                ok = false;
+    if (warp < 4) {
+        // ------------------------------------------------------------ producers
+        const int kq = (tid >> 3) & 3;
+        int rowj[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rowj[j] = ((tid >> 5) + 4 * j) * 8 + (tid & 7);
+        const int bcol = tid & 63;
+        const float2 *abase[2] = {nullptr, nullptr};
+        int64_t offA[2][4];
+        int64_t bbase = -1;
+        int64_t issued = 0;
+        for (int64_t gch = 0; gch < total_chunks && !*abort_flag; ++gch) {
+            while (issued < total_chunks && issued <= gch + C::LOOK) {
+                const int64_t l = issued / nch;
+                const int c = int(issued - l * nch);
+                const int slot = int(issued % C::STAGES);
+                const uint32_t ph = uint32_t(issued / C::STAGES) & 1u;
+                if (c == 0) {
+                    const TileInfo t = decode_tile(d, blockIdx.x + l * gridDim.x, mtiles);
+                    abase[l & 1] = d.A + a_instance(d, t.i0) * d.sA;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int64_t m = t.m0 + rowj[j];
+                        offA[l & 1][j] = m < M ? dep(m, d.pAm, d.mb) : -1;
+                    }
+                }
+                if (!mbar_wait(&X.empty[slot], ph ^ 1u)) {
+                    give_up();
+                    break;
+                }
+                const float2 *ab = abase[l & 1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t oa = offA[l & 1][j];
+                    const int k = c * TBK + 4 * kq;
+                    const bool v = oa >= 0 && k + 3 < K;
+                    const float2 *src = v ? ab + oa + k : ab;
+                    if (PREC == 1) {
+                        const uint32_t dst = smem_u32(sm + slot * C::SLOT_A);
+                        cp_async16(dst + kmaj_off(rowj[j], 8 * kq, 4), src, v ? 16 : 0);
+                        cp_async16(dst + kmaj_off(rowj[j], 8 * kq + 4, 4), v ? src + 2 : ab, v ? 16 : 0);
+                    } else {
+                        const uint32_t dst = smem_u32(sm + C::OFF_RAW + slot * C::SLOT_RAW) + uint32_t(tid * 4 + j) * 32;
+                        cp_async16(dst, src, v ? 16 : 0);
+                        cp_async16(dst + 16, v ? src + 2 : ab, v ? 16 : 0);
+                    }
+                }
+                cp_async_commit();
+                ++issued;
+            }
+            if (*abort_flag) break;
+            cp_async_wait(int(issued - gch - 1));
+            const int64_t l = gch / nch;
+            const int c = int(gch - l * nch);
+            const int slot = int(gch % C::STAGES);
+            if (c == 0) {
+                const TileInfo t = decode_tile(d, blockIdx.x + l * gridDim.x, mtiles);
+                const int64_t gc = t.c0 + bcol;
+                bbase = -1;
+                if (gc < (t.icount << d.nb)) {
+                    const int64_t inst = t.i0 + (gc >> d.nb);
+                    bbase = b_instance(d, inst) * d.sB + dep(gc & (N - 1), d.pBn, d.nb);
+                }
+            }
+            if (PREC == 2) {
+                uint8_t *bh = sm + slot * C::SLOT_A, *bl = bh + TBM * TBKR * 2;
+                const uint8_t *raw = sm + C::OFF_RAW + slot * C::SLOT_RAW;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 v0 = *reinterpret_cast<const float4 *>(raw + (tid * 4 + j) * 32);
+                    const float4 v1 = *reinterpret_cast<const float4 *>(raw + (tid * 4 + j) * 32 + 16);
+                    const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                    __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        hi[q] = __float2bfloat16_rn(x[q]);
+                        lo[q] = __float2bfloat16_rn(x[q] - __bfloat162float(hi[q]));
+                    }
+                    *reinterpret_cast<uint4 *>(bh + kmaj_off(rowj[j], 8 * kq, 2)) = *reinterpret_cast<uint4 *>(hi);
+                    *reinterpret_cast<uint4 *>(bl + kmaj_off(rowj[j], 8 * kq, 2)) = *reinterpret_cast<uint4 *>(lo);
+                }
+            }
+            // B: this thread's column, k quads (tid >> 6) and (tid >> 6) + 2
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int kqb = (tid >> 6) + 2 * j;
+                float2 t4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = c * TBK + 4 * kqb + q;
+                    t4[q] = (bbase >= 0 && k < K) ? __ldg(d.B + bbase + k) : make_float2(0.f, 0.f);
+                }
+                const float r0[8] = {t4[0].x, -t4[0].y, t4[1].x, -t4[1].y, t4[2].x, -t4[2].y, t4[3].x, -t4[3].y};
+                const float r1[8] = {t4[0].y, t4[0].x, t4[1].y, t4[1].x, t4[2].y, t4[2].x, t4[3].y, t4[3].x};
+                uint8_t *base = sm + C::OFF_B + slot * C::SLOT_B;
+                if (PREC == 1) {
+                    *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol, 8 * kqb, 4)) = make_float4(r0[0], r0[1], r0[2], r0[3]);
+                    *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol, 8 * kqb + 4, 4)) = make_float4(r0[4], r0[5], r0[6], r0[7]);
+                    *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb, 4)) = make_float4(r1[0], r1[1], r1[2], r1[3]);
+                    *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb + 4, 4)) = make_float4(r1[4], r1[5], r1[6], r1[7]);
+                } else {
+                    __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        h0[q] = __float2bfloat16_rn(r0[q]);
+                        l0[q] = __float2bfloat16_rn(r0[q] - __bfloat162float(h0[q]));
+                        h1[q] = __float2bfloat16_rn(r1[q]);
+                        l1[q] = __float2bfloat16_rn(r1[q] - __bfloat162float(h1[q]));
+                    }
+                    uint8_t *blo = base + TBNR * TBKR * 2;
+                    *reinterpret_cast<uint4 *>(base + kmaj_off(2 * bcol, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(h0);
+                    *reinterpret_cast<uint4 *>(blo + kmaj_off(2 * bcol, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(l0);
+                    *reinterpret_cast<uint4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(h1);
+                    *reinterpret_cast<uint4 *>(blo + kmaj_off(2 * bcol + 1, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(l1);
+                }
+            }
+            proxy_fence();
+            mbar_arrive(&X.full[slot]);
+        }
+        cp_async_wait(0);
+    } else if (warp == MMA_WARP) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t LBO = TBM * 16, SBO = 128;
+            int64_t gch = 0;
+            for (int64_t l = 0; l < my_tiles && !*abort_flag; ++l) {
+                const int acc = int(l & 1);
+                if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> 1) & 1u) ^ 1u)) {
+                    give_up();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
+                bool ok = true;
+                for (int c = 0; c < nch; ++c, ++gch) {
+                    const int slot = int(gch % C::STAGES);
+                    if (!mbar_wait(&X.full[slot], uint32_t(gch / C::STAGES) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (PREC == 1) {
+                        const uint32_t id = idesc(2u);
+                        const uint32_t a0 = smem_u32(sm + slot * C::SLOT_A);
+                        const uint32_t b0 = smem_u32(sm + C::OFF_B + slot * C::SLOT_B);
+#pragma unroll
+                        for (int j = 0; j < TBKR / 8; ++j) {
+                            const uint32_t off = uint32_t(2 * j) * LBO;
+                            mma_tf32(dtm, sdesc(a0 + off, LBO, SBO), sdesc(b0 + off, LBO, SBO), id,
+                                     (c > 0 || j > 0) ? 1u : 0u);
+                        }
+                    } else {
+                        const uint32_t id = idesc(1u);
+                        const uint32_t ah = smem_u32(sm + slot * C::SLOT_A), al = ah + TBM * TBKR * 2;
+                        const uint32_t bh = smem_u32(sm + C::OFF_B + slot * C::SLOT_B), bl = bh + TBNR * TBKR * 2;
+#pragma unroll
+                        for (int j = 0; j < TBKR / 16; ++j) {
+                            const uint32_t off = uint32_t(2 * j) * LBO;
+                            mma_f16(dtm, sdesc(ah + off, LBO, SBO), sdesc(bh + off, LBO, SBO), id,
+                                    (c > 0 || j > 0) ? 1u : 0u);
+                            mma_f16(dtm, sdesc(ah + off, LBO, SBO), sdesc(bl + off, LBO, SBO), id, 1u);
+                            mma_f16(dtm, sdesc(al + off, LBO, SBO), sdesc(bh + off, LBO, SBO), id, 1u);
+                        }
+                    }
+                    mma_commit(&X.empty[slot]);
+                }
+                if (!ok) {
+                    give_up();
+                    break;
+                }
+                mma_commit(&X.tfull[acc]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int e = tid - EPI_WARP0 * 32;  // 0..127
+        const int lanegrp = warp & 3;        // TMEM lanes 32*lanegrp ...
+        const int row = lanegrp * 32 + lane;
+        for (int64_t l = 0; l < my_tiles; ++l) {
+            const int acc = int(l & 1);
+            EpiMeta &em = X.epi[acc];
+            const TileInfo t = decode_tile(d, blockIdx.x + l * gridDim.x, mtiles);
+            const int64_t cols = t.icount << d.nb;
+            if (e == 0) {
+                const int64_t ia = a_instance(d, t.i0);
+                em.ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
+                X.epi_stop = *abort_flag;
+                X.epi_fail = 0;
+            }
+            named_sync(1, 128);
+            if (X.epi_stop) break;  // uniform: read after the barrier
+            if (e < TBN) {
+                const int64_t gc = t.c0 + e;
+                em.mx[e] = 0;
+                if (gc < cols) {
+                    const int64_t inst = t.i0 + (gc >> d.nb);
+                    const int n = int(gc & (N - 1));
+                    const int64_t ib = b_instance(d, inst);
+                    em.cbase[e] = inst * d.sC + dep(n, d.pCn, d.nb);
+                    em.eb[e] = d.mxB ? exp_of(d.mxB[ib]) : 0;
+                    if (n == 0 && t.mt == 0) d.EC[inst] = d.EA[a_instance(d, t.i0)] + em.ea + d.EB[ib] + em.eb[e];
+                } else {
+                    em.cbase[e] = -1;
+                    em.eb[e] = 0;
+                }
+            }
+            if (!mbar_wait(&X.tfull[acc], uint32_t(l >> 1) & 1u)) atomicOr(&X.epi_fail, 1);
+            named_sync(1, 128);
+            if (X.epi_fail) {  // uniform
+                if (e == 0) give_up();
                 break;
             }
             tc_fence_after();
-        }
-        const int k0 = c * TBK;
-        // ---- stage A: units of 4 complex (32 B) per row; 128 rows x 4 units
-        for (int u = tid; u < TBM * (TBK / 4); u += 128) {
-            const int rl = u & 7, kq = (u >> 3) & 3, rh = u >> 5;
-            const int row = rh * 8 + rl;
-            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-            if (S.offA[row] >= 0) {
-                const float2 *src = A + S.offA[row] + k0 + 4 * kq;
-                if (4 * kq + 3 < kc) {
-                    v0 = __ldg(reinterpret_cast<const float4 *>(src));
-                    v1 = __ldg(reinterpret_cast<const float4 *>(src) + 1);
-                } else {
-                    float2 t[4];
-                    for (int j = 0; j < 4; ++j) t[j] = (4 * kq + j < kc) ? __ldg(src + j) : make_float2(0.f, 0.f);
-                    v0 = make_float4(t[0].x, t[0].y, t[1].x, t[1].y);
-                    v1 = make_float4(t[2].x, t[2].y, t[3].x, t[3].y);
-                }
-            }
-            if (PREC == 1) {
-                uint8_t *base = S.a[s];
-                *reinterpret_cast<float4 *>(base + kmaj_off(row, 8 * kq, 4)) = v0;
-                *reinterpret_cast<float4 *>(base + kmaj_off(row, 8 * kq + 4, 4)) = v1;
-            } else {
-                const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    hi[j] = __float2bfloat16_rn(x[j]);
-                    lo[j] = __float2bfloat16_rn(x[j] - __bfloat162float(hi[j]));
-                }
-                uint8_t *bh = S.a[s], *bl = S.a[s] + TBM * TBKR * 2;
-                *reinterpret_cast<uint4 *>(bh + kmaj_off(row, 8 * kq, 2)) = *reinterpret_cast<uint4 *>(hi);
-                *reinterpret_cast<uint4 *>(bl + kmaj_off(row, 8 * kq, 2)) = *reinterpret_cast<uint4 *>(lo);
-            }
-        }
-        // ---- stage B: 64 complex columns x 4 units of 4 complex k
-        for (int u = tid; u < TBN * (TBK / 4); u += 128) {
-            const int col = u % TBN, kq = u / TBN;
-            float2 t[4];
-            for (int j = 0; j < 4; ++j) {
-                const int k = 4 * kq + j;
-                t[j] = (S.bbase[col] >= 0 && k < kc) ? __ldg(d.B + S.bbase[col] + k0 + k) : make_float2(0.f, 0.f);
-            }
-            // row 2col: (Re, -Im) pairs; row 2col+1: (Im, Re) pairs
-            const float r0[8] = {t[0].x, -t[0].y, t[1].x, -t[1].y, t[2].x, -t[2].y, t[3].x, -t[3].y};
-            const float r1[8] = {t[0].y, t[0].x, t[1].y, t[1].x, t[2].y, t[2].x, t[3].y, t[3].x};
-            if (PREC == 1) {
-                uint8_t *base = S.b[s];
-                *reinterpret_cast<float4 *>(base + kmaj_off(2 * col, 8 * kq, 4)) = make_float4(r0[0], r0[1], r0[2], r0[3]);
-                *reinterpret_cast<float4 *>(base + kmaj_off(2 * col, 8 * kq + 4, 4)) = make_float4(r0[4], r0[5], r0[6], r0[7]);
-                *reinterpret_cast<float4 *>(base + kmaj_off(2 * col + 1, 8 * kq, 4)) = make_float4(r1[0], r1[1], r1[2], r1[3]);
-                *reinterpret_cast<float4 *>(base + kmaj_off(2 * col + 1, 8 * kq + 4, 4)) = make_float4(r1[4], r1[5], r1[6], r1[7]);
-            } else {
-                __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    h0[j] = __float2bfloat16_rn(r0[j]);
-                    l0[j] = __float2bfloat16_rn(r0[j] - __bfloat162float(h0[j]));
-                    h1[j] = __float2bfloat16_rn(r1[j]);
-                    l1[j] = __float2bfloat16_rn(r1[j] - __bfloat162float(h1[j]));
-                }
-                uint8_t *bh = S.b[s], *bl = S.b[s] + TBNR * TBKR * 2;
-                *reinterpret_cast<uint4 *>(bh + kmaj_off(2 * col, 8 * kq, 2)) = *reinterpret_cast<uint4 *>(h0);
-                *reinterpret_cast<uint4 *>(bl + kmaj_off(2 * col, 8 * kq, 2)) = *reinterpret_cast<uint4 *>(l0);
-                *reinterpret_cast<uint4 *>(bh + kmaj_off(2 * col + 1, 8 * kq, 2)) = *reinterpret_cast<uint4 *>(h1);
-                *reinterpret_cast<uint4 *>(bl + kmaj_off(2 * col + 1, 8 * kq, 2)) = *reinterpret_cast<uint4 *>(l1);
-            }
-        }
-        proxy_fence();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            if (PREC == 1) {
-                const uint32_t id = idesc(2u);
-                const uint32_t a0 = smem_u32(S.a[s]), b0 = smem_u32(S.b[s]);
-#pragma unroll
-                for (int j = 0; j < TBKR / 8; ++j) {  // K = 8 tf32 = 2 core-matrix columns per MMA
-                    const uint32_t off = uint32_t(2 * j) * LBO;
-                    mma_tf32(tmem, sdesc(a0 + off, LBO, SBO), sdesc(b0 + off, LBO, SBO), id, (c > 0 || j > 0) ? 1u : 0u);
-                }
-            } else {
-                const uint32_t id = idesc(1u);
-                const uint32_t ah = smem_u32(S.a[s]), al = ah + TBM * TBKR * 2;
-                const uint32_t bh = smem_u32(S.b[s]), bl = bh + TBNR * TBKR * 2;
-#pragma unroll
-                for (int j = 0; j < TBKR / 16; ++j) {  // K = 16 bf16 = 2 core-matrix columns per MMA
-                    const uint32_t off = uint32_t(2 * j) * LBO;
-                    mma_f16(tmem, sdesc(ah + off, LBO, SBO), sdesc(bh + off, LBO, SBO), id, (c > 0 || j > 0) ? 1u : 0u);
-                    mma_f16(tmem, sdesc(ah + off, LBO, SBO), sdesc(bl + off, LBO, SBO), id, 1u);
-                    mma_f16(tmem, sdesc(al + off, LBO, SBO), sdesc(bh + off, LBO, SBO), id, 1u);
-                }
-            }
-            mma_commit(&S.bar[s]);
-        }
-    }
-    // wait for the last two commits (every MMA of the tile)
-    if (ok) {
-        for (int c = (nchunks >= 2 ? nchunks - 2 : 0); c < nchunks; ++c)
-            if (!mbar_wait(&S.bar[c & 1], uint32_t(c >> 1) & 1u)) ok = false;
-    }
-    if (!ok) {
-        atomicExch(err, 1);
-        S.abort_ = 1;
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (!S.abort_) {
-        const int row = warp * 32 + lane;
-        const bool rv = S.offC[row] >= 0;
-        const int64_t offc = S.offC[row];
+            const int64_t m = t.m0 + row;
+            const int64_t offc = m < M ? dep(m, d.pCm, d.mb) : -1;
 #pragma unroll 1
-        for (int cb = 0; cb < TBNR / 16; ++cb) {
-            float v[16];
-            tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(cb * 16), v);
+            for (int cb = 0; cb < TBNR / 16; ++cb) {
+                float v[16];
+                tmem_ld16(tmem + uint32_t(acc * ACC_COLS) + (uint32_t(lanegrp * 32) << 16) + uint32_t(cb * 16), v);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int col = cb * 8 + j;
-                if (!rv || S.cbase[col] < 0) continue;
-                const float sc = pow2f(-(S.ea + S.eb[col]));
-                const float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
-                d.C[S.cbase[col] + offc] = o;
-                if (d.mxC) atomicMax(&S.mx[col], __float_as_uint(fmaxf(fabsf(o.x), fabsf(o.y))));
+                for (int j = 0; j < 8; ++j) {
+                    const int col = cb * 8 + j;
+                    if (offc < 0 || em.cbase[col] < 0) continue;
+                    const float sc = pow2f(-(em.ea + em.eb[col]));
+                    const float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
+                    d.C[em.cbase[col] + offc] = o;
+                    if (d.mxC) atomicMax(&em.mx[col], __float_as_uint(fmaxf(fabsf(o.x), fabsf(o.y))));
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&X.tempty[acc]);
+            named_sync(1, 128);
+            if (d.mxC && e < TBN && em.cbase[e] >= 0 && em.mx[e]) {
+                const int64_t inst = t.i0 + ((t.c0 + e) >> d.nb);
+                record_max(d.mxC + inst, em.mx[e]);
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (d.mxC && !S.abort_ && tid < TBN && S.cbase[tid] >= 0) {
-        const int64_t inst = i0 + (c0 + tid) / N;
-        record_max(d.mxC + inst, S.mx[tid]);
-    }
-    if (warp == 0) {
+    if (warp == MMA_WARP) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS2) : "memory");
     }
 }
 
@@ -416,32 +559,37 @@ bool gemm_tc_supports(const StepDesc &d) {
     return d.kb >= 3 && d.mb >= 6 && d.kb <= 24;
 }
 
+namespace {
+int g_num_sms = 0;
+}
+
 cudaError_t launch_step_gemm_tc(const StepDesc &d, int precision, int32_t *err, cudaStream_t s) {
     if (!gemm_tc_supports(d)) return cudaErrorNotSupported;
     const int64_t M = int64_t(1) << d.mb;
-    const int64_t N = int64_t(1) << d.nb;
-    const int64_t ctiles = (int64_t(d.max_group) * N + TBN - 1) / TBN;
     const int64_t mtiles = (M + TBM - 1) / TBM;
-    const int64_t blocks = d.n_groups * ctiles * mtiles;
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL || ctiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    // padded so that every descriptor-addressed read stays inside the
-    // allocation even for a misread of the LBO/SBO roles
-    const size_t smem = (sizeof(Smem) + 128 > 96 * 1024 ? sizeof(Smem) + 128 : 96 * 1024);
+    const int64_t tiles = d.n_ctab * mtiles;
+    if (tiles <= 0) return cudaSuccess;
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    const int64_t grid = tiles < g_num_sms ? tiles : g_num_sms;
     if (precision == 1) {
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_step_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_step_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
             attr = true;
         }
-        k_step_gemm_tc<1><<<dim3((unsigned)blocks), 128, smem, s>>>(d, (int)ctiles, (int)mtiles, err);
+        k_step_gemm_tc<1><<<dim3((unsigned)grid), NTHREADS, smem_bytes<1>(), s>>>(d, mtiles, err);
     } else {
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_step_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_step_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2>());
             attr = true;
         }
-        k_step_gemm_tc<2><<<dim3((unsigned)blocks), 128, smem, s>>>(d, (int)ctiles, (int)mtiles, err);
+        k_step_gemm_tc<2><<<dim3((unsigned)grid), NTHREADS, smem_bytes<2>(), s>>>(d, mtiles, err);
     }
     return cudaGetLastError();
 }

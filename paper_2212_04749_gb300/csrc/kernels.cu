@@ -73,19 +73,24 @@ __global__ void k_fill(const FillJobD *__restrict__ jobs, int64_t njobs, const L
 
 constexpr int ROW_THREADS = 256;
 
-// One thread per row m of an A instance; B (K x N <= 256 entries) of the
-// instance in shared memory when the block lies inside one instance.
-// N = 2^NB <= 16, K <= 128.  A rows are K-contiguous (K-major operands).
+// Small-rank step (N = 2^NB <= 16, K*N <= 256): the warp-shuffle kernel.
+// Each row's K-contiguous run of A is split over L = min(8, K/2) lanes that
+// load 16 bytes (2 complex) at a time, so every warp load covers runs of
+// L x 16 contiguous bytes; the partial products of the N outputs are summed
+// across the row's L lanes with xor-shuffles.  R = 32 / L rows per warp
+// pass, rows_per_block rows per block (whole rows; when the block lies
+// inside one instance its B is staged in shared memory and its max-|x|
+// word is recorded once).
 template <int NB>
-__global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d) {
+__global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int rows_per_block) {
     constexpr int N = 1 << NB;
     __shared__ int8_t s_pAm[40], s_pCm[40];
     __shared__ int64_t s_offBn[16], s_offCn[16];
-    __shared__ int64_t s_mloA[ROW_THREADS], s_mloC[ROW_THREADS];
+    __shared__ int64_t s_mloA[256], s_mloC[256];
     __shared__ float2 s_B[256];
     __shared__ int64_t s_hiA, s_hiC, s_ia, s_ib;
     __shared__ int s_ea, s_eb;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = 1 << d.kb;
     const int mb = d.mb;
     const int64_t M = int64_t(1) << mb;
@@ -100,88 +105,116 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d) {
     }
     __syncthreads();
     const int lob = mb < 8 ? mb : 8;
-    const int lo = tid & ((1 << lob) - 1);
-    s_mloA[tid] = dep(lo, s_pAm, lob);
-    s_mloC[tid] = dep(lo, s_pCm, lob);
-    const int64_t gid0 = int64_t(blockIdx.x) * ROW_THREADS;
-    const bool uniform = M >= ROW_THREADS;  // the whole block inside one instance
-    if (uniform && tid == 0 && gid0 < total) {
-        const int64_t i = gid0 >> mb;
+    {
+        const int lo = tid & ((1 << lob) - 1);
+        s_mloA[tid] = dep(lo, s_pAm, lob);
+        s_mloC[tid] = dep(lo, s_pCm, lob);
+    }
+    const int64_t r0 = int64_t(blockIdx.x) * rows_per_block;
+    const bool uniform = M >= rows_per_block;  // the block lies inside one instance
+    if (uniform && tid == 0 && r0 < total) {
+        const int64_t i = r0 >> mb;
         const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
         s_ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
         s_ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
-        const int64_t mh = (gid0 & (M - 1)) >> 8;
-        s_hiA = mb > 8 ? dep(mh, s_pAm + 8, mb - 8) : 0;
-        s_hiC = mb > 8 ? dep(mh, s_pCm + 8, mb - 8) : 0;
         s_ea = d.mxA ? exp_of(d.mxA[s_ia]) : 0;
         s_eb = d.mxB ? exp_of(d.mxB[s_ib]) : 0;
     }
     __syncthreads();
-    if (uniform && gid0 < total) {
+    if (uniform && r0 < total) {
         for (int e = tid; e < K * N; e += ROW_THREADS) {
             const int k = e >> NB, n = e & (N - 1);
             s_B[e] = d.B[s_ib * d.sB + k + s_offBn[n]];
         }
         __syncthreads();
     }
-    const int64_t gid = gid0 + tid;
-    if (gid >= total) return;
-    const int64_t i = gid >> mb;
-    const int64_t m = gid & (M - 1);
-    int64_t ia, ib, offA, offC;
-    int ea, eb;
-    if (uniform) {
-        ia = s_ia;
-        ib = s_ib;
-        offA = s_hiA + s_mloA[tid];
-        offC = s_hiC + s_mloC[tid];
-        ea = s_ea;
-        eb = s_eb;
-    } else {
-        const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
-        ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
-        ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
-        offA = s_mloA[m & 255];
-        offC = s_mloC[m & 255];
-        ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
-        eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
-    }
-    const float2 *A = d.A + ia * d.sA + offA;
-    float2 acc[N];
-#pragma unroll
-    for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
-    if (uniform) {
-        for (int k = 0; k < K; ++k) {
-            const float2 a = __ldg(A + k);
-#pragma unroll
-            for (int n = 0; n < N; ++n) cfma(acc[n], a, s_B[k * N + n]);
-        }
-    } else {
-        const float2 *B = d.B + ib * d.sB;
-        for (int k = 0; k < K; ++k) {
-            const float2 a = __ldg(A + k);
-#pragma unroll
-            for (int n = 0; n < N; ++n) cfma(acc[n], a, __ldg(B + k + s_offBn[n]));
-        }
-    }
-    const float sc = pow2f(-(ea + eb));
-    float2 *C = d.C + i * d.sC + offC;
-    uint32_t mx = 0;
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-        const float2 v = make_float2(acc[n].x * sc, acc[n].y * sc);
-        C[s_offCn[n]] = v;
-        mx = max(mx, absmax_bits(v));
-    }
-    if (m == 0) d.EC[i] = d.EA[ia] + ea + d.EB[ib] + eb;
-    if (d.mxC) {
-        if (M >= 32) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if ((tid & 31) == 0) record_max(d.mxC + i, mx);
+    const int L = K >= 16 ? 8 : (K >= 2 ? K / 2 : 1);  // lanes per row
+    const int R = 32 / L;                              // rows per warp pass
+    const int sub = lane / L, kl = lane % L;
+    const int passes = rows_per_block / (8 * R);
+    uint32_t mx_run = 0;  // uniform blocks: max over every row of the block
+    for (int it = 0; it < passes; ++it) {
+        const int64_t gid = r0 + (int64_t(it) * 8 + warp) * R + sub;
+        const bool valid = gid < total;
+        const int64_t g = valid ? gid : r0;
+        const int64_t i = g >> mb;
+        const int64_t m = g & (M - 1);
+        int64_t ia, ib;
+        int ea, eb;
+        const float2 *Bp = nullptr;
+        if (uniform) {
+            ia = s_ia;
+            ib = s_ib;
+            ea = s_ea;
+            eb = s_eb;
         } else {
-            record_max(d.mxC + i, mx);
+            const uint32_t ii = uint32_t(i), no = uint32_t(d.nOut);
+            const uint32_t sig = ii / no, beta = ii - sig * no;
+            ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
+            ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
+            ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
+            eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
+            Bp = d.B + ib * d.sB;
         }
+        const int64_t offA = (mb > 8 ? dep(m >> 8, s_pAm + 8, mb - 8) : 0) + s_mloA[m & 255];
+        const float2 *A = d.A + ia * d.sA + offA;
+        float2 acc[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
+        if (valid) {
+            if (K >= 2) {
+                for (int k = 2 * kl; k < K; k += 2 * L) {
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(A + k));
+                    const float2 a0 = make_float2(v.x, v.y), a1 = make_float2(v.z, v.w);
+#pragma unroll
+                    for (int n = 0; n < N; ++n) {
+                        const float2 b0 = uniform ? s_B[k * N + n] : __ldg(Bp + k + s_offBn[n]);
+                        const float2 b1 = uniform ? s_B[(k + 1) * N + n] : __ldg(Bp + k + 1 + s_offBn[n]);
+                        cfma(acc[n], a0, b0);
+                        cfma(acc[n], a1, b1);
+                    }
+                }
+            } else {
+                const float2 a0 = __ldg(A);
+#pragma unroll
+                for (int n = 0; n < N; ++n) cfma(acc[n], a0, uniform ? s_B[n] : __ldg(Bp + s_offBn[n]));
+            }
+        }
+        for (int o = L >> 1; o > 0; o >>= 1) {
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                acc[n].x += __shfl_xor_sync(0xffffffffu, acc[n].x, o);
+                acc[n].y += __shfl_xor_sync(0xffffffffu, acc[n].y, o);
+            }
+        }
+        const float sc = pow2f(-(ea + eb));
+        uint32_t mx = 0;
+        if (valid) {
+            const int64_t offC = (mb > 8 ? dep(m >> 8, s_pCm + 8, mb - 8) : 0) + s_mloC[m & 255];
+            float2 *C = d.C + i * d.sC + offC;
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                if (n % L != kl) continue;  // lanes of the row split the stores
+                const float2 v = make_float2(acc[n].x * sc, acc[n].y * sc);
+                C[s_offCn[n]] = v;
+                mx = max(mx, absmax_bits(v));
+            }
+            if (m == 0 && kl == 0) d.EC[i] = d.EA[ia] + ea + d.EB[ib] + eb;
+        }
+        if (d.mxC) {
+            if (uniform) mx_run = max(mx_run, mx);
+            else if (valid && mx) record_max(d.mxC + i, mx);
+        }
+    }
+    if (d.mxC && uniform) {
+        __shared__ uint32_t s_mx;
+        if (tid == 0) s_mx = 0;
+        __syncthreads();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx_run = max(mx_run, __shfl_xor_sync(0xffffffffu, mx_run, o));
+        if (lane == 0) atomicMax(&s_mx, mx_run);
+        __syncthreads();
+        if (tid == 0 && s_mx && r0 < total) record_max(d.mxC + (r0 >> mb), s_mx);
     }
 }
 
@@ -371,17 +404,26 @@ cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *hi
 
 cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
     if (d.kb + d.nb > 8 || d.nb > 4 || d.mb > 40) return cudaErrorInvalidValue;
+    const int K = 1 << d.kb;
+    const int L = K >= 16 ? 8 : (K >= 2 ? K / 2 : 1);
+    const int R = 32 / L;
+    // 8 warps x R rows per pass, up to 16 passes, and no more rows than one
+    // instance has (so that a block stays inside one instance when it can)
+    const int64_t M = int64_t(1) << d.mb;
+    int64_t passes = M / (8 * R);
+    passes = passes < 1 ? 1 : (passes > 16 ? 16 : passes);
+    const int rows_per_block = int(8 * R * passes);
     const int64_t rows = d.nInst << d.mb;
-    const int64_t blocks = (rows + ROW_THREADS - 1) / ROW_THREADS;
+    const int64_t blocks = (rows + rows_per_block - 1) / rows_per_block;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const dim3 g((unsigned)blocks);
     switch (d.nb) {
-        case 0: k_step_row<0><<<g, ROW_THREADS, 0, s>>>(d); break;
-        case 1: k_step_row<1><<<g, ROW_THREADS, 0, s>>>(d); break;
-        case 2: k_step_row<2><<<g, ROW_THREADS, 0, s>>>(d); break;
-        case 3: k_step_row<3><<<g, ROW_THREADS, 0, s>>>(d); break;
-        default: k_step_row<4><<<g, ROW_THREADS, 0, s>>>(d); break;
+        case 0: k_step_row<0><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
+        case 1: k_step_row<1><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
+        case 2: k_step_row<2><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
+        case 3: k_step_row<3><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
+        default: k_step_row<4><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
     }
     return cudaGetLastError();
 }

@@ -34,6 +34,8 @@ struct StepDesc {
     int32_t max_group;            // largest group (instances)
     const int64_t *gfirst;        // [n_groups + 1]
     int64_t n_groups;
+    const int64_t *ctab;          // non-empty column tiles: (group << 20) | tile of 64 columns
+    int64_t n_ctab;
     int8_t pAm[40];
     int8_t pBn[24];
     int8_t pCm[40];

@@ -391,6 +391,13 @@ struct Builder {
             }
             st.group_first.push_back(nd.n_inst);
             st.n_groups = (int64_t)st.group_first.size() - 1;
+            // GEMM column tiles of 64 complex columns over each group's
+            // concatenated instances (N columns each)
+            st.col_tiles.clear();
+            for (int64_t g = 0; g < st.n_groups; ++g) {
+                const int64_t cols = (st.group_first[g + 1] - st.group_first[g]) << st.nb;
+                for (int64_t t = 0; t * 64 < cols; ++t) st.col_tiles.push_back((g << 20) | t);
+            }
             // kernel family: the per-row kernel takes a small B (N <= 16,
             // K*N <= 256) when few instances share an A (under 16 columns per
             // A on average); everything else is a GEMM over instance groups
@@ -565,6 +572,8 @@ struct Builder {
         for (Step &st : p.steps) {
             st.off_groups = take(int64_t(st.group_first.size()) * 8);
             if (emit) push_upload(p, st.off_groups, st.group_first);
+            st.off_col_tiles = take(int64_t(st.col_tiles.size()) * 8);
+            if (emit) push_upload(p, st.off_col_tiles, st.col_tiles);
         }
         // transient intermediates: first-fit over one full pass of the steps
         Arena ar;

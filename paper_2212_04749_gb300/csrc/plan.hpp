@@ -97,6 +97,8 @@ struct Step {
     int64_t n_groups = 0;    // runs of consecutive output instances sharing an A instance
     std::vector<int64_t> group_first;  // n_groups + 1 boundaries
     int64_t off_groups = -1;           // workspace offset of group_first
+    std::vector<int64_t> col_tiles;    // non-empty (group, 64-column tile) pairs: g * 2^20 + tile
+    int64_t off_col_tiles = -1;
     int kernel = 0;          // 0 = per-row SIMT, 1 = tiled SIMT GEMM, 2 = tensor-core GEMM
     double flops = 0;        // executed per pass: 8 * n_inst * 2^{mb+kb+nb}
     double bytes = 0;        // A + B reads and C write per pass
