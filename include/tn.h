@@ -148,6 +148,8 @@ typedef struct {
                                  consecutive m (resp. k) bits: contiguous runs */
     int32_t b_run_k, b_run_n;
     int64_t n_groups;         /* runs of output instances sharing one A instance */
+    int8_t c_pos_m[40];       /* address bit of C holding each m bit, and each n bit */
+    int8_t c_pos_n[24];
 } tn_step_info;
 
 int tn_plan_steps(tn_plan_t plan, tn_step_info *steps, int32_t n);

@@ -97,6 +97,8 @@ void build_descs(PlanObj *o) {
         d.n_groups = st.n_groups;
         d.ctab = at<const int64_t>(o, st.off_col_tiles);
         d.n_ctab = (int64_t)st.col_tiles.size();
+        d.trec = at<const int4>(o, st.off_tile_rec);
+        d.instab = at<const int2>(o, st.off_inst_ab);
         int64_t mg = 0;
         for (int64_t g = 0; g < st.n_groups; ++g) mg = std::max(mg, st.group_first[g + 1] - st.group_first[g]);
         d.max_group = (int32_t)mg;
@@ -305,6 +307,8 @@ int tn_plan_steps(tn_plan_t plan, tn_step_info *out, int32_t n) {
         r.b_run_k = run(st.pBk);
         r.b_run_n = run(st.pBn);
         r.n_groups = st.n_groups;
+        for (int j = 0; j < 40; ++j) r.c_pos_m[j] = j < st.mb ? st.pCm[j] : -1;
+        for (int j = 0; j < 24; ++j) r.c_pos_n[j] = j < st.nb ? st.pCn[j] : -1;
     }
     return TN_OK;
 }

@@ -144,18 +144,6 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
 // byte offset of element (row, kr) in a K-major no-swizzle tile of 128 rows,
 // element size es bytes
 __device__ __forceinline__ uint32_t kmaj_off(int row, int kr, int es) {
@@ -187,16 +175,20 @@ __device__ __forceinline__ void named_sync(int id, int n) {
 }
 
 // Persistent warp-specialised kernel.
-//   warps 0-3 : producers.  cp.async of A rows several chunks ahead (TF32:
-//               straight into the MMA layout; BF16x3: into a raw FP32 ring,
-//               then split into hi/lo), B expanded from L2-resident rows.
-//   warp 4    : TMEM allocation; lane 0 issues tcgen05.mma and commits.
-//   warps 5-8 : epilogue (TMEM lanes 32*(warp%4) ...), two accumulators so
-//               that a tile's epilogue overlaps the next tile's MMAs.
-constexpr int NPROD = 128;
-constexpr int MMA_WARP = 4;
-constexpr int EPI_WARP0 = 5;
-constexpr int NTHREADS = 288;
+//   warps 0-7  : producers.  cp.async of A rows and B columns several chunks
+//                ahead (TF32 A straight into the MMA layout; BF16x3 A into
+//                a raw FP32 ring, then split into hi/lo; B expanded into the
+//                real 2x2 block form at finalise time).
+//   warp 8     : TMEM allocation; lane 0 issues tcgen05.mma and commits.
+//   warps 9-16 : epilogue, two warps per TMEM lane quadrant (warp % 4), each
+//                draining 32 of the tile's 64 complex columns; two
+//                accumulators so that a tile's epilogue overlaps the next
+//                tile's MMAs.
+constexpr int NPROD = 256;   // warps 0-7
+constexpr int MMA_WARP = 8;
+constexpr int EPI_WARP0 = 9; // warps 9-16: two per TMEM lane quadrant
+constexpr int NEPI = 256;
+constexpr int NTHREADS = 544;
 constexpr int ACC_COLS = 128;
 constexpr int TMEM_COLS2 = 256;
 
@@ -207,24 +199,29 @@ struct Cfg {
     static constexpr int SLOT_A = TBM * TBKR * 4;
     static constexpr int SLOT_B = TBNR * TBKR * 4;
     static constexpr int SLOT_RAW = PREC == 2 ? TBM * TBK * 8 : 0;
+    static constexpr int SLOT_BRAW = TBN * TBK * 8;  // raw complex64 B chunk, per-thread pieces
     static constexpr int OFF_B = STAGES * SLOT_A;
     static constexpr int OFF_RAW = OFF_B + STAGES * SLOT_B;
-    static constexpr int OFF_CTRL = OFF_RAW + STAGES * SLOT_RAW;
+    static constexpr int OFF_BRAW = OFF_RAW + STAGES * SLOT_RAW;
+    static constexpr int OFF_CTRL = OFF_BRAW + STAGES * SLOT_BRAW;
 };
 
 struct EpiMeta {
     int64_t cbase[TBN];
+    int64_t inst[TBN];
+    float sc[TBN];
     int32_t eb[TBN];
+    int32_t EB[TBN];
     uint32_t mx[TBN];
-    int32_t ea;
-    int32_t pad;
+    int32_t ea, EA;
+    int32_t mt, pad;
 };
 
 struct Ctrl {
     uint64_t full[4], empty[4], tfull[2], tempty[2];
     uint32_t tmem_base;
     int32_t abort_;
-    int32_t epi_stop, epi_fail;  // epilogue-uniform abort decisions
+    int32_t epi_fail[2];  // epilogue-uniform abort decisions, by tile parity
     EpiMeta epi[2];
 };
 
@@ -233,32 +230,9 @@ constexpr size_t smem_bytes() {
     return size_t(Cfg<PREC>::OFF_CTRL) + sizeof(Ctrl) + 128;
 }
 
-struct TileInfo {
-    int64_t i0, icount, c0, m0;
-    int mt;
-};
-
-__device__ __forceinline__ TileInfo decode_tile(const StepDesc &d, int64_t T, int64_t mtiles) {
-    TileInfo t;
-    const int64_t e = T / mtiles;
-    t.mt = int(T - e * mtiles);
-    const int64_t packed = d.ctab[e];
-    const int64_t g = packed >> 20;
-    t.i0 = d.gfirst[g];
-    t.icount = d.gfirst[g + 1] - t.i0;
-    t.c0 = (packed & 0xfffff) * TBN;
-    t.m0 = int64_t(t.mt) * TBM;
-    return t;
-}
-
-__device__ __forceinline__ int64_t a_instance(const StepDesc &d, int64_t i) {
-    const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
-    return int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
-}
-
-__device__ __forceinline__ int64_t b_instance(const StepDesc &d, int64_t i) {
-    const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
-    return int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
+// tile T of a step: column-tile record e = T / mtiles, row tile T % mtiles
+__device__ __forceinline__ int4 tile_rec(const StepDesc &d, int64_t T, int64_t mtiles) {
+    return __ldg(d.trec + T / mtiles);
 }
 
 template <int PREC>
@@ -290,7 +264,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&X.tfull[a], 1);
-            mbar_init(&X.tempty[a], 128);
+            mbar_init(&X.tempty[a], NEPI);
         }
         X.abort_ = *reinterpret_cast<volatile int32_t *>(err);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -305,17 +279,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         *abort_flag = 1;
     };
 
-    if (warp < 4) {
+    if (warp < NPROD / 32) {
         // ------------------------------------------------------------ producers
         const int kq = (tid >> 3) & 3;
-        int rowj[4];
+        int rowj[2];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) rowj[j] = ((tid >> 5) + 4 * j) * 8 + (tid & 7);
-        const int bcol = tid & 63;
+        for (int j = 0; j < 2; ++j) rowj[j] = ((tid >> 5) + 8 * j) * 8 + (tid & 7);
+        const int bcol = tid & 63, kqb = tid >> 6;
         const float2 *abase[2] = {nullptr, nullptr};
-        int64_t offA[2][4];
-        int64_t bbase = -1;
+        int64_t offA[2][2];
+        int64_t bbase[2] = {-1, -1};
         int64_t issued = 0;
+        // metadata pipeline: records two tiles ahead, B instance one tile ahead
+        int4 rec_pf[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
+        int ib_pf = 0;
+        auto tile_of = [&](int64_t l) { return int64_t(blockIdx.x) + l * gridDim.x; };
+        auto col_inst = [&](const int4 &r) -> int64_t {  // instance of this thread's B column, or -1
+            const int64_t gc = int64_t(r.w) + bcol;
+            return gc < (int64_t(r.y) << d.nb) ? int64_t(r.x) + (gc >> d.nb) : -1;
+        };
+        if (my_tiles > 0) {
+            rec_pf[0] = tile_rec(d, tile_of(0), mtiles);
+            if (my_tiles > 1) rec_pf[1] = tile_rec(d, tile_of(1), mtiles);
+            const int64_t ci = col_inst(rec_pf[0]);
+            ib_pf = ci >= 0 ? __ldg(d.instab + ci).y : 0;
+        }
         for (int64_t gch = 0; gch < total_chunks && !*abort_flag; ++gch) {
             while (issued < total_chunks && issued <= gch + C::LOOK) {
                 const int64_t l = issued / nch;
@@ -323,13 +311,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int slot = int(issued % C::STAGES);
                 const uint32_t ph = uint32_t(issued / C::STAGES) & 1u;
                 if (c == 0) {
-                    const TileInfo t = decode_tile(d, blockIdx.x + l * gridDim.x, mtiles);
-                    abase[l & 1] = d.A + a_instance(d, t.i0) * d.sA;
+                    const int4 r = rec_pf[l & 1];
+                    const int64_t m0 = (tile_of(l) % mtiles) * TBM;
+                    abase[l & 1] = d.A + int64_t(r.z) * d.sA;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int64_t m = t.m0 + rowj[j];
+                    for (int j = 0; j < 2; ++j) {
+                        const int64_t m = m0 + rowj[j];
                         offA[l & 1][j] = m < M ? dep(m, d.pAm, d.mb) : -1;
                     }
+                    const int64_t ci = col_inst(r);
+                    bbase[l & 1] = ci >= 0 ? int64_t(ib_pf) * d.sB + dep((int64_t(r.w) + bcol) & (N - 1), d.pBn, d.nb) : -1;
+                    // prefetch: the B instance of tile l+1, the record of tile l+2
+                    if (l + 1 < my_tiles) {
+                        const int64_t cn = col_inst(rec_pf[(l + 1) & 1]);
+                        ib_pf = cn >= 0 ? __ldg(d.instab + cn).y : 0;
+                    }
+                    if (l + 2 < my_tiles) rec_pf[l & 1] = tile_rec(d, tile_of(l + 2), mtiles);
                 }
                 if (!mbar_wait(&X.empty[slot], ph ^ 1u)) {
                     give_up();
@@ -337,7 +334,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 const float2 *ab = abase[l & 1];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 2; ++j) {
                     const int64_t oa = offA[l & 1][j];
                     const int k = c * TBK + 4 * kq;
                     const bool v = oa >= 0 && k + 3 < K;
@@ -347,35 +344,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         cp_async16(dst + kmaj_off(rowj[j], 8 * kq, 4), src, v ? 16 : 0);
                         cp_async16(dst + kmaj_off(rowj[j], 8 * kq + 4, 4), v ? src + 2 : ab, v ? 16 : 0);
                     } else {
-                        const uint32_t dst = smem_u32(sm + C::OFF_RAW + slot * C::SLOT_RAW) + uint32_t(tid * 4 + j) * 32;
+                        const uint32_t dst = smem_u32(sm + C::OFF_RAW + slot * C::SLOT_RAW) + uint32_t(tid * 2 + j) * 32;
                         cp_async16(dst, src, v ? 16 : 0);
                         cp_async16(dst + 16, v ? src + 2 : ab, v ? 16 : 0);
                     }
+                }
+                {  // B: this thread's column, k quad kqb
+                    const int64_t bb = bbase[l & 1];
+                    const uint32_t dst = smem_u32(sm + C::OFF_BRAW + slot * C::SLOT_BRAW) + uint32_t(tid) * 32;
+                    const int k = c * TBK + 4 * kqb;
+                    const bool v = bb >= 0 && k + 3 < K;
+                    const float2 *src = v ? d.B + bb + k : d.B;
+                    cp_async16(dst, src, v ? 16 : 0);
+                    cp_async16(dst + 16, v ? src + 2 : d.B, v ? 16 : 0);
                 }
                 cp_async_commit();
                 ++issued;
             }
             if (*abort_flag) break;
             cp_async_wait(int(issued - gch - 1));
-            const int64_t l = gch / nch;
-            const int c = int(gch - l * nch);
             const int slot = int(gch % C::STAGES);
-            if (c == 0) {
-                const TileInfo t = decode_tile(d, blockIdx.x + l * gridDim.x, mtiles);
-                const int64_t gc = t.c0 + bcol;
-                bbase = -1;
-                if (gc < (t.icount << d.nb)) {
-                    const int64_t inst = t.i0 + (gc >> d.nb);
-                    bbase = b_instance(d, inst) * d.sB + dep(gc & (N - 1), d.pBn, d.nb);
-                }
-            }
             if (PREC == 2) {
                 uint8_t *bh = sm + slot * C::SLOT_A, *bl = bh + TBM * TBKR * 2;
                 const uint8_t *raw = sm + C::OFF_RAW + slot * C::SLOT_RAW;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float4 v0 = *reinterpret_cast<const float4 *>(raw + (tid * 4 + j) * 32);
-                    const float4 v1 = *reinterpret_cast<const float4 *>(raw + (tid * 4 + j) * 32 + 16);
+                for (int j = 0; j < 2; ++j) {
+                    const float4 v0 = *reinterpret_cast<const float4 *>(raw + (tid * 2 + j) * 32);
+                    const float4 v1 = *reinterpret_cast<const float4 *>(raw + (tid * 2 + j) * 32 + 16);
                     const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                     __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
@@ -387,16 +382,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     *reinterpret_cast<uint4 *>(bl + kmaj_off(rowj[j], 8 * kq, 2)) = *reinterpret_cast<uint4 *>(lo);
                 }
             }
-            // B: this thread's column, k quads (tid >> 6) and (tid >> 6) + 2
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int kqb = (tid >> 6) + 2 * j;
-                float2 t4[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int k = c * TBK + 4 * kqb + q;
-                    t4[q] = (bbase >= 0 && k < K) ? __ldg(d.B + bbase + k) : make_float2(0.f, 0.f);
-                }
+            // B: expand this thread's prefetched piece into the MMA layout
+            const uint8_t *braw = sm + C::OFF_BRAW + slot * C::SLOT_BRAW + tid * 32;
+            {
+                const float4 p0 = *reinterpret_cast<const float4 *>(braw);
+                const float4 p1 = *reinterpret_cast<const float4 *>(braw + 16);
+                const float2 t4[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
+                                      make_float2(p1.z, p1.w)};
                 const float r0[8] = {t4[0].x, -t4[0].y, t4[1].x, -t4[1].y, t4[2].x, -t4[2].y, t4[3].x, -t4[3].y};
                 const float r1[8] = {t4[0].y, t4[0].x, t4[1].y, t4[1].x, t4[2].y, t4[2].x, t4[3].y, t4[3].x};
                 uint8_t *base = sm + C::OFF_B + slot * C::SLOT_B;
@@ -481,67 +473,119 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int e = tid - EPI_WARP0 * 32;  // 0..127
-        const int lanegrp = warp & 3;        // TMEM lanes 32*lanegrp ...
+        const int e = tid - EPI_WARP0 * 32;     // 0..255
+        const int lanegrp = warp & 3;           // TMEM lanes 32*lanegrp ...
+        const int half = (warp - EPI_WARP0) >> 2;  // complex columns 32*half ...
         const int row = lanegrp * 32 + lane;
+        // metadata of tile l into X.epi[l & 1] (threads 0..63: one column each)
+        auto meta = [&](int64_t l) {
+            EpiMeta &em = X.epi[l & 1];
+            const int64_t T = int64_t(blockIdx.x) + l * gridDim.x;
+            const int4 r = tile_rec(d, T, mtiles);
+            if (e == 0) {
+                em.ea = d.mxA ? exp_of(__ldg(d.mxA + r.z)) : 0;
+                em.EA = __ldg(d.EA + r.z);
+                em.mt = int(T % mtiles);
+            }
+            if (e < TBN) {
+                const int64_t gc = int64_t(r.w) + e;
+                em.mx[e] = 0;
+                if (gc < (int64_t(r.y) << d.nb)) {
+                    const int64_t inst = int64_t(r.x) + (gc >> d.nb);
+                    const int ib = __ldg(d.instab + inst).y;
+                    em.inst[e] = inst;
+                    em.cbase[e] = inst * d.sC + dep(gc & (N - 1), d.pCn, d.nb);
+                    em.eb[e] = d.mxB ? exp_of(__ldg(d.mxB + ib)) : 0;
+                    em.EB[e] = __ldg(d.EB + ib);
+                } else {
+                    em.inst[e] = -1;
+                    em.cbase[e] = -1;
+                    em.eb[e] = 0;
+                    em.EB[e] = 0;
+                }
+            }
+        };
+        // per-column scale 2^-(ea + eb), once the tile's exponents are in place
+        auto scales = [&](int64_t l) {
+            EpiMeta &em = X.epi[l & 1];
+            if (e < TBN) em.sc[e] = pow2f(-(em.ea + em.eb[e]));
+        };
+        if (my_tiles > 0) meta(0);
+        if (e == 0) X.epi_fail[0] = X.epi_fail[1] = 0;
+        named_sync(1, NEPI);
+        if (my_tiles > 0) scales(0);
         for (int64_t l = 0; l < my_tiles; ++l) {
             const int acc = int(l & 1);
             EpiMeta &em = X.epi[acc];
-            const TileInfo t = decode_tile(d, blockIdx.x + l * gridDim.x, mtiles);
-            const int64_t cols = t.icount << d.nb;
-            if (e == 0) {
-                const int64_t ia = a_instance(d, t.i0);
-                em.ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
-                X.epi_stop = *abort_flag;
-                X.epi_fail = 0;
-            }
-            named_sync(1, 128);
-            if (X.epi_stop) break;  // uniform: read after the barrier
-            if (e < TBN) {
-                const int64_t gc = t.c0 + e;
-                em.mx[e] = 0;
-                if (gc < cols) {
-                    const int64_t inst = t.i0 + (gc >> d.nb);
-                    const int n = int(gc & (N - 1));
-                    const int64_t ib = b_instance(d, inst);
-                    em.cbase[e] = inst * d.sC + dep(n, d.pCn, d.nb);
-                    em.eb[e] = d.mxB ? exp_of(d.mxB[ib]) : 0;
-                    if (n == 0 && t.mt == 0) d.EC[inst] = d.EA[a_instance(d, t.i0)] + em.ea + d.EB[ib] + em.eb[e];
-                } else {
-                    em.cbase[e] = -1;
-                    em.eb[e] = 0;
-                }
-            }
-            if (!mbar_wait(&X.tfull[acc], uint32_t(l >> 1) & 1u)) atomicOr(&X.epi_fail, 1);
-            named_sync(1, 128);
-            if (X.epi_fail) {  // uniform
+            if (l + 1 < my_tiles) meta(l + 1);  // overlaps the wait for tile l's accumulator
+            const int64_t m0 = int64_t(em.mt) * TBM;
+            if (!mbar_wait(&X.tfull[acc], uint32_t(l >> 1) & 1u)) atomicOr(&X.epi_fail[acc], 1);
+            if (e == 0 && *abort_flag) atomicOr(&X.epi_fail[acc], 1);
+            named_sync(1, NEPI);
+            if (X.epi_fail[acc]) {  // uniform: read between barriers
                 if (e == 0) give_up();
                 break;
             }
+            if (e == 0) X.epi_fail[acc ^ 1] = 0;  // next tile's slot; its last readers are done
             tc_fence_after();
-            const int64_t m = t.m0 + row;
+            const int64_t m = m0 + row;
             const int64_t offc = m < M ? dep(m, d.pCm, d.mb) : -1;
-#pragma unroll 1
-            for (int cb = 0; cb < TBNR / 16; ++cb) {
-                float v[16];
-                tmem_ld16(tmem + uint32_t(acc * ACC_COLS) + (uint32_t(lanegrp * 32) << 16) + uint32_t(cb * 16), v);
+            // this warp's 32 complex columns = 64 accumulator columns, loaded
+            // with four x16 loads and one wait
+            float v[64];
+            {
+                const uint32_t ta = tmem + uint32_t(acc * ACC_COLS + half * 64) + (uint32_t(lanegrp * 32) << 16);
+                uint32_t r[64];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = cb * 8 + j;
-                    if (offc < 0 || em.cbase[col] < 0) continue;
-                    const float sc = pow2f(-(em.ea + em.eb[col]));
-                    const float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
-                    d.C[em.cbase[col] + offc] = o;
-                    if (d.mxC) atomicMax(&em.mx[col], __float_as_uint(fmaxf(fabsf(o.x), fabsf(o.y))));
+                for (int q = 0; q < 4; ++q)
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(r[16 * q + 0]), "=r"(r[16 * q + 1]), "=r"(r[16 * q + 2]), "=r"(r[16 * q + 3]),
+                          "=r"(r[16 * q + 4]), "=r"(r[16 * q + 5]), "=r"(r[16 * q + 6]), "=r"(r[16 * q + 7]),
+                          "=r"(r[16 * q + 8]), "=r"(r[16 * q + 9]), "=r"(r[16 * q + 10]), "=r"(r[16 * q + 11]),
+                          "=r"(r[16 * q + 12]), "=r"(r[16 * q + 13]), "=r"(r[16 * q + 14]), "=r"(r[16 * q + 15])
+                        : "r"(ta + uint32_t(16 * q)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 64; ++q) v[q] = __uint_as_float(r[q]);
+            }
+            // running max of the current instance's columns; one warp
+            // reduction and one shared atomic per instance run
+            uint32_t tmx = 0;
+            int run_col = half * 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = half * 32 + j;
+                if (d.mxC && j > 0 && em.inst[col] != em.inst[col - 1]) {  // a new instance starts
+                    const uint32_t r = __reduce_max_sync(0xffffffffu, tmx);
+                    if (lane == 0 && r) atomicMax(&em.mx[run_col], r);
+                    tmx = 0;
+                    run_col = col;
                 }
+                const int64_t cb = em.cbase[col];
+                if (offc < 0 || cb < 0) continue;
+                const float sc = em.sc[col];
+                const float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
+                d.C[cb + offc] = o;
+                tmx = max(tmx, __float_as_uint(fmaxf(fabsf(o.x), fabsf(o.y))));
+            }
+            if (d.mxC) {
+                const uint32_t r = __reduce_max_sync(0xffffffffu, tmx);
+                if (lane == 0 && r) atomicMax(&em.mx[run_col], r);
             }
             tc_fence_before();
             mbar_arrive(&X.tempty[acc]);
-            named_sync(1, 128);
-            if (d.mxC && e < TBN && em.cbase[e] >= 0 && em.mx[e]) {
-                const int64_t inst = t.i0 + ((t.c0 + e) >> d.nb);
-                record_max(d.mxC + inst, em.mx[e]);
+            named_sync(1, NEPI);
+            if (e < TBN && em.inst[e] >= 0) {
+                // exponent of the instance, written once (at its n = 0 column, row tile 0)
+                const int64_t gc_n = em.cbase[e] - em.inst[e] * d.sC;  // dep(n) == 0 iff n == 0
+                if (gc_n == 0 && em.mt == 0) d.EC[em.inst[e]] = em.EA + em.ea + em.EB[e] + em.eb[e];
+                // em.mx[e] != 0 only where a run of this instance's columns
+                // starts (instance start, or the second epilogue half)
+                if (d.mxC && em.mx[e]) record_max(d.mxC + em.inst[e], em.mx[e]);
             }
+            if (l + 1 < my_tiles) scales(l + 1);  // meta(l + 1) is visible since the last barrier
+            named_sync(1, NEPI);  // em (this parity) is rewritten by meta(l + 2)
         }
     }
     tc_fence_before();

@@ -333,7 +333,11 @@ __global__ void __launch_bounds__(256) k_step_gemm_simt(const StepDesc d, int ct
             d.C[s_cbase[c] + s_offC[r]] = v;
             mx = max(mx, absmax_bits(v));
         }
-        if (d.mxC) atomicMax(&s_mx[c], mx);
+        if (d.mxC) {  // lanes tn*16 .. tn*16+15 share column c: reduce each half-warp first
+            const unsigned half = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
+            const uint32_t r = __reduce_max_sync(half, mx);
+            if (tm == 0 && r) atomicMax(&s_mx[c], r);
+        }
     }
     if (d.mxC) {
         __syncthreads();

@@ -36,6 +36,8 @@ struct StepDesc {
     int64_t n_groups;
     const int64_t *ctab;          // non-empty column tiles: (group << 20) | tile of 64 columns
     int64_t n_ctab;
+    const int4 *trec;             // per column tile: {first instance, count, A instance, first column}
+    const int2 *instab;           // per output instance: {A instance, B instance}
     int8_t pAm[40];
     int8_t pBn[24];
     int8_t pCm[40];

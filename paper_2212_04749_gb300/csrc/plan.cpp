@@ -574,6 +574,35 @@ struct Builder {
             if (emit) push_upload(p, st.off_groups, st.group_first);
             st.off_col_tiles = take(int64_t(st.col_tiles.size()) * 8);
             if (emit) push_upload(p, st.off_col_tiles, st.col_tiles);
+            // one 16-byte record per column tile and one int32 pair per
+            // output instance, so that a kernel reaches every index it needs
+            // with a single load instead of a chain of dependent ones
+            const Node &nd = p.nodes[st.node];
+            const bool a_left = st.a == nd.left;
+            const std::vector<int32_t> &sgA = a_left ? nd.sigL : nd.sigR, &otA = a_left ? nd.outL : nd.outR;
+            const std::vector<int32_t> &sgB = a_left ? nd.sigR : nd.sigL, &otB = a_left ? nd.outR : nd.outL;
+            const int64_t noA = p.nodes[st.a].n_out, noB = p.nodes[st.b].n_out;
+            st.off_tile_rec = take(int64_t(st.col_tiles.size()) * 16);
+            st.off_inst_ab = take(nd.n_inst * 8);
+            if (emit) {
+                std::vector<int32_t> ab(2 * nd.n_inst);
+                for (int64_t i = 0; i < nd.n_inst; ++i) {
+                    const int64_t sg = i / nd.n_out, bt = i % nd.n_out;
+                    ab[2 * i] = int32_t(int64_t(sgA[sg]) * noA + otA[bt]);
+                    ab[2 * i + 1] = int32_t(int64_t(sgB[sg]) * noB + otB[bt]);
+                }
+                std::vector<int32_t> rec(4 * st.col_tiles.size());
+                for (size_t t = 0; t < st.col_tiles.size(); ++t) {
+                    const int64_t g = st.col_tiles[t] >> 20, ct = st.col_tiles[t] & 0xfffff;
+                    const int64_t i0 = st.group_first[g];
+                    rec[4 * t] = int32_t(i0);
+                    rec[4 * t + 1] = int32_t(st.group_first[g + 1] - i0);
+                    rec[4 * t + 2] = ab[2 * i0];
+                    rec[4 * t + 3] = int32_t(ct * 64);
+                }
+                push_upload(p, st.off_inst_ab, ab);
+                push_upload(p, st.off_tile_rec, rec);
+            }
         }
         // transient intermediates: first-fit over one full pass of the steps
         Arena ar;

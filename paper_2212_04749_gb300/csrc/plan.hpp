@@ -99,6 +99,8 @@ struct Step {
     int64_t off_groups = -1;           // workspace offset of group_first
     std::vector<int64_t> col_tiles;    // non-empty (group, 64-column tile) pairs: g * 2^20 + tile
     int64_t off_col_tiles = -1;
+    int64_t off_tile_rec = -1;         // per column tile: {first instance, count, A instance, first column}
+    int64_t off_inst_ab = -1;          // per output instance: {A instance, B instance} (int32 pairs)
     int kernel = 0;          // 0 = per-row SIMT, 1 = tiled SIMT GEMM, 2 = tensor-core GEMM
     double flops = 0;        // executed per pass: 8 * n_inst * 2^{mb+kb+nb}
     double bytes = 0;        // A + B reads and C write per pass

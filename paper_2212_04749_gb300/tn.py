@@ -66,7 +66,8 @@ class tn_step_info(ctypes.Structure):
                 ("n_inst", ctypes.c_int64), ("n_inst_a", ctypes.c_int64), ("n_inst_b", ctypes.c_int64),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("runs", ctypes.c_double),
                 ("a_run_m", ctypes.c_int32), ("a_run_k", ctypes.c_int32), ("b_run_k", ctypes.c_int32),
-                ("b_run_n", ctypes.c_int32), ("n_groups", ctypes.c_int64)]
+                ("b_run_n", ctypes.c_int32), ("n_groups", ctypes.c_int64),
+                ("c_pos_m", ctypes.c_int8 * 40), ("c_pos_n", ctypes.c_int8 * 24)]
 
 
 _lib = None
@@ -219,7 +220,14 @@ class Plan:
         n = self.info["n_steps"]
         arr = (tn_step_info * max(n, 1))()
         _check(self._lib.tn_plan_steps(self.h, arr, n))
-        return [{f: getattr(arr[i], f) for f, _ in tn_step_info._fields_} for i in range(n)]
+        out = []
+        for i in range(n):
+            r = {}
+            for f, _ in tn_step_info._fields_:
+                v = getattr(arr[i], f)
+                r[f] = [x for x in v if x >= 0] if f.startswith("c_pos") else v
+            out.append(r)
+        return out
 
     def tn_plan_bind(self, workspace, nbytes=None, stream=None):
         if nbytes is None:
