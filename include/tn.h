@@ -87,7 +87,10 @@ typedef struct {
                                  one GEMM against a pre-contracted operator */
     int32_t fuse_max_bits;    /* d^t: largest K or N bit count of a fused
                                  chain operator (SM Sec. V.C); 0: default 7 */
-    int32_t reserved[10];
+    int32_t graphs;           /* 1: tn_contract captures its launch sequence in
+                                 a CUDA graph on first use of a (precision,
+                                 batch range, output buffer) and replays it */
+    int32_t reserved[9];
 } tn_options;
 
 typedef struct {

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -42,6 +43,20 @@ struct PlanObj {
     size_t ev_used = 0;
     std::vector<int32_t> step_kernel;     // kernel family each step ran last (0 row, 1 SIMT GEMM, 2 TC GEMM)
     std::vector<int32_t> kernel_override; // per step: -1 plan choice, 0 row, 1 GEMM
+    struct GraphKey {
+        int precision;
+        int64_t lo, hi;
+        const double *amps;
+        bool operator<(const GraphKey &o) const {
+            return std::tie(precision, lo, hi, amps) < std::tie(o.precision, o.lo, o.hi, o.amps);
+        }
+    };
+    std::map<GraphKey, cudaGraphExec_t> graphs;  // captured tn_contract launch sequences
+    cudaStream_t cap_stream = nullptr;           // private stream the sequences are captured on
+    void drop_graphs() {
+        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+        graphs.clear();
+    }
     int64_t last_batches = 0;
 };
 
@@ -323,6 +338,8 @@ int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream) {
         return set_err(TN_ENOMEM, "tn_plan_bind: workspace has " + std::to_string(bytes) + " bytes, plan needs " +
                                       std::to_string(o->P.ws_bytes));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    CU(tnk::init_kernels());
+    o->drop_graphs();
     o->ws = static_cast<uint8_t *>(workspace);
     o->ws_bytes = bytes;
     for (auto &u : o->P.uploads) {
@@ -352,12 +369,43 @@ int tn_contract(tn_plan_t plan, int precision, int64_t batch_lo, int64_t batch_h
     const float2 *root = at<const float2>(o, R.buf.data);
     const int32_t *E = at<const int32_t>(o, R.buf.E);
     const int32_t *uniq = at<const int32_t>(o, P.off_uniq);
-    int rc = run_batches(o, precision, batch_lo, batch_hi, st, [&](int64_t) -> int {
-        cudaError_t e = tnk::launch_accumulate(root, E, uniq, P.k, R.n_sig, R.n_out, amps, st);
-        if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("accumulate: ") + cudaGetErrorString(e));
+    auto enqueue = [&]() {
+        return run_batches(o, precision, batch_lo, batch_hi, st, [&](int64_t) -> int {
+            cudaError_t e = tnk::launch_accumulate(root, E, uniq, P.k, R.n_sig, R.n_out, amps, st);
+            if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("accumulate: ") + cudaGetErrorString(e));
+            return TN_OK;
+        });
+    };
+    if (!P.opt.graphs || o->profile) {
+        if (int rc = enqueue()) return rc;
+        g_err.clear();
         return TN_OK;
-    });
-    if (rc) return rc;
+    }
+    const PlanObj::GraphKey key{precision, batch_lo, batch_hi, amps};
+    auto it = o->graphs.find(key);
+    if (it == o->graphs.end()) {
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); nothing runs during capture
+        if (!o->cap_stream) CU(cudaStreamCreateWithFlags(&o->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaStream_t user = st;
+        st = o->cap_stream;
+        CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue();
+        const cudaError_t ec = cudaStreamEndCapture(st, &g);
+        st = user;
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return set_err(TN_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ec));
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return set_err(TN_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+        it = o->graphs.emplace(key, ex).first;
+    }
+    CU(cudaGraphLaunch(it->second, st));
     g_err.clear();
     return TN_OK;
 }
@@ -425,10 +473,13 @@ int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream
     uint8_t *prev_ws = o->ws;
     const size_t prev_bytes = o->ws_bytes;
     int32_t *prev_flag = o->err_flag;
+    const int32_t prev_graphs = o->P.opt.graphs;
+    o->P.opt.graphs = 0;  // every call re-uploads the tables: nothing to replay
     int rc = tn_plan_bind(plan, scratch, (size_t)TN_STATIC_SCRATCH_BYTES, stream);
     if (rc == TN_OK) rc = tn_contract(plan, precision, 0, o->P.n_batches, amps, stream);
     if (rc == TN_OK) rc = tn_plan_check(plan, stream);
     const std::string msg = g_err;
+    o->P.opt.graphs = prev_graphs;
     o->ws = prev_ws;
     o->ws_bytes = prev_bytes;
     o->err_flag = prev_flag;
@@ -449,6 +500,7 @@ int tn_plan_set_kernel(tn_plan_t plan, int32_t step, int32_t kernel) {
         return set_err(TN_EINVAL, "tn_plan_set_kernel: per-row kernel needs N <= 16 and K*N <= 256");
     o->kernel_override.resize(P.steps.size(), -1);
     o->kernel_override[step] = kernel;
+    o->drop_graphs();
     return TN_OK;
 }
 
@@ -493,6 +545,8 @@ int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t *kernel, int32_t n) {
 void tn_destroy(tn_plan_t plan) {
     if (!plan) return;
     PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    o->drop_graphs();
+    if (o->cap_stream) cudaStreamDestroy(o->cap_stream);
     for (cudaEvent_t e : o->ev) cudaEventDestroy(e);
     delete o;
 }

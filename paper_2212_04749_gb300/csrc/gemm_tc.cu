@@ -607,34 +607,29 @@ namespace {
 int g_num_sms = 0;
 }
 
+cudaError_t init_kernels() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_step_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_step_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2>());
+}
+
 cudaError_t launch_step_gemm_tc(const StepDesc &d, int precision, int32_t *err, cudaStream_t s) {
     if (!gemm_tc_supports(d)) return cudaErrorNotSupported;
+    if (g_num_sms <= 0) return cudaErrorNotReady;  // init_kernels() not called
     const int64_t M = int64_t(1) << d.mb;
     const int64_t mtiles = (M + TBM - 1) / TBM;
     const int64_t tiles = d.n_ctab * mtiles;
     if (tiles <= 0) return cudaSuccess;
-    if (g_num_sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 148;
-    }
     const int64_t grid = tiles < g_num_sms ? tiles : g_num_sms;
-    if (precision == 1) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_step_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
-            attr = true;
-        }
+    if (precision == 1)
         k_step_gemm_tc<1><<<dim3((unsigned)grid), NTHREADS, smem_bytes<1>(), s>>>(d, mtiles, err);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_step_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2>());
-            attr = true;
-        }
+    else
         k_step_gemm_tc<2><<<dim3((unsigned)grid), NTHREADS, smem_bytes<2>(), s>>>(d, mtiles, err);
-    }
     return cudaGetLastError();
 }
 

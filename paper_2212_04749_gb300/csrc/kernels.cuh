@@ -69,6 +69,9 @@ cudaError_t launch_xeb(const double *amps, int64_t k, double scale, double *out,
 // Tensor-core path (gemm_tc.cu).  precision: 1 = TF32, 2 = BF16x3.
 // Returns cudaErrorNotSupported for shapes it does not take.
 bool gemm_tc_supports(const StepDesc &d);
+// One-time per-device setup (function attributes, SM count); call outside
+// any stream capture.
+cudaError_t init_kernels();
 cudaError_t launch_step_gemm_tc(const StepDesc &d, int precision, int32_t *err_flag, cudaStream_t s);
 
 }  // namespace tnk

@@ -19,6 +19,7 @@ extern "C" void tn_options_default(tn_options *opt) {
     opt->rescale = 1;
     opt->fuse = 0;
     opt->fuse_max_bits = 7;
+    opt->graphs = 1;
 }
 
 namespace tnp {

@@ -45,7 +45,7 @@ class tn_circuit(ctypes.Structure):
 class tn_options(ctypes.Structure):
     _fields_ = [("workspace_limit", ctypes.c_int64), ("slice_batch_log2", ctypes.c_int32),
                 ("rescale", ctypes.c_int32), ("fuse", ctypes.c_int32), ("fuse_max_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class tn_plan_info(ctypes.Structure):

@@ -7,8 +7,11 @@ Seeds: circuit 1000+i, bitstrings 2000+i, tree search 3000+i for workload i.
 * ``grid5x6_m14``  : 30 qubits, 5x6 grid, 14 cycles, 171 fSim gates,
                      4096 bitstrings, 10 sliced bond edges (2^10 slices) chosen
                      with the largest per-instance intermediate capped at 2^28.
-* ``grid6x7_m16``  : 42 qubits, 6x7 grid, 16 cycles, 284 fSim gates,
-                     1024 bitstrings, 14 sliced bond edges (2^14 slices).
+* ``grid6x7_m10``  : 42 qubits, 6x7 grid, 10 cycles (ABCDCDABAB), 178 fSim
+                     gates, 1024 bitstrings, 14 sliced bond edges (2^14
+                     slices).  At 16 cycles the seeded search's trees keep
+                     per-slice intermediates of rank 39 after 14 slices
+                     (~6e18 flops), beyond one GPU; 10 cycles gives rank 23.
 * ``diamond53_m12``: 53 qubits, 54-site diamond with one dead site,
                      12 cycles, 258 fSim gates, 8192 bitstrings, sliced until
                      the largest per-instance intermediate has <= 2^32 entries.
@@ -41,7 +44,7 @@ class WorkloadSpec:
 WORKLOADS = {
     "grid3x4_m8": WorkloadSpec("grid3x4_m8", 1, "grid3x4", 8, 64, None, None),
     "grid5x6_m14": WorkloadSpec("grid5x6_m14", 2, "grid5x6", 14, 4096, 10, 28),
-    "grid6x7_m16": WorkloadSpec("grid6x7_m16", 3, "grid6x7", 16, 1024, 14, None),
+    "grid6x7_m10": WorkloadSpec("grid6x7_m10", 3, "grid6x7", 10, 1024, 14, None, trials=8),
     "diamond53_m12": WorkloadSpec("diamond53_m12", 4, "diamond53", 12, 8192, None, 32),
 }
 

@@ -139,3 +139,24 @@ def test_grid5x6_fp32_matches_stored_state_vector():
     got, p = run_plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced)
     assert p.info["n_sliced"] == 10
     assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_graph_replay_equals_eager_bitwise():
+    from gpu_helpers import require_cuda
+    torch, tn = require_cuda()
+    w = make_workload("grid3x4_m8")
+    sl = choose_slices(w.struct, w.tree, 64, n_sliced=3)
+    out = {}
+    for graphs in (0, 1):
+        p = tn.Plan(w.circuit, w.bits, w.tree.ssa, sl, slice_batch_log2=1, graphs=graphs)
+        ws = torch.empty(p.info["workspace_bytes"], dtype=torch.uint8, device="cuda")
+        p.tn_plan_bind(ws)
+        res = []
+        for _ in range(3):  # capture, then replays
+            amps = torch.zeros(2 * 64, dtype=torch.float64, device="cuda")
+            p.tn_contract(amps, "fp32")
+            torch.cuda.synchronize()
+            res.append(amps.cpu().numpy().copy())
+        out[graphs] = res
+    for r in out[0] + out[1]:
+        assert np.array_equal(r, out[0][0])

@@ -1,0 +1,54 @@
+"""The larger workloads against stored CPU-oracle values.
+
+* grid6x7_m10 (42 qubits, 10 cycles, 2^14 slices): 32 seeded slices x 16
+  seeded bitstrings of per-slice partial amplitudes from the complex128
+  tensor-network oracle, in FP32, BF16x3 and TF32.
+* diamond53_m12 (53 qubits, 12 cycles, 8192 bitstrings): the full
+  contraction on the GPU, 16 seeded amplitudes compared with the oracle.
+"""
+
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import rel_l2, run_plan, run_slices
+from rqc import make_workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16x3": 1e-3, "tf32": 1e-2}
+
+
+def _mg():
+    spec = importlib.util.spec_from_file_location(
+        "make_golden", os.path.join(os.path.dirname(__file__), "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    return mg
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32"])
+def test_grid6x7_sampled_slices(prec):
+    mg = _mg()
+    rec = mg.read_json(mg.slices_path("grid6x7_m10"))
+    w = make_workload("grid6x7_m10")
+    assert rec["inputs_sha256"] == mg.input_digest(w.circuit, w.bits)
+    bits = w.bits[rec["rows"]]
+    got = run_slices(w.circuit, bits, rec["tree_ssa"], rec["sliced_edges"], rec["slice_ids"], precision=prec)
+    err = rel_l2(got, rec["partials"])
+    print(f"grid6x7_m10 {prec}: rel-L2 over {got.size} partials {err:.3e}")
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_diamond53_sampled_amplitudes(prec):
+    mg = _mg()
+    rec = mg.read_json(mg.sample_path("diamond53_m12"))
+    w = make_workload("diamond53_m12")
+    assert rec["inputs_sha256"] == mg.input_digest(w.circuit, w.bits)
+    got, p = run_plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, precision=prec, workspace_limit=160 << 30)
+    err = rel_l2(got[rec["rows"]], rec["amplitudes"])
+    print(f"diamond53_m12 {prec}: rel-L2 over {len(rec['rows'])} sampled amplitudes {err:.3e}")
+    assert err <= TOL[prec], err

@@ -63,7 +63,7 @@ def test_diamond_has_53_qubits_with_nearest_neighbour_couplers():
 
 
 @pytest.mark.parametrize("name,n2q", [("grid3x4_m8", 34), ("grid5x6_m14", 171),
-                                      ("grid6x7_m16", 284), ("diamond53_m12", 258)])
+                                      ("grid6x7_m10", 178), ("diamond53_m12", 258)])
 def test_workload_gate_counts(name, n2q):
     from rqc.configs import WORKLOADS, _layout
     spec = WORKLOADS[name]
