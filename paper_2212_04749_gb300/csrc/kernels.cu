@@ -4,9 +4,10 @@
 //                    tensors with output legs projected on the bitstrings'
 //                    values and sliced legs on the slice's values)
 //   k_step_row       one pairwise step C = A (x) B with a small B operand
-//                    (K*N <= 64): one thread per row m of A, the B block of the
-//                    instance in shared memory; the bandwidth-bound
-//                    "high-rank x low-rank" contraction of SM Sec. V.A
+//                    (N <= 16, K*N <= 256), grouped by shared A instance: each
+//                    A row is read once and multiplied by every B block of
+//                    its group; the bandwidth-bound "high-rank x low-rank"
+//                    contraction of SM Sec. V.A
 //   k_step_gemm_simt tiled complex GEMM with gathered (bit-permuted) operand
 //                    loads, FP32 FMA; the plain FP32 form of big x big steps
 //   k_accumulate     amp[p] += sum over the batch's slices of the root
@@ -72,149 +73,220 @@ __global__ void k_fill(const FillJobD *__restrict__ jobs, int64_t njobs, const L
 }
 
 constexpr int ROW_THREADS = 256;
+constexpr int ROW_SB = 2048;  // staged B entries (complex) per block: 16 KB
+constexpr int ROW_CH = 32;    // most instances staged at once
 
-// Small-rank step (N = 2^NB <= 16, K*N <= 256): the warp-shuffle kernel.
-// Each row's K-contiguous run of A is split over L = min(8, K/2) lanes that
-// load 16 bytes (2 complex) at a time, so every warp load covers runs of
-// L x 16 contiguous bytes; the partial products of the N outputs are summed
-// across the row's L lanes with xor-shuffles.  R = 32 / L rows per warp
-// pass, rows_per_block rows per block (whole rows; when the block lies
-// inside one instance its B is staged in shared memory and its max-|x|
-// word is recorded once).
-template <int NB>
-__global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int rows_per_block) {
+// Small-rank step (N = 2^NB <= 16, K*N <= 256), grouped: the output
+// instances that read one A instance (a group) are computed together, so
+// every A row is read once and multiplied by each of the group's B blocks.
+// A row's K-contiguous run (rows are affine: A + m*K) is split over
+// L = min(8, K/2) lanes holding KL = K/L complex values each in registers,
+// loaded 16 bytes at a time; each output's partial products are summed over
+// the row's L lanes with xor-shuffles.  R = 32/L rows per warp pass.
+//   uniform (M >= 8R): a block = rows_per_block rows of one group; the
+//     group's B blocks (column-affine: K*N contiguous complex each) are
+//     staged in shared memory, ROW_SB entries at a time; max-|x| words and
+//     exponents are recorded once per instance.
+//   small instances (M < 8R): a block = rows_per_block consecutive rows of
+//     consecutive groups; B comes through the L1 cache.
+template <int NB, int KL>
+__global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int rows_per_block, int64_t mblocks) {
     constexpr int N = 1 << NB;
-    __shared__ int8_t s_pAm[40], s_pCm[40];
-    __shared__ int64_t s_offBn[16], s_offCn[16];
-    __shared__ int64_t s_mloA[256], s_mloC[256];
-    __shared__ float2 s_B[256];
-    __shared__ int64_t s_hiA, s_hiC, s_ia, s_ib;
-    __shared__ int s_ea, s_eb;
+    __shared__ int8_t s_pCm[40];
+    __shared__ int64_t s_offCn[N];
+    __shared__ int64_t s_mloC[256];
+    __shared__ __align__(16) float2 s_B[ROW_SB];
+    __shared__ int64_t s_ib[ROW_CH];
+    __shared__ int32_t s_e[ROW_CH], s_EC[ROW_CH];
+    __shared__ uint32_t s_mx[ROW_CH];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = 1 << d.kb;
+    const int KN = K * N;
     const int mb = d.mb;
     const int64_t M = int64_t(1) << mb;
-    const int64_t total = d.nInst << mb;
-    if (tid < 40) {
-        s_pAm[tid] = d.pAm[tid];
-        s_pCm[tid] = d.pCm[tid];
-    }
-    if (tid < N) {
-        s_offBn[tid] = dep(tid, d.pBn, NB);
-        s_offCn[tid] = dep(tid, d.pCn, NB);
-    }
-    __syncthreads();
-    const int lob = mb < 8 ? mb : 8;
-    {
-        const int lo = tid & ((1 << lob) - 1);
-        s_mloA[tid] = dep(lo, s_pAm, lob);
-        s_mloC[tid] = dep(lo, s_pCm, lob);
-    }
-    const int64_t r0 = int64_t(blockIdx.x) * rows_per_block;
-    const bool uniform = M >= rows_per_block;  // the block lies inside one instance
-    if (uniform && tid == 0 && r0 < total) {
-        const int64_t i = r0 >> mb;
-        const int64_t sig = i / d.nOut, beta = i - sig * d.nOut;
-        s_ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
-        s_ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
-        s_ea = d.mxA ? exp_of(d.mxA[s_ia]) : 0;
-        s_eb = d.mxB ? exp_of(d.mxB[s_ib]) : 0;
-    }
-    __syncthreads();
-    if (uniform && r0 < total) {
-        for (int e = tid; e < K * N; e += ROW_THREADS) {
-            const int k = e >> NB, n = e & (N - 1);
-            s_B[e] = d.B[s_ib * d.sB + k + s_offBn[n]];
-        }
-        __syncthreads();
-    }
-    const int L = K >= 16 ? 8 : (K >= 2 ? K / 2 : 1);  // lanes per row
-    const int R = 32 / L;                              // rows per warp pass
+    const int L = K >= 16 ? 8 : (K >= 2 ? K / 2 : 1);
+    const int R = 32 / L;
     const int sub = lane / L, kl = lane % L;
     const int passes = rows_per_block / (8 * R);
-    uint32_t mx_run = 0;  // uniform blocks: max over every row of the block
-    for (int it = 0; it < passes; ++it) {
-        const int64_t gid = r0 + (int64_t(it) * 8 + warp) * R + sub;
-        const bool valid = gid < total;
-        const int64_t g = valid ? gid : r0;
-        const int64_t i = g >> mb;
-        const int64_t m = g & (M - 1);
-        int64_t ia, ib;
-        int ea, eb;
-        const float2 *Bp = nullptr;
-        if (uniform) {
-            ia = s_ia;
-            ib = s_ib;
-            ea = s_ea;
-            eb = s_eb;
+    if (tid < 40) s_pCm[tid] = d.pCm[tid];
+    if (tid < N) s_offCn[tid] = dep(tid, d.pCn, NB);
+    __syncthreads();
+    {
+        const int lob = mb < 8 ? mb : 8;
+        s_mloC[tid] = dep(tid & ((1 << lob) - 1), s_pCm, lob);
+    }
+    __syncthreads();
+
+    // this lane's KL values of row m of A instance ia
+    auto load_row = [&](float2 (&a)[KL], int64_t ia, int64_t m, bool valid) {
+        const float2 *A = d.A + ia * d.sA + (m << d.kb);
+        if (KL == 1) {
+            a[0] = valid ? __ldg(A) : make_float2(0.f, 0.f);
         } else {
-            const uint32_t ii = uint32_t(i), no = uint32_t(d.nOut);
-            const uint32_t sig = ii / no, beta = ii - sig * no;
-            ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
-            ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
-            ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
-            eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
-            Bp = d.B + ib * d.sB;
+#pragma unroll
+            for (int q = 0; q < KL / 2; ++q) {
+                const float4 v = valid ? __ldg(reinterpret_cast<const float4 *>(A + 2 * kl + 2 * L * q))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                a[2 * q] = make_float2(v.x, v.y);
+                a[2 * q + 1] = make_float2(v.z, v.w);
+            }
         }
-        const int64_t offA = (mb > 8 ? dep(m >> 8, s_pAm + 8, mb - 8) : 0) + s_mloA[m & 255];
-        const float2 *A = d.A + ia * d.sA + offA;
-        float2 acc[N];
+    };
+    // acc[n] = sum over this lane's k of a[k] B[n*K + k], then summed over
+    // the row's L lanes by recursive halving: at xor level o = 1, 2, 4 a lane
+    // keeps one half of the outputs it still holds (the upper half when bit o
+    // of its lane index is set) and adds its partner's copy of that half;
+    // once one output is left, plain xor sums finish.  Afterwards each lane
+    // holds max(1, N / L) outputs (n0, n_held below).
+    auto row_times_b = [&](float2 (&acc)[N], const float2 (&a)[KL], const float2 *Bj) {
 #pragma unroll
         for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
-        if (valid) {
-            if (K >= 2) {
-                for (int k = 2 * kl; k < K; k += 2 * L) {
-                    const float4 v = __ldg(reinterpret_cast<const float4 *>(A + k));
-                    const float2 a0 = make_float2(v.x, v.y), a1 = make_float2(v.z, v.w);
+        if (KL == 1) {
 #pragma unroll
-                    for (int n = 0; n < N; ++n) {
-                        const float2 b0 = uniform ? s_B[k * N + n] : __ldg(Bp + k + s_offBn[n]);
-                        const float2 b1 = uniform ? s_B[(k + 1) * N + n] : __ldg(Bp + k + 1 + s_offBn[n]);
-                        cfma(acc[n], a0, b0);
-                        cfma(acc[n], a1, b1);
+            for (int n = 0; n < N; ++n) cfma(acc[n], a[0], Bj[n * K]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < KL / 2; ++q) {
+                const int k = 2 * kl + 2 * L * q;
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    const float4 b = *reinterpret_cast<const float4 *>(Bj + n * K + k);
+                    cfma(acc[n], a[2 * q], make_float2(b.x, b.y));
+                    cfma(acc[n], a[2 * q + 1], make_float2(b.z, b.w));
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int o = 1 << t;
+            if (o >= L) break;
+            constexpr int W0 = N;
+            const int width = W0 >> t;  // a constant once unrolled
+            if (width > 1) {
+                const bool up = (kl & o) != 0;
+#pragma unroll
+                for (int n = 0; n < N / 2; ++n) {
+                    if (n < (width >> 1)) {
+                        const int h = width >> 1;
+                        const float2 send = up ? acc[n] : acc[n + h];
+                        const float2 keep = up ? acc[n + h] : acc[n];
+                        acc[n].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, o);
+                        acc[n].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, o);
                     }
                 }
             } else {
-                const float2 a0 = __ldg(A);
-#pragma unroll
-                for (int n = 0; n < N; ++n) cfma(acc[n], a0, uniform ? s_B[n] : __ldg(Bp + s_offBn[n]));
+                acc[0].x += __shfl_xor_sync(0xffffffffu, acc[0].x, o);
+                acc[0].y += __shfl_xor_sync(0xffffffffu, acc[0].y, o);
             }
         }
-        for (int o = L >> 1; o > 0; o >>= 1) {
-#pragma unroll
-            for (int n = 0; n < N; ++n) {
-                acc[n].x += __shfl_xor_sync(0xffffffffu, acc[n].x, o);
-                acc[n].y += __shfl_xor_sync(0xffffffffu, acc[n].y, o);
-            }
-        }
-        const float sc = pow2f(-(ea + eb));
-        uint32_t mx = 0;
-        if (valid) {
-            const int64_t offC = (mb > 8 ? dep(m >> 8, s_pCm + 8, mb - 8) : 0) + s_mloC[m & 255];
-            float2 *C = d.C + i * d.sC + offC;
-#pragma unroll
-            for (int n = 0; n < N; ++n) {
-                if (n % L != kl) continue;  // lanes of the row split the stores
-                const float2 v = make_float2(acc[n].x * sc, acc[n].y * sc);
-                C[s_offCn[n]] = v;
-                mx = max(mx, absmax_bits(v));
-            }
-            if (m == 0 && kl == 0) d.EC[i] = d.EA[ia] + ea + d.EB[ib] + eb;
-        }
-        if (d.mxC) {
-            if (uniform) mx_run = max(mx_run, mx);
-            else if (valid && mx) record_max(d.mxC + i, mx);
-        }
+    };
+    // outputs this lane holds after row_times_b: acc[j] is output n0 + j
+    int n0 = 0, n_held = N;
+    for (int t = 0; (1 << t) < L && n_held > 1; ++t) {
+        n_held >>= 1;
+        if (kl & (1 << t)) n0 += n_held;
     }
-    if (d.mxC && uniform) {
-        __shared__ uint32_t s_mx;
-        if (tid == 0) s_mx = 0;
-        __syncthreads();
+    const bool store_lane = N >= L || kl < N;  // higher lane bits hold copies
+
+    if (M >= 8 * R) {
+        const int64_t g = int64_t(blockIdx.x) / mblocks;
+        const int64_t m0 = (int64_t(blockIdx.x) - g * mblocks) * rows_per_block;
+        const int64_t i0 = d.gfirst[g], cnt = d.gfirst[g + 1] - i0;
+        const int64_t ia = d.instab[i0].x;
+        const int ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
+        const int EAa = d.EA[ia] + ea;
+        const int ch_max = min(ROW_CH, ROW_SB / KN);
+        for (int64_t c0 = 0; c0 < cnt; c0 += ch_max) {
+            const int ch = int(cnt - c0 < ch_max ? cnt - c0 : int64_t(ch_max));
+            if (tid < ch) {
+                const int64_t ib = d.instab[i0 + c0 + tid].y;
+                const int eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
+                s_ib[tid] = ib;
+                s_e[tid] = ea + eb;
+                s_EC[tid] = EAa + d.EB[ib] + eb;
+                s_mx[tid] = 0u;
+            }
+            __syncthreads();
+            for (int e = tid; e < ch * KN; e += ROW_THREADS) {
+                const int j = e / KN;
+                s_B[e] = __ldg(d.B + s_ib[j] * d.sB + (e - j * KN));
+            }
+            __syncthreads();
+            for (int it = 0; it < passes; ++it) {
+                const int64_t m = m0 + (int64_t(it) * 8 + warp) * R + sub;
+                float2 a[KL];
+                load_row(a, ia, m, true);
+                const int64_t offC = (mb > 8 ? dep(m >> 8, s_pCm + 8, mb - 8) : 0) + s_mloC[m & 255];
+                for (int j = 0; j < ch; ++j) {
+                    float2 acc[N];
+                    row_times_b(acc, a, s_B + j * KN);
+                    const float sc = pow2f(-s_e[j]);
+                    float2 *C = d.C + (i0 + c0 + j) * d.sC + offC;
+                    uint32_t mx = 0;
+                    if (store_lane) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx_run = max(mx_run, __shfl_xor_sync(0xffffffffu, mx_run, o));
-        if (lane == 0) atomicMax(&s_mx, mx_run);
-        __syncthreads();
-        if (tid == 0 && s_mx && r0 < total) record_max(d.mxC + (r0 >> mb), s_mx);
+                        for (int h = 0; h < N; ++h) {
+                            if (h >= n_held) break;
+                            const float2 v = make_float2(acc[h].x * sc, acc[h].y * sc);
+                            C[s_offCn[n0 + h]] = v;
+                            mx = max(mx, absmax_bits(v));
+                        }
+                    }
+                    if (d.mxC) {
+                        const uint32_t r = __reduce_max_sync(0xffffffffu, mx);
+                        if (lane == 0 && r) atomicMax(&s_mx[j], r);
+                    }
+                }
+            }
+            __syncthreads();
+            if (tid < ch) {
+                const int64_t i = i0 + c0 + tid;
+                if (m0 == 0) d.EC[i] = s_EC[tid];
+                if (d.mxC && s_mx[tid]) record_max(d.mxC + i, s_mx[tid]);
+            }
+            __syncthreads();
+        }
+    } else {
+        const int64_t total = d.n_groups << mb;
+        for (int it = 0; it < passes; ++it) {
+            const int64_t gid = int64_t(blockIdx.x) * rows_per_block + (int64_t(it) * 8 + warp) * R + sub;
+            const bool valid = gid < total;
+            const int64_t gr = valid ? gid : 0;
+            const int64_t g = gr >> mb, m = gr & (M - 1);
+            const int64_t i0 = d.gfirst[g];
+            const int cnt = valid ? int(d.gfirst[g + 1] - i0) : 0;
+            const int64_t ia = d.instab[i0].x;
+            const int ea = d.mxA ? exp_of(d.mxA[ia]) : 0;
+            float2 a[KL];
+            load_row(a, ia, m, valid);
+            const int64_t offC = (mb > 8 ? dep(m >> 8, s_pCm + 8, mb - 8) : 0) + s_mloC[m & 255];
+            const int jmax = int(__reduce_max_sync(0xffffffffu, uint32_t(cnt)));  // warp-uniform trip count
+            for (int j = 0; j < jmax; ++j) {
+                const bool vj = j < cnt;
+                const int64_t i = i0 + j;
+                const int64_t ib = vj ? d.instab[i].y : 0;
+                float2 acc[N];
+                row_times_b(acc, a, d.B + ib * d.sB);
+                const int eb = vj && d.mxB ? exp_of(d.mxB[ib]) : 0;
+                const float sc = pow2f(-(ea + eb));
+                uint32_t mx = 0;
+                if (vj) {
+                    float2 *C = d.C + i * d.sC + offC;
+                    if (store_lane) {
+#pragma unroll
+                        for (int h = 0; h < N; ++h) {
+                            if (h >= n_held) break;
+                            const float2 v = make_float2(acc[h].x * sc, acc[h].y * sc);
+                            C[s_offCn[n0 + h]] = v;
+                            mx = max(mx, absmax_bits(v));
+                        }
+                    }
+                    if (m == 0 && kl == 0) d.EC[i] = d.EA[ia] + ea + d.EB[ib] + eb;
+                }
+                for (int o = L >> 1; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (d.mxC && vj && kl == 0 && mx) record_max(d.mxC + i, mx);
+            }
+        }
     }
 }
 
@@ -411,24 +483,42 @@ cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
     const int K = 1 << d.kb;
     const int L = K >= 16 ? 8 : (K >= 2 ? K / 2 : 1);
     const int R = 32 / L;
-    // 8 warps x R rows per pass, up to 16 passes, and no more rows than one
-    // instance has (so that a block stays inside one instance when it can)
+    const int KL = K / L;
     const int64_t M = int64_t(1) << d.mb;
-    int64_t passes = M / (8 * R);
-    passes = passes < 1 ? 1 : (passes > 16 ? 16 : passes);
-    const int rows_per_block = int(8 * R * passes);
-    const int64_t rows = d.nInst << d.mb;
-    const int64_t blocks = (rows + rows_per_block - 1) / rows_per_block;
+    int64_t blocks, mblocks = 1;
+    int rows_per_block;
+    if (M >= 8 * R) {  // blocks inside one group: up to 16 passes of 8 warps x R rows
+        int64_t passes = M / (8 * R);
+        passes = passes > 16 ? 16 : passes;
+        rows_per_block = int(8 * R * passes);
+        mblocks = M / rows_per_block;
+        blocks = d.n_groups * mblocks;
+    } else {  // small instances: 4 passes over consecutive groups' rows
+        rows_per_block = 8 * R * 4;
+        blocks = ((d.n_groups << d.mb) + rows_per_block - 1) / rows_per_block;
+    }
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const dim3 g((unsigned)blocks);
-    switch (d.nb) {
-        case 0: k_step_row<0><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
-        case 1: k_step_row<1><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
-        case 2: k_step_row<2><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
-        case 3: k_step_row<3><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
-        default: k_step_row<4><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block); break;
+#define TN_ROW(NB_, KL_) k_step_row<NB_, KL_><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block, mblocks)
+#define TN_ROW_KL(NB_)                         \
+    switch (KL) {                              \
+        case 1: TN_ROW(NB_, 1); break;         \
+        case 2: TN_ROW(NB_, 2); break;         \
+        case 4: TN_ROW(NB_, (NB_ <= 3 ? 4 : 2)); break;   \
+        case 8: TN_ROW(NB_, (NB_ <= 2 ? 8 : 2)); break;   \
+        case 16: TN_ROW(NB_, (NB_ <= 1 ? 16 : 2)); break; \
+        default: TN_ROW(NB_, (NB_ == 0 ? 32 : 2)); break; \
     }
+    switch (d.nb) {
+        case 0: TN_ROW_KL(0); break;
+        case 1: TN_ROW_KL(1); break;
+        case 2: TN_ROW_KL(2); break;
+        case 3: TN_ROW_KL(3); break;
+        default: TN_ROW_KL(4); break;
+    }
+#undef TN_ROW_KL
+#undef TN_ROW
     return cudaGetLastError();
 }
 

@@ -201,6 +201,7 @@ struct Builder {
     std::vector<int> slice_of;             // bond edge -> internal slice index (-1: not sliced)
     bool bad_offsets = false;              // set by layout_workspace's self-check
     std::vector<std::vector<int>> low_bits; // per node: bonds its consumer contracts (edge-id order)
+    std::vector<std::vector<int>> tails;    // per node: its other bonds, in its consumer's row/column order
 
     bool fail(int c, const std::string &msg) {
         code = c;
@@ -335,26 +336,16 @@ struct Builder {
             Node &nd = P.nodes[st.node];
             const Node &A = P.nodes[st.a], &B = P.nodes[st.b];
             auto in = [](const std::vector<int> &v, int e) { return std::find(v.begin(), v.end(), e) != v.end(); };
-            const std::vector<int> &Lv = low_bits[st.node];
-            std::vector<int> kk, fa_l, fa_r, fb_l, fb_r;
-            for (int e : A.layout) {
-                if (in(B.layout, e)) kk.push_back(e);
-                else if (in(Lv, e)) fa_l.push_back(e);
-                else fa_r.push_back(e);
-            }
-            for (int e : B.layout) {
-                if (in(A.layout, e)) continue;
-                if (in(Lv, e)) fb_l.push_back(e);
-                else fb_r.push_back(e);
-            }
-            std::sort(fa_l.begin(), fa_l.end());
-            std::sort(fb_l.begin(), fb_l.end());
-            std::vector<int> mord(fa_l), nord(fb_l);
-            mord.insert(mord.end(), fa_r.begin(), fa_r.end());
-            nord.insert(nord.end(), fb_r.begin(), fb_r.end());
-            nd.layout = Lv;
-            nd.layout.insert(nd.layout.end(), fb_r.begin(), fb_r.end());
-            nd.layout.insert(nd.layout.end(), fa_r.begin(), fa_r.end());
+            // rows: A's bits above K in address order; columns: B's likewise.
+            // Both start with the bits that the next step contracts (the
+            // lowest bits of C), so consecutive rows store to neighbouring
+            // addresses.
+            std::vector<int> kk, mord, nord;
+            for (int e : A.layout) (in(B.layout, e) ? kk : mord).push_back(e);
+            for (int e : B.layout)
+                if (!in(A.layout, e)) nord.push_back(e);
+            nd.layout = low_bits[st.node];
+            nd.layout.insert(nd.layout.end(), tails[st.node].begin(), tails[st.node].end());
             auto pos = [](const std::vector<int> &lay, int e) {
                 return int8_t(std::find(lay.begin(), lay.end(), e) - lay.begin());
             };
@@ -369,6 +360,14 @@ struct Builder {
             for (int j = 0; j < st.kb; ++j)
                 if (st.pAk[j] != j || st.pBk[j] != j)
                     return fail(TN_EUNSUPPORTED, "internal error: operand not K-major");
+            for (int j = 0; j < st.mb; ++j)
+                if (st.pAm[j] != st.kb + j || st.pCm[j] >= (int)nd.layout.size())
+                    return fail(TN_EUNSUPPORTED, "internal error: A operand not row-affine");
+            for (int j = 0; j < st.nb; ++j)
+                if (st.pBn[j] != st.kb + j || st.pCn[j] >= (int)nd.layout.size())
+                    return fail(TN_EUNSUPPORTED, "internal error: B operand not column-affine");
+            if ((int)nd.layout.size() != st.mb + st.nb)
+                return fail(TN_EUNSUPPORTED, "internal error: output layout");
             P.max_rank = std::max(P.max_rank, nd.rank);
             if (nd.rank > 40 || st.mb > 40 || st.kb > 24 || st.nb > 24)
                 return fail(TN_EUNSUPPORTED, "intermediate rank above 40 (or contracted/free bits above 24)");
@@ -751,13 +750,27 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
         low_bits[a] = kset;
         low_bits[b] = kset;
     }
-    // leaf layouts: the contracted bonds first (edge-id order), then the rest
+    // Address order above the contracted bonds: the bonds the grandparent's
+    // step contracts first, then the rest, each in edge-id order.  That is
+    // the consumer's row (resp. column) order, so every operand is
+    // row-affine: address = k + 2^kb * m.
+    std::vector<std::vector<int>> tails(NN);
+    for (int v = 0; v < NN; ++v) {
+        const int p = P.nodes[v].parent;
+        auto has = [](const std::vector<int> &s, int e) { return std::binary_search(s.begin(), s.end(), e); };
+        std::vector<int> rest;
+        for (int e : open[v]) {
+            if (has(low_bits[v], e)) continue;
+            if (p >= 0 && has(low_bits[p], e)) tails[v].push_back(e);
+            else rest.push_back(e);
+        }
+        tails[v].insert(tails[v].end(), rest.begin(), rest.end());
+    }
+    // leaf layouts: the contracted bonds first (edge-id order), then the tail
     for (int v = 0; v < T; ++v) {
         Node &nd = P.nodes[v];
-        std::vector<int> lay = low_bits[v];
-        for (int e : nd.layout)
-            if (std::find(lay.begin(), lay.end(), e) == lay.end()) lay.push_back(e);
-        nd.layout = lay;
+        nd.layout = low_bits[v];
+        nd.layout.insert(nd.layout.end(), tails[v].begin(), tails[v].end());
     }
 
     Builder B{P, err, code, 0, 0, 0, {}, {}, false, {}};
@@ -765,6 +778,7 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
     B.NN = NN;
     B.m = n_sliced;
     B.low_bits = low_bits;
+    B.tails = tails;
     B.out_instances();
     // Internal slice order.  The first m_low sliced edges run side by side in
     // one pass; the rest are looped over, bit t - m_low of the batch index,
