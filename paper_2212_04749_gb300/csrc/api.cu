@@ -36,6 +36,11 @@ struct PlanObj {
     uint8_t *ws = nullptr;
     size_t ws_bytes = 0;
     std::vector<tnk::StepDesc> desc;  // per step
+    struct alignas(64) AMap {
+        CUtensorMap map;
+        bool ok;
+    };
+    std::vector<AMap> amap;           // per step: TMA descriptor of A (tensor-core steps)
     int32_t *err_flag = nullptr;      // device word for bounded waits
     bool profile = false;
     std::vector<cudaEvent_t> ev;          // pool, two per profiled launch
@@ -120,6 +125,14 @@ void build_descs(PlanObj *o) {
         d.max_group = (int32_t)mg;
         o->desc.push_back(d);
     }
+    // TMA descriptors of the A operands, for every step the tensor-core
+    // kernel can take (it may be chosen at run time)
+    o->amap.assign(P.steps.size(), PlanObj::AMap{});
+    for (size_t s = 0; s < P.steps.size(); ++s) {
+        const tnk::StepDesc &d = o->desc[s];
+        o->amap[s].ok = tnk::gemm_tc_supports(d) &&
+                        tnk::make_a_map(d, P.nodes[P.steps[s].a].n_inst, &o->amap[s].map) == cudaSuccess;
+    }
 }
 
 int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
@@ -134,7 +147,8 @@ int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
         e = tnk::launch_step_row(d, st);
     } else if (precision != TN_FP32 && tnk::gemm_tc_supports(d)) {
         fam = 2;
-        e = tnk::launch_step_gemm_tc(d, precision, o->err_flag, st);
+        e = o->amap[s].ok ? tnk::launch_step_gemm_tc(d, &o->amap[s].map, precision, o->err_flag, st)
+                          : cudaErrorInvalidValue;  // its TMA descriptor could not be encoded
     } else {
         fam = 1;
         e = tnk::launch_step_gemm_simt(d, st);
@@ -484,7 +498,10 @@ int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream
     o->ws_bytes = prev_bytes;
     o->err_flag = prev_flag;
     if (prev_ws) build_descs(o);
-    else o->desc.clear();
+    else {
+        o->desc.clear();
+        o->amap.clear();
+    }
     g_err = msg;
     return rc;
 }

@@ -16,18 +16,21 @@
 //            kind::f16 products hi*hi + hi*lo + lo*hi into the same FP32
 //            accumulator.
 //
-// CTA: 128 threads, tile BM = 128 rows x 64 complex columns (MMA M = 128,
-// N = 128), K in chunks of 16 complex (32 real) through two shared-memory
-// stages in the canonical K-major no-swizzle layout (core matrix 8 rows x
-// 16 bytes; LBO = distance between K-adjacent core matrices = 128 rows x
-// 16 B, SBO = distance between 8-row groups = 128 B).  All threads stage;
-// one thread issues the MMAs and commits them to the stage's mbarrier; the
-// FP32 accumulator lives in 128 TMEM columns and is read back with
-// tcgen05.ld for the epilogue (power-of-two scale, scattered complex64
+// Tile: 128 rows x 64 complex columns (MMA M = 128, N = 128), K in chunks
+// of 16 complex (32 real).  Shared-memory operands use the canonical K-major
+// no-swizzle layout (core matrix 8 rows x 16 bytes; LBO = distance between
+// K-adjacent core matrices = 128 rows x 16 B, SBO = distance between 8-row
+// groups = 128 B).  A arrives by TMA already in that order (FP32; TF32 uses
+// it as is, BF16x3 splits it into hi/lo planes); B columns are gathered per
+// instance and expanded into the real 2x2 form.  One thread issues the MMAs
+// into an FP32 accumulator in TMEM (two 128-column accumulators), read back
+// with tcgen05.ld for the epilogue (power-of-two scale, scattered complex64
 // stores through the output bit positions, max-|x| tracking).
 //
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // code in *err, skips the remaining work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -166,7 +169,11 @@ __device__ __forceinline__ void cp_async_wait(int pending) {
         case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
         case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
         case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-        default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+        case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
     }
 }
 
@@ -174,11 +181,30 @@ __device__ __forceinline__ void named_sync(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// 4-D TMA tile load (shared::cluster destination = this CTA's own memory),
+// completing on an mbarrier with a byte count.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 // Persistent warp-specialised kernel.
-//   warps 0-7  : producers.  cp.async of A rows and B columns several chunks
-//                ahead (TF32 A straight into the MMA layout; BF16x3 A into
-//                a raw FP32 ring, then split into hi/lo; B expanded into the
-//                real 2x2 block form at finalise time).
+//   warp 17    : lane 0 streams A: one TMA tile load per chunk (128 rows x
+//                16 complex k, already in the K-major core-matrix order)
+//                into a ring of RST raw stages, several chunks ahead.
+//   warps 0-7  : B columns by cp.async (LOOK chunks ahead), expanded into the
+//                real 2x2 block form; BF16x3: A split into hi/lo from the
+//                raw ring.  TF32 reads A straight from the raw ring.
 //   warp 8     : TMEM allocation; lane 0 issues tcgen05.mma and commits.
 //   warps 9-16 : epilogue, two warps per TMEM lane quadrant (warp % 4), each
 //                draining 32 of the tile's 64 complex columns; two
@@ -188,22 +214,26 @@ constexpr int NPROD = 256;   // warps 0-7
 constexpr int MMA_WARP = 8;
 constexpr int EPI_WARP0 = 9; // warps 9-16: two per TMEM lane quadrant
 constexpr int NEPI = 256;
-constexpr int NTHREADS = 544;
+constexpr int TMA_WARP = 17;
+constexpr int NTHREADS = 576;
 constexpr int ACC_COLS = 128;
 constexpr int TMEM_COLS2 = 256;
 
 template <int PREC>
 struct Cfg {
-    static constexpr int STAGES = PREC == 1 ? 4 : 3;
-    static constexpr int LOOK = STAGES - 1;
-    static constexpr int SLOT_A = TBM * TBKR * 4;
+    static constexpr int ST = PREC == 1 ? 4 : 3;      // MMA stages (B; BF16x3: also A hi/lo)
+    static constexpr int RST = PREC == 1 ? 6 : 4;     // raw A stages filled by TMA
+    static constexpr int BRST = 6;                    // raw B stages (per-thread cp.async pieces)
+    static constexpr int LOOK = BRST - 1;             // B chunks issued ahead
+    static constexpr int SLOT_RAW = TBM * TBK * 8;    // FP32 A chunk, [16-byte k column][row]
+    static constexpr int SLOT_A = PREC == 2 ? TBM * TBKR * 4 : 0;
     static constexpr int SLOT_B = TBNR * TBKR * 4;
-    static constexpr int SLOT_RAW = PREC == 2 ? TBM * TBK * 8 : 0;
-    static constexpr int SLOT_BRAW = TBN * TBK * 8;  // raw complex64 B chunk, per-thread pieces
-    static constexpr int OFF_B = STAGES * SLOT_A;
-    static constexpr int OFF_RAW = OFF_B + STAGES * SLOT_B;
-    static constexpr int OFF_BRAW = OFF_RAW + STAGES * SLOT_RAW;
-    static constexpr int OFF_CTRL = OFF_BRAW + STAGES * SLOT_BRAW;
+    static constexpr int SLOT_BRAW = TBN * TBK * 8;   // raw complex64 B chunk
+    static constexpr int OFF_RAW = 0;
+    static constexpr int OFF_A = OFF_RAW + RST * SLOT_RAW;
+    static constexpr int OFF_B = OFF_A + ST * SLOT_A;
+    static constexpr int OFF_BRAW = OFF_B + ST * SLOT_B;
+    static constexpr int OFF_CTRL = OFF_BRAW + BRST * SLOT_BRAW;
 };
 
 struct EpiMeta {
@@ -218,7 +248,7 @@ struct EpiMeta {
 };
 
 struct Ctrl {
-    uint64_t full[4], empty[4], tfull[2], tempty[2];
+    uint64_t full[4], empty[4], rfull[8], rempty[8], tfull[2], tempty[2];
     uint32_t tmem_base;
     int32_t abort_;
     int32_t epi_fail[2];  // epilogue-uniform abort decisions, by tile parity
@@ -229,6 +259,7 @@ template <int PREC>
 constexpr size_t smem_bytes() {
     return size_t(Cfg<PREC>::OFF_CTRL) + sizeof(Ctrl) + 128;
 }
+static_assert(smem_bytes<1>() <= 232448 && smem_bytes<2>() <= 232448, "shared memory above 227 KB");
 
 // tile T of a step: column-tile record e = T / mtiles, row tile T % mtiles
 __device__ __forceinline__ int4 tile_rec(const StepDesc &d, int64_t T, int64_t mtiles) {
@@ -236,8 +267,8 @@ __device__ __forceinline__ int4 tile_rec(const StepDesc &d, int64_t T, int64_t m
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err) {
+__global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 registers (5 warps on a sub-partition)
+    k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA) {
     using C = Cfg<PREC>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -258,9 +289,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
+        for (int s = 0; s < C::ST; ++s) {
             mbar_init(&X.full[s], NPROD);
             mbar_init(&X.empty[s], 1);
+        }
+        for (int s = 0; s < C::RST; ++s) {
+            mbar_init(&X.rfull[s], 1);
+            mbar_init(&X.rempty[s], PREC == 2 ? NPROD : 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&X.tfull[a], 1);
@@ -278,22 +313,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         atomicExch(err, 1);
         *abort_flag = 1;
     };
+    auto tile_of = [&](int64_t l) { return int64_t(blockIdx.x) + l * gridDim.x; };
 
-    if (warp < NPROD / 32) {
-        // ------------------------------------------------------------ producers
-        const int kq = (tid >> 3) & 3;
-        int rowj[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) rowj[j] = ((tid >> 5) + 8 * j) * 8 + (tid & 7);
+    if (warp == TMA_WARP) {
+        // ------------------------------------------------------------ A stream
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            int64_t issued = 0;
+            bool ok = true;
+            for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
+                const int64_t T = tile_of(l);
+                const int4 r = tile_rec(d, T, mtiles);
+                const int m0 = int((T % mtiles) * TBM);
+                for (int c = 0; c < nch; ++c, ++issued) {
+                    const int rs = int(issued % C::RST);
+                    if (!mbar_wait(&X.rempty[rs], (uint32_t(issued / C::RST) & 1u) ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&X.rfull[rs], C::SLOT_RAW);
+                    tma_load_4d(smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), &tmA, 0, m0, 8 * c, r.z, &X.rfull[rs]);
+                }
+            }
+            if (!ok) give_up();
+            // loads still in flight land before the CTA leaves (bounded)
+            for (int64_t j = issued > C::RST ? issued - C::RST : 0; j < issued; ++j)
+                mbar_wait(&X.rfull[j % C::RST], uint32_t(j / C::RST) & 1u);
+        }
+        __syncwarp();
+    } else if (warp < NPROD / 32) {
+        // ------------------------------------------------------------ B loads, A split
         const int bcol = tid & 63, kqb = tid >> 6;
-        const float2 *abase[2] = {nullptr, nullptr};
-        int64_t offA[2][2];
         int64_t bbase[2] = {-1, -1};
         int64_t issued = 0;
         // metadata pipeline: records two tiles ahead, B instance one tile ahead
         int4 rec_pf[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
         int ib_pf = 0;
-        auto tile_of = [&](int64_t l) { return int64_t(blockIdx.x) + l * gridDim.x; };
         auto col_inst = [&](const int4 &r) -> int64_t {  // instance of this thread's B column, or -1
             const int64_t gc = int64_t(r.w) + bcol;
             return gc < (int64_t(r.y) << d.nb) ? int64_t(r.x) + (gc >> d.nb) : -1;
@@ -305,53 +360,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ib_pf = ci >= 0 ? __ldg(d.instab + ci).y : 0;
         }
         for (int64_t gch = 0; gch < total_chunks && !*abort_flag; ++gch) {
+            // B pieces run LOOK chunks ahead.  Each thread reads back only
+            // the 32 bytes it copied, and its raw slot was last used by a
+            // chunk it has already expanded, so the ring needs no barrier.
             while (issued < total_chunks && issued <= gch + C::LOOK) {
                 const int64_t l = issued / nch;
                 const int c = int(issued - l * nch);
-                const int slot = int(issued % C::STAGES);
-                const uint32_t ph = uint32_t(issued / C::STAGES) & 1u;
+                const int bslot = int(issued % C::BRST);
                 if (c == 0) {
                     const int4 r = rec_pf[l & 1];
-                    const int64_t m0 = (tile_of(l) % mtiles) * TBM;
-                    abase[l & 1] = d.A + int64_t(r.z) * d.sA;
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int64_t m = m0 + rowj[j];
-                        offA[l & 1][j] = m < M ? dep(m, d.pAm, d.mb) : -1;
-                    }
                     const int64_t ci = col_inst(r);
-                    bbase[l & 1] = ci >= 0 ? int64_t(ib_pf) * d.sB + dep((int64_t(r.w) + bcol) & (N - 1), d.pBn, d.nb) : -1;
-                    // prefetch: the B instance of tile l+1, the record of tile l+2
+                    // column-affine B: column n of instance ib starts at ib*sB + n*K
+                    bbase[l & 1] = ci >= 0 ? int64_t(ib_pf) * d.sB + (((int64_t(r.w) + bcol) & (N - 1)) << d.kb) : -1;
                     if (l + 1 < my_tiles) {
                         const int64_t cn = col_inst(rec_pf[(l + 1) & 1]);
                         ib_pf = cn >= 0 ? __ldg(d.instab + cn).y : 0;
                     }
                     if (l + 2 < my_tiles) rec_pf[l & 1] = tile_rec(d, tile_of(l + 2), mtiles);
                 }
-                if (!mbar_wait(&X.empty[slot], ph ^ 1u)) {
-                    give_up();
-                    break;
-                }
-                const float2 *ab = abase[l & 1];
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int64_t oa = offA[l & 1][j];
-                    const int k = c * TBK + 4 * kq;
-                    const bool v = oa >= 0 && k + 3 < K;
-                    const float2 *src = v ? ab + oa + k : ab;
-                    if (PREC == 1) {
-                        const uint32_t dst = smem_u32(sm + slot * C::SLOT_A);
-                        cp_async16(dst + kmaj_off(rowj[j], 8 * kq, 4), src, v ? 16 : 0);
-                        cp_async16(dst + kmaj_off(rowj[j], 8 * kq + 4, 4), v ? src + 2 : ab, v ? 16 : 0);
-                    } else {
-                        const uint32_t dst = smem_u32(sm + C::OFF_RAW + slot * C::SLOT_RAW) + uint32_t(tid * 2 + j) * 32;
-                        cp_async16(dst, src, v ? 16 : 0);
-                        cp_async16(dst + 16, v ? src + 2 : ab, v ? 16 : 0);
-                    }
-                }
                 {  // B: this thread's column, k quad kqb
                     const int64_t bb = bbase[l & 1];
-                    const uint32_t dst = smem_u32(sm + C::OFF_BRAW + slot * C::SLOT_BRAW) + uint32_t(tid) * 32;
+                    const uint32_t dst = smem_u32(sm + C::OFF_BRAW + bslot * C::SLOT_BRAW) + uint32_t(tid) * 32;
                     const int k = c * TBK + 4 * kqb;
                     const bool v = bb >= 0 && k + 3 < K;
                     const float2 *src = v ? d.B + bb + k : d.B;
@@ -361,16 +390,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 cp_async_commit();
                 ++issued;
             }
-            if (*abort_flag) break;
-            cp_async_wait(int(issued - gch - 1));
-            const int slot = int(gch % C::STAGES);
+            const int slot = int(gch % C::ST);
+            // the MMA stage is free once the MMAs of chunk gch - ST are done
+            if (!mbar_wait(&X.empty[slot], (uint32_t(gch / C::ST) & 1u) ^ 1u)) {
+                give_up();
+                break;
+            }
             if (PREC == 2) {
-                uint8_t *bh = sm + slot * C::SLOT_A, *bl = bh + TBM * TBKR * 2;
-                const uint8_t *raw = sm + C::OFF_RAW + slot * C::SLOT_RAW;
+                // A: split the raw FP32 chunk into hi/lo (rows 8 at a time,
+                // 16-byte k columns p and p+1 of the raw chunk per item)
+                const int rs = int(gch % C::RST);
+                if (!mbar_wait(&X.rfull[rs], uint32_t(gch / C::RST) & 1u)) {
+                    give_up();
+                    break;
+                }
+                const uint8_t *raw = sm + C::OFF_RAW + rs * C::SLOT_RAW;
+                uint8_t *bh = sm + C::OFF_A + slot * C::SLOT_A, *bl = bh + TBM * TBKR * 2;
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const float4 v0 = *reinterpret_cast<const float4 *>(raw + (tid * 2 + j) * 32);
-                    const float4 v1 = *reinterpret_cast<const float4 *>(raw + (tid * 2 + j) * 32 + 16);
+                    const int item = tid + NPROD * j;  // 0..511
+                    const int row = item & (TBM - 1), p = item >> 7;
+                    const float4 v0 = *reinterpret_cast<const float4 *>(raw + (2 * p) * (TBM * 16) + row * 16);
+                    const float4 v1 = *reinterpret_cast<const float4 *>(raw + (2 * p + 1) * (TBM * 16) + row * 16);
                     const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                     __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
@@ -378,12 +419,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         hi[q] = __float2bfloat16_rn(x[q]);
                         lo[q] = __float2bfloat16_rn(x[q] - __bfloat162float(hi[q]));
                     }
-                    *reinterpret_cast<uint4 *>(bh + kmaj_off(rowj[j], 8 * kq, 2)) = *reinterpret_cast<uint4 *>(hi);
-                    *reinterpret_cast<uint4 *>(bl + kmaj_off(rowj[j], 8 * kq, 2)) = *reinterpret_cast<uint4 *>(lo);
+                    *reinterpret_cast<uint4 *>(bh + kmaj_off(row, 8 * p, 2)) = *reinterpret_cast<uint4 *>(hi);
+                    *reinterpret_cast<uint4 *>(bl + kmaj_off(row, 8 * p, 2)) = *reinterpret_cast<uint4 *>(lo);
                 }
+                mbar_arrive(&X.rempty[rs]);
             }
+            cp_async_wait(int(issued - gch - 1));
             // B: expand this thread's prefetched piece into the MMA layout
-            const uint8_t *braw = sm + C::OFF_BRAW + slot * C::SLOT_BRAW + tid * 32;
+            const uint8_t *braw = sm + C::OFF_BRAW + int(gch % C::BRST) * C::SLOT_BRAW + tid * 32;
             {
                 const float4 p0 = *reinterpret_cast<const float4 *>(braw);
                 const float4 p1 = *reinterpret_cast<const float4 *>(braw + 16);
@@ -432,15 +475,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
                 bool ok = true;
                 for (int c = 0; c < nch; ++c, ++gch) {
-                    const int slot = int(gch % C::STAGES);
-                    if (!mbar_wait(&X.full[slot], uint32_t(gch / C::STAGES) & 1u)) {
+                    const int slot = int(gch % C::ST);
+                    const int rs = int(gch % C::RST);
+                    if (!mbar_wait(&X.full[slot], uint32_t(gch / C::ST) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    if (PREC == 1 && !mbar_wait(&X.rfull[rs], uint32_t(gch / C::RST) & 1u)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     if (PREC == 1) {
                         const uint32_t id = idesc(2u);
-                        const uint32_t a0 = smem_u32(sm + slot * C::SLOT_A);
+                        const uint32_t a0 = smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW);
                         const uint32_t b0 = smem_u32(sm + C::OFF_B + slot * C::SLOT_B);
 #pragma unroll
                         for (int j = 0; j < TBKR / 8; ++j) {
@@ -448,9 +496,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             mma_tf32(dtm, sdesc(a0 + off, LBO, SBO), sdesc(b0 + off, LBO, SBO), id,
                                      (c > 0 || j > 0) ? 1u : 0u);
                         }
+                        mma_commit(&X.empty[slot]);
+                        mma_commit(&X.rempty[rs]);
                     } else {
                         const uint32_t id = idesc(1u);
-                        const uint32_t ah = smem_u32(sm + slot * C::SLOT_A), al = ah + TBM * TBKR * 2;
+                        const uint32_t ah = smem_u32(sm + C::OFF_A + slot * C::SLOT_A), al = ah + TBM * TBKR * 2;
                         const uint32_t bh = smem_u32(sm + C::OFF_B + slot * C::SLOT_B), bl = bh + TBNR * TBKR * 2;
 #pragma unroll
                         for (int j = 0; j < TBKR / 16; ++j) {
@@ -460,8 +510,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             mma_f16(dtm, sdesc(ah + off, LBO, SBO), sdesc(bl + off, LBO, SBO), id, 1u);
                             mma_f16(dtm, sdesc(al + off, LBO, SBO), sdesc(bh + off, LBO, SBO), id, 1u);
                         }
+                        mma_commit(&X.empty[slot]);
                     }
-                    mma_commit(&X.empty[slot]);
                 }
                 if (!ok) {
                     give_up();
@@ -530,48 +580,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_after();
             const int64_t m = m0 + row;
             const int64_t offc = m < M ? dep(m, d.pCm, d.mb) : -1;
-            // this warp's 32 complex columns = 64 accumulator columns, loaded
-            // with four x16 loads and one wait
-            float v[64];
-            {
-                const uint32_t ta = tmem + uint32_t(acc * ACC_COLS + half * 64) + (uint32_t(lanegrp * 32) << 16);
-                uint32_t r[64];
+            // this warp's 32 complex columns = 64 accumulator columns, in two
+            // rounds of 16 complex columns (two x16 loads and one wait each).
+            // Scaled stores, then the per-instance max-|x|: each column's
+            // warp maximum lands in lane j = column, and runs of min(N, 32)
+            // lanes (one instance's columns) are combined with xor-shuffles.
+            // No branch depends on the column, so the loop pipelines.
+            uint32_t colmax = 0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(r[16 * q + 0]), "=r"(r[16 * q + 1]), "=r"(r[16 * q + 2]), "=r"(r[16 * q + 3]),
-                          "=r"(r[16 * q + 4]), "=r"(r[16 * q + 5]), "=r"(r[16 * q + 6]), "=r"(r[16 * q + 7]),
-                          "=r"(r[16 * q + 8]), "=r"(r[16 * q + 9]), "=r"(r[16 * q + 10]), "=r"(r[16 * q + 11]),
-                          "=r"(r[16 * q + 12]), "=r"(r[16 * q + 13]), "=r"(r[16 * q + 14]), "=r"(r[16 * q + 15])
-                        : "r"(ta + uint32_t(16 * q)));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int rnd = 0; rnd < 2; ++rnd) {
+                float v[32];
+                {
+                    const uint32_t ta = tmem + uint32_t(acc * ACC_COLS + half * 64 + rnd * 32) + (uint32_t(lanegrp * 32) << 16);
+                    uint32_t r[32];
 #pragma unroll
-                for (int q = 0; q < 64; ++q) v[q] = __uint_as_float(r[q]);
-            }
-            // running max of the current instance's columns; one warp
-            // reduction and one shared atomic per instance run
-            uint32_t tmx = 0;
-            int run_col = half * 32;
+                    for (int q = 0; q < 2; ++q)
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                            : "=r"(r[16 * q + 0]), "=r"(r[16 * q + 1]), "=r"(r[16 * q + 2]), "=r"(r[16 * q + 3]),
+                              "=r"(r[16 * q + 4]), "=r"(r[16 * q + 5]), "=r"(r[16 * q + 6]), "=r"(r[16 * q + 7]),
+                              "=r"(r[16 * q + 8]), "=r"(r[16 * q + 9]), "=r"(r[16 * q + 10]), "=r"(r[16 * q + 11]),
+                              "=r"(r[16 * q + 12]), "=r"(r[16 * q + 13]), "=r"(r[16 * q + 14]), "=r"(r[16 * q + 15])
+                            : "r"(ta + uint32_t(16 * q)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = half * 32 + j;
-                if (d.mxC && j > 0 && em.inst[col] != em.inst[col - 1]) {  // a new instance starts
-                    const uint32_t r = __reduce_max_sync(0xffffffffu, tmx);
-                    if (lane == 0 && r) atomicMax(&em.mx[run_col], r);
-                    tmx = 0;
-                    run_col = col;
+                    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
                 }
-                const int64_t cb = em.cbase[col];
-                if (offc < 0 || cb < 0) continue;
-                const float sc = em.sc[col];
-                const float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
-                d.C[cb + offc] = o;
-                tmx = max(tmx, __float_as_uint(fmaxf(fabsf(o.x), fabsf(o.y))));
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int j = rnd * 16 + jj;
+                    const int col = half * 32 + j;
+                    const int64_t cb = em.cbase[col];
+                    const float sc = em.sc[col];
+                    const float2 o = make_float2(v[2 * jj] * sc, v[2 * jj + 1] * sc);
+                    const bool ok = offc >= 0 && cb >= 0;
+                    if (ok) d.C[cb + offc] = o;
+                    if (d.mxC) {
+                        const uint32_t mj = ok ? __float_as_uint(fmaxf(fabsf(o.x), fabsf(o.y))) : 0u;
+                        const uint32_t rj = __reduce_max_sync(0xffffffffu, mj);
+                        colmax = lane == j ? rj : colmax;
+                    }
+                }
             }
             if (d.mxC) {
-                const uint32_t r = __reduce_max_sync(0xffffffffu, tmx);
-                if (lane == 0 && r) atomicMax(&em.mx[run_col], r);
+                const int runlen = N < 32 ? N : 32;
+                for (int sft = 1; sft < runlen; sft <<= 1) colmax = max(colmax, __shfl_xor_sync(0xffffffffu, colmax, sft));
+                if ((lane & (runlen - 1)) == 0 && colmax) atomicMax(&em.mx[half * 32 + lane], colmax);
             }
             tc_fence_before();
             mbar_arrive(&X.tempty[acc]);
@@ -599,12 +653,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }  // namespace
 
 bool gemm_tc_supports(const StepDesc &d) {
-    // K >= 8 complex (at least half a chunk), M >= 64 rows
-    return d.kb >= 3 && d.mb >= 6 && d.kb <= 24;
+    // K >= 8 complex (at least half a chunk), 64 <= M < 2^31 rows
+    return d.kb >= 3 && d.mb >= 6 && d.mb <= 30 && d.kb <= 24;
 }
 
 namespace {
 int g_num_sms = 0;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }
 
 cudaError_t init_kernels() {
@@ -613,23 +668,49 @@ cudaError_t init_kernels() {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", reinterpret_cast<void **>(&g_encode), 12000,
+                                             cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !g_encode) return cudaErrorNotSupported;
+    }
     e = cudaFuncSetAttribute(k_step_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_step_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2>());
 }
 
-cudaError_t launch_step_gemm_tc(const StepDesc &d, int precision, int32_t *err, cudaStream_t s) {
+// The A operand of a step as a 4-D tensor for TMA: (4 floats = one 16-byte
+// k column of a row, rows m, 16-byte k columns, instances).  The box
+// (4, 128, 8, 1) lands in shared memory as [k column][row][16 bytes], the
+// K-major core-matrix order the MMA descriptors use.  Rows past M and k past
+// K read as zeros.
+cudaError_t make_a_map(const StepDesc &d, int64_t n_inst_a, CUtensorMap *map) {
+    if (!g_encode) return cudaErrorNotReady;
+    const cuuint64_t K = cuuint64_t(1) << d.kb;
+    const cuuint64_t dims[4] = {4, cuuint64_t(1) << d.mb, K / 2, cuuint64_t(n_inst_a)};
+    const cuuint64_t strides[3] = {K * 8, 16, cuuint64_t(d.sA) * 8};
+    const cuuint32_t box[4] = {4, TBM, TBKR / 4, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2 *>(d.A), dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int precision, int32_t *err,
+                                cudaStream_t s) {
     if (!gemm_tc_supports(d)) return cudaErrorNotSupported;
-    if (g_num_sms <= 0) return cudaErrorNotReady;  // init_kernels() not called
+    if (g_num_sms <= 0 || !a_map) return cudaErrorNotReady;  // init_kernels() / make_a_map() not called
     const int64_t M = int64_t(1) << d.mb;
     const int64_t mtiles = (M + TBM - 1) / TBM;
     const int64_t tiles = d.n_ctab * mtiles;
     if (tiles <= 0) return cudaSuccess;
     const int64_t grid = tiles < g_num_sms ? tiles : g_num_sms;
     if (precision == 1)
-        k_step_gemm_tc<1><<<dim3((unsigned)grid), NTHREADS, smem_bytes<1>(), s>>>(d, mtiles, err);
+        k_step_gemm_tc<1><<<dim3((unsigned)grid), NTHREADS, smem_bytes<1>(), s>>>(d, mtiles, err, *a_map);
     else
-        k_step_gemm_tc<2><<<dim3((unsigned)grid), NTHREADS, smem_bytes<2>(), s>>>(d, mtiles, err);
+        k_step_gemm_tc<2><<<dim3((unsigned)grid), NTHREADS, smem_bytes<2>(), s>>>(d, mtiles, err, *a_map);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // the kernels (kernels.cu, gemm_tc.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -10,10 +11,10 @@ namespace tnk {
 // One pairwise contraction step, passed by value to every step kernel.
 //   C[i](m, n) = sum_k  A[a(i)](m, k) * B[b(i)](k, n)       (complex)
 // Instance i = sigma * nOut + beta;  a(i) = sigA[sigma] * nOutA + outA[beta],
-// b(i) likewise.  Both operands are K-major: entry (m, k) of an A instance
-// sits at element offset k + dep(m, pAm), entry (k, n) of a B instance at
-// k + dep(n, pBn), where dep scatters the bits of its first argument to the
-// listed bit positions (all >= kb).  C(m, n) of instance i sits at
+// b(i) likewise.  Both operands are K-major and affine: entry (m, k) of an
+// A instance sits at element offset k + m * 2^kb (pAm[j] = kb + j), entry
+// (k, n) of a B instance at k + n * 2^kb (pBn[j] = kb + j); dep scatters
+// the bits of its first argument to the listed bit positions.  C(m, n) of instance i sits at
 // i * sC + dep(m, pCm) + dep(n, pCn).  Consecutive output instances
 // [gfirst[g], gfirst[g+1]) read the same A instance (group g).
 struct StepDesc {
@@ -72,6 +73,10 @@ bool gemm_tc_supports(const StepDesc &d);
 // One-time per-device setup (function attributes, SM count); call outside
 // any stream capture.
 cudaError_t init_kernels();
-cudaError_t launch_step_gemm_tc(const StepDesc &d, int precision, int32_t *err_flag, cudaStream_t s);
+// TMA descriptor of a step's A operand (n_inst_a instances); encoded on the
+// host once the workspace is bound.
+cudaError_t make_a_map(const StepDesc &d, int64_t n_inst_a, CUtensorMap *map);
+cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int precision, int32_t *err_flag,
+                                cudaStream_t s);
 
 }  // namespace tnk
