@@ -24,8 +24,10 @@
 // it as is, BF16x3 splits it into hi/lo planes); B columns are gathered per
 // instance and expanded into the real 2x2 form.  One thread issues the MMAs
 // into an FP32 accumulator in TMEM (two 128-column accumulators), read back
-// with tcgen05.ld for the epilogue (power-of-two scale, scattered complex64
-// stores through the output bit positions, max-|x| tracking).
+// with tcgen05.ld for the epilogue: power-of-two scale and max-|x|
+// tracking, then each half tile goes through shared memory, reordered by
+// C address (the output bit positions), and leaves as coalesced 16-byte
+// stores.
 //
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // code in *err, skips the remaining work, frees its TMEM and returns.
@@ -64,8 +66,10 @@ __device__ __forceinline__ int64_t dep(int64_t x, const int8_t *pos, int nbits) 
     return r;
 }
 
+// fire-and-forget global max (a reduction, no returned value: the issuing
+// thread never waits on memory)
 __device__ __forceinline__ void record_max(uint32_t *slot, uint32_t v) {
-    if (v > __ldcg(slot)) atomicMax(slot, v);
+    asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(slot), "r"(v) : "memory");
 }
 
 // shared-memory matrix descriptor: start, LBO, SBO (bytes, 16-byte units),
@@ -177,10 +181,6 @@ __device__ __forceinline__ void cp_async_wait(int pending) {
     }
 }
 
-__device__ __forceinline__ void named_sync(int id, int n) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
 // 4-D TMA tile load (shared::cluster destination = this CTA's own memory),
 // completing on an mbarrier with a byte count.
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
@@ -198,61 +198,89 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Persistent warp-specialised kernel.
-//   warp 17    : lane 0 streams A: one TMA tile load per chunk (128 rows x
-//                16 complex k, already in the K-major core-matrix order)
-//                into a ring of RST raw stages, several chunks ahead.
+// Persistent warp-specialised kernel, five warpgroups.
 //   warps 0-7  : B columns by cp.async (LOOK chunks ahead), expanded into the
 //                real 2x2 block form; BF16x3: A split into hi/lo from the
 //                raw ring.  TF32 reads A straight from the raw ring.
-//   warp 8     : TMEM allocation; lane 0 issues tcgen05.mma and commits.
-//   warps 9-16 : epilogue, two warps per TMEM lane quadrant (warp % 4), each
-//                draining 32 of the tile's 64 complex columns; two
+//   warps 8-15 : epilogue, two warps per TMEM lane quadrant (warp % 4), each
+//                draining 16 complex columns of each half tile; two
 //                accumulators so that a tile's epilogue overlaps the next
 //                tile's MMAs.
+//   warp 16    : TMEM allocation; lane 0 issues tcgen05.mma and commits.
+//   warp 17    : lane 0 streams A: one TMA tile load per chunk (128 rows x
+//                16 complex k, already in the K-major core-matrix order)
+//                into a ring of RST raw stages, several chunks ahead.
+//   warp 18    : epilogue metadata (instances, rescale, C offsets, E_C),
+//                a ring of MS tiles ahead of the epilogue.
+// The epilogue warpgroups take registers from the others (setmaxnreg).
 constexpr int NPROD = 256;   // warps 0-7
-constexpr int MMA_WARP = 8;
-constexpr int EPI_WARP0 = 9; // warps 9-16: two per TMEM lane quadrant
+constexpr int EPI_WARP0 = 8; // warps 8-15: two per TMEM lane quadrant
 constexpr int NEPI = 256;
+constexpr int MMA_WARP = 16;
 constexpr int TMA_WARP = 17;
-constexpr int NTHREADS = 576;
+constexpr int META_WARP = 18;  // warp 19 idles
+constexpr int NTHREADS = 640;
+// Register split (setmaxnreg, per warpgroup).  The block is launched with
+// 96 registers a thread (640 x 96 = 61440); after the split: producers
+// 256 x 88 + epilogue 256 x 112 + control warpgroup 128 x 72 = 60416.
+constexpr int LAUNCH_REGS = 96, PROD_REGS = 88, EPI_REGS = 112, CTL_REGS = 72;
+static_assert(NPROD * PROD_REGS + NEPI * EPI_REGS + 128 * CTL_REGS <= NTHREADS * LAUNCH_REGS,
+              "register split above the launch allocation");
+constexpr int MS = 4;         // epilogue metadata ring (tiles ahead of the epilogue)
 constexpr int ACC_COLS = 128;
 constexpr int TMEM_COLS2 = 256;
 
 template <int PREC>
 struct Cfg {
     static constexpr int ST = PREC == 1 ? 4 : 3;      // MMA stages (B; BF16x3: also A hi/lo)
-    static constexpr int RST = PREC == 1 ? 6 : 4;     // raw A stages filled by TMA
-    static constexpr int BRST = 6;                    // raw B stages (per-thread cp.async pieces)
+    static constexpr int RST = PREC == 1 ? 4 : 3;     // raw A stages filled by TMA
+    static constexpr int BRST = 4;                    // raw B stages (per-thread cp.async pieces)
     static constexpr int LOOK = BRST - 1;             // B chunks issued ahead
     static constexpr int SLOT_RAW = TBM * TBK * 8;    // FP32 A chunk, [16-byte k column][row]
     static constexpr int SLOT_A = PREC == 2 ? TBM * TBKR * 4 : 0;
     static constexpr int SLOT_B = TBNR * TBKR * 4;
     static constexpr int SLOT_BRAW = TBN * TBK * 8;   // raw complex64 B chunk
+    static constexpr int STAGE = 8 * 32 * 16 * 8;     // 4 KB per epilogue warp, in destination order
     static constexpr int OFF_RAW = 0;
     static constexpr int OFF_A = OFF_RAW + RST * SLOT_RAW;
     static constexpr int OFF_B = OFF_A + ST * SLOT_A;
     static constexpr int OFF_BRAW = OFF_B + ST * SLOT_B;
-    static constexpr int OFF_CTRL = OFF_BRAW + BRST * SLOT_BRAW;
+    static constexpr int OFF_STAGE = OFF_BRAW + BRST * SLOT_BRAW;
+    static constexpr int OFF_CTRL = OFF_STAGE + STAGE;
 };
 
-struct EpiMeta {
-    int64_t cbase[TBN];
-    int64_t inst[TBN];
-    float sc[TBN];
-    int32_t eb[TBN];
-    int32_t EB[TBN];
-    uint32_t mx[TBN];
-    int32_t ea, EA;
-    int32_t mt, pad;
+// Per-tile epilogue metadata, written by the metadata warp into a ring of
+// MS slots ahead of the epilogue.
+struct alignas(16) EpiMeta {
+    int32_t inst[TBN];    // output instance of each column (-1: none)
+    float sc[TBN];        // 2^-(ea + eb): the column's power-of-two rescale
+    int64_t base;         // element offset of tile element (row 0, column 0) in C
+    int32_t ncv, pad;     // valid columns
+};
+
+// Destination order of one epilogue warp's 32 rows x 16 complex columns.
+// Its 9 tile bits (row bits 0-4 = lane, column bits 0-3) are sorted by the
+// C offset they add; bit k of a compressed index is the k-th of them.
+// Compressed neighbours land at neighbouring addresses wherever the C
+// layout allows, so each store instruction covers one contiguous run.
+struct EpiMap {
+    int64_t doff[9];      // C offset of compressed bit k
+    int64_t offI[8];      // C offset of compressed bits 6-8 = i (store round)
+    int64_t qoff[4];      // C offset of row block 32q (row bits 5, 6)
+    int64_t hoff[4];      // C offset of column block 16s (column bits 4, 5)
+    int32_t colI[8];      // column of compressed bits 6-8 = i
+    int32_t dcol[9];      // column of compressed bit k
+    int32_t rank[9];      // compressed position of warp bit b (rows 0-4, columns 0-3)
+    int32_t pair;         // doff[0] == 1: compressed elements 2u, 2u+1 are one 16-byte store
+    int32_t nrows;        // valid rows per tile (min(M, 128))
 };
 
 struct Ctrl {
-    uint64_t full[4], empty[4], rfull[8], rempty[8], tfull[2], tempty[2];
+    uint64_t full[4], empty[4], rfull[8], rempty[8], tfull[2], tempty[2], mfull[MS], mempty[MS];
     uint32_t tmem_base;
     int32_t abort_;
-    int32_t epi_fail[2];  // epilogue-uniform abort decisions, by tile parity
-    EpiMeta epi[2];
+    EpiMeta epi[MS];
+    EpiMap map;
 };
 
 template <int PREC>
@@ -261,13 +289,29 @@ constexpr size_t smem_bytes() {
 }
 static_assert(smem_bytes<1>() <= 232448 && smem_bytes<2>() <= 232448, "shared memory above 227 KB");
 
-// tile T of a step: column-tile record e = T / mtiles, row tile T % mtiles
-__device__ __forceinline__ int4 tile_rec(const StepDesc &d, int64_t T, int64_t mtiles) {
-    return __ldg(d.trec + T / mtiles);
+// Tile T of a step.  The tiles of one group (its column tiles x row tiles)
+// are numbered row tile major, column tile minor, so the column tiles that
+// share an A row tile run on neighbouring CTAs and A is read from DRAM
+// about once.  Returns the column-tile record with its first column, and
+// the row tile in mt.
+__device__ __forceinline__ int4 tile_decode(const StepDesc &d, int64_t T, int64_t mtiles, int64_t &mt) {
+    const int64_t e0 = T / mtiles;  // some column tile of T's group
+    int4 r = __ldg(d.trec + e0);
+    const int64_t nct = ((int64_t(r.y) << d.nb) + TBN - 1) / TBN;
+    const int64_t f = e0 - r.w / TBN;  // the group's first column tile
+    const int64_t local = T - f * mtiles;
+    mt = local / nct;
+    r.w = int((local - mt * nct) * TBN);
+    return r;
 }
 
+// XOR swizzle of a warp staging area (256 16-byte units): eight consecutive
+// units stay within one 128-byte row, and units that differ in higher bits
+// spread over the banks
+__device__ __forceinline__ int stage_swz(int u) { return u ^ (((u >> 3) ^ (u >> 6)) & 7); }
+
 template <int PREC>
-__global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 registers (5 warps on a sub-partition)
+__global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 warps on a sub-partition)
     k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA) {
     using C = Cfg<PREC>;
     extern __shared__ uint8_t smem_raw[];
@@ -276,7 +320,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 register
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_tiles = d.n_ctab * mtiles;
     const int N = 1 << d.nb;
-    const int64_t M = int64_t(1) << d.mb;
     const int K = 1 << d.kb;
     const int nch = (K + TBK - 1) / TBK;
     const int64_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -301,8 +344,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 register
             mbar_init(&X.tfull[a], 1);
             mbar_init(&X.tempty[a], NEPI);
         }
+        for (int s = 0; s < MS; ++s) {
+            mbar_init(&X.mfull[s], 32);
+            mbar_init(&X.mempty[s], NEPI);
+        }
         X.abort_ = *reinterpret_cast<volatile int32_t *>(err);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // destination order of an epilogue warp's block (same for every tile)
+        EpiMap &mp = X.map;
+        constexpr int64_t NONE = 0x7fffffffffffffffLL;  // row bits at or above mb: never stored
+        auto rowkey = [&](int b) -> int64_t { return b < d.mb ? (int64_t(1) << d.pCm[b]) : NONE; };
+        auto colkey = [&](int j) -> int64_t { return j < d.nb ? (int64_t(1) << d.pCn[j]) : (d.sC << (j - d.nb)); };
+        int64_t key[9];
+        for (int b = 0; b < 5; ++b) key[b] = rowkey(b);
+        for (int j = 0; j < 4; ++j) key[5 + j] = colkey(j);
+        int perm[9];
+        for (int b = 0; b < 9; ++b) perm[b] = b;
+        for (int a = 1; a < 9; ++a)
+            for (int b = a; b > 0 && key[perm[b]] < key[perm[b - 1]]; --b) {
+                const int t = perm[b];
+                perm[b] = perm[b - 1];
+                perm[b - 1] = t;
+            }
+        for (int k = 0; k < 9; ++k) {
+            const int b = perm[k];
+            mp.rank[b] = k;
+            mp.doff[k] = key[b];
+            mp.dcol[k] = b < 5 ? 0 : (1 << (b - 5));
+        }
+        for (int i = 0; i < 8; ++i) {
+            int64_t o = 0;
+            int c = 0;
+            for (int k = 6; k < 9; ++k)
+                if ((i >> (k - 6)) & 1) {
+                    o += mp.doff[k];
+                    c += mp.dcol[k];
+                }
+            mp.offI[i] = o;
+            mp.colI[i] = c;
+        }
+        for (int q = 0; q < 4; ++q) {
+            mp.qoff[q] = ((q & 1) && d.mb > 5 ? rowkey(5) : 0) + ((q & 2) && d.mb > 6 ? rowkey(6) : 0);
+            mp.hoff[q] = ((q & 1) ? colkey(4) : 0) + ((q & 2) ? colkey(5) : 0);
+        }
+        mp.pair = mp.doff[0] == 1;
+        mp.nrows = d.mb >= 7 ? TBM : (1 << d.mb);
     }
     tc_fence_before();
     __syncthreads();
@@ -315,16 +401,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 register
     };
     auto tile_of = [&](int64_t l) { return int64_t(blockIdx.x) + l * gridDim.x; };
 
+    if (warp >= MMA_WARP) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(CTL_REGS));
     if (warp == TMA_WARP) {
         // ------------------------------------------------------------ A stream
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             int64_t issued = 0;
             bool ok = true;
+            int64_t mt_n = 0;
+            int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_n) : make_int4(0, 0, 0, 0);
             for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
-                const int64_t T = tile_of(l);
-                const int4 r = tile_rec(d, T, mtiles);
-                const int m0 = int((T % mtiles) * TBM);
+                const int4 r = r_n;  // the next tile's record is fetched one tile ahead
+                const int m0 = int(mt_n * TBM);
+                if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_n);
                 for (int c = 0; c < nch; ++c, ++issued) {
                     const int rs = int(issued % C::RST);
                     if (!mbar_wait(&X.rempty[rs], (uint32_t(issued / C::RST) & 1u) ^ 1u)) {
@@ -343,6 +432,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 register
         __syncwarp();
     } else if (warp < NPROD / 32) {
         // ------------------------------------------------------------ B loads, A split
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(PROD_REGS));
         const int bcol = tid & 63, kqb = tid >> 6;
         int64_t bbase[2] = {-1, -1};
         int64_t issued = 0;
@@ -353,9 +443,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 register
             const int64_t gc = int64_t(r.w) + bcol;
             return gc < (int64_t(r.y) << d.nb) ? int64_t(r.x) + (gc >> d.nb) : -1;
         };
+        int64_t mt_unused;
         if (my_tiles > 0) {
-            rec_pf[0] = tile_rec(d, tile_of(0), mtiles);
-            if (my_tiles > 1) rec_pf[1] = tile_rec(d, tile_of(1), mtiles);
+            rec_pf[0] = tile_decode(d, tile_of(0), mtiles, mt_unused);
+            if (my_tiles > 1) rec_pf[1] = tile_decode(d, tile_of(1), mtiles, mt_unused);
             const int64_t ci = col_inst(rec_pf[0]);
             ib_pf = ci >= 0 ? __ldg(d.instab + ci).y : 0;
         }
@@ -376,7 +467,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 register
                         const int64_t cn = col_inst(rec_pf[(l + 1) & 1]);
                         ib_pf = cn >= 0 ? __ldg(d.instab + cn).y : 0;
                     }
-                    if (l + 2 < my_tiles) rec_pf[l & 1] = tile_rec(d, tile_of(l + 2), mtiles);
+                    if (l + 2 < my_tiles) rec_pf[l & 1] = tile_decode(d, tile_of(l + 2), mtiles, mt_unused);
                 }
                 {  // B: this thread's column, k quad kqb
                     const int64_t bb = bbase[l & 1];
@@ -521,125 +612,226 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 18 warps: at most 96 register
             }
         }
         __syncwarp();
-    } else {
-        // ------------------------------------------------------------ epilogue
-        const int e = tid - EPI_WARP0 * 32;     // 0..255
-        const int lanegrp = warp & 3;           // TMEM lanes 32*lanegrp ...
-        const int half = (warp - EPI_WARP0) >> 2;  // complex columns 32*half ...
-        const int row = lanegrp * 32 + lane;
-        // metadata of tile l into X.epi[l & 1] (threads 0..63: one column each)
-        auto meta = [&](int64_t l) {
-            EpiMeta &em = X.epi[l & 1];
-            const int64_t T = int64_t(blockIdx.x) + l * gridDim.x;
-            const int4 r = tile_rec(d, T, mtiles);
-            if (e == 0) {
-                em.ea = d.mxA ? exp_of(__ldg(d.mxA + r.z)) : 0;
-                em.EA = __ldg(d.EA + r.z);
-                em.mt = int(T % mtiles);
+    } else if (warp == META_WARP) {
+        // ------------------------------------------------------------ epilogue metadata
+        // Software pipeline over this CTA's tiles: round j loads the column
+        // records of tile j+2, the B instances of tile j+1 and the operand
+        // exponents of tile j together (one memory latency per round), then
+        // fills tile j's slot (instance and rescale per column, C base
+        // offset, valid columns).  The instance exponents E_C are written
+        // here as well, once per instance: at its n = 0 column in row tile 0.
+        int64_t mt0 = 0, mt1 = 0, mt2 = 0;
+        int4 r0 = make_int4(0, 0, 0, 0), r1 = r0, r2 = r0;
+        int ib0[2] = {-1, -1};
+        auto col_inst = [&](const int4 &r, int c) -> int {  // instance of tile column c, or -1
+            const int64_t gc = int64_t(r.w) + c;
+            return gc < (int64_t(r.y) << d.nb) ? r.x + int(gc >> d.nb) : -1;
+        };
+        if (my_tiles > 0) {
+            r0 = tile_decode(d, tile_of(0), mtiles, mt0);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int i = col_inst(r0, lane + 32 * q);
+                ib0[q] = i >= 0 ? __ldg(d.instab + i).y : -1;
             }
-            if (e < TBN) {
-                const int64_t gc = int64_t(r.w) + e;
-                em.mx[e] = 0;
-                if (gc < (int64_t(r.y) << d.nb)) {
-                    const int64_t inst = int64_t(r.x) + (gc >> d.nb);
-                    const int ib = __ldg(d.instab + inst).y;
-                    em.inst[e] = inst;
-                    em.cbase[e] = inst * d.sC + dep(gc & (N - 1), d.pCn, d.nb);
-                    em.eb[e] = d.mxB ? exp_of(__ldg(d.mxB + ib)) : 0;
-                    em.EB[e] = __ldg(d.EB + ib);
-                } else {
-                    em.inst[e] = -1;
-                    em.cbase[e] = -1;
-                    em.eb[e] = 0;
-                    em.EB[e] = 0;
+        }
+        if (my_tiles > 1) r1 = tile_decode(d, tile_of(1), mtiles, mt1);
+        bool ok = true;
+        for (int64_t j = 0; j < my_tiles; ++j) {
+            uint32_t mxb[2] = {0u, 0u};
+            int32_t EBv[2] = {0, 0};
+            int ib1[2] = {-1, -1};
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (ib0[q] >= 0) {
+                    mxb[q] = d.mxB ? __ldg(d.mxB + ib0[q]) : 0u;
+                    EBv[q] = __ldg(d.EB + ib0[q]);
+                }
+            const uint32_t mxa = d.mxA ? __ldg(d.mxA + r0.z) : 0u;
+            const int32_t EAv = __ldg(d.EA + r0.z);
+            if (j + 1 < my_tiles) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int i = col_inst(r1, lane + 32 * q);
+                    ib1[q] = i >= 0 ? __ldg(d.instab + i).y : -1;
                 }
             }
-        };
-        // per-column scale 2^-(ea + eb), once the tile's exponents are in place
-        auto scales = [&](int64_t l) {
-            EpiMeta &em = X.epi[l & 1];
-            if (e < TBN) em.sc[e] = pow2f(-(em.ea + em.eb[e]));
-        };
-        if (my_tiles > 0) meta(0);
-        if (e == 0) X.epi_fail[0] = X.epi_fail[1] = 0;
-        named_sync(1, NEPI);
-        if (my_tiles > 0) scales(0);
-        for (int64_t l = 0; l < my_tiles; ++l) {
-            const int acc = int(l & 1);
-            EpiMeta &em = X.epi[acc];
-            if (l + 1 < my_tiles) meta(l + 1);  // overlaps the wait for tile l's accumulator
-            const int64_t m0 = int64_t(em.mt) * TBM;
-            if (!mbar_wait(&X.tfull[acc], uint32_t(l >> 1) & 1u)) atomicOr(&X.epi_fail[acc], 1);
-            if (e == 0 && *abort_flag) atomicOr(&X.epi_fail[acc], 1);
-            named_sync(1, NEPI);
-            if (X.epi_fail[acc]) {  // uniform: read between barriers
-                if (e == 0) give_up();
+            if (j + 2 < my_tiles) r2 = tile_decode(d, tile_of(j + 2), mtiles, mt2);
+            const int slot = int(j % MS);
+            const bool w = mbar_wait(&X.mempty[slot], (uint32_t(j / MS) & 1u) ^ 1u);
+            if (!__all_sync(0xffffffffu, w) || __any_sync(0xffffffffu, *abort_flag != 0)) {
+                ok = false;
                 break;
             }
-            if (e == 0) X.epi_fail[acc ^ 1] = 0;  // next tile's slot; its last readers are done
+            EpiMeta &em = X.epi[slot];
+            const int ea = d.mxA ? exp_of(mxa) : 0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int c = lane + 32 * q;
+                const int inst = col_inst(r0, c);
+                const int eb = d.mxB ? exp_of(mxb[q]) : 0;
+                em.inst[c] = inst;
+                em.sc[c] = pow2f(-(ea + eb));
+                if (inst >= 0 && mt0 == 0 && ((int64_t(r0.w) + c) & (N - 1)) == 0) d.EC[inst] = EAv + ea + EBv[q] + eb;
+            }
+            if (lane == 0) {
+                const int64_t ncols = int64_t(r0.y) << d.nb;
+                em.base = (int64_t(r0.x) + (r0.w >> d.nb)) * d.sC + dep(int64_t(r0.w) & (N - 1), d.pCn, d.nb) +
+                          dep(mt0 * TBM, d.pCm, d.mb);
+                em.ncv = int(ncols - r0.w < TBN ? ncols - r0.w : TBN);
+            }
+            mbar_arrive(&X.mfull[slot]);  // every lane (count 32): its writes are released
+            r0 = r1;
+            mt0 = mt1;
+            ib0[0] = ib1[0];
+            ib0[1] = ib1[1];
+            r1 = r2;
+            mt1 = mt2;
+        }
+        if (!ok) give_up();
+        __syncwarp();
+    } else if (warp < EPI_WARP0 + NEPI / 32) {
+        // ------------------------------------------------------------ epilogue
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(EPI_REGS));
+        // Each warp drains 32 rows (its TMEM lane quadrant) x 16 complex
+        // columns of each half tile: TMEM -> registers (max-|x| per
+        // instance, power-of-two scale) -> its own 4 KB of shared memory in
+        // destination order -> 16-byte stores, one contiguous run per
+        // instruction where the C layout allows.  No barrier couples the
+        // epilogue warps; the accumulator is released as soon as its last
+        // half is in registers.
+        const int ew = warp - EPI_WARP0;  // 0..7
+        const int lanegrp = warp & 3;     // TMEM lanes 32*lanegrp ...
+        const int sub = ew >> 2;          // 16-column block of a half
+        const EpiMap &mp = X.map;
+        uint8_t *wst = sm + C::OFF_STAGE + ew * 4096;
+        // staging byte address of compressed index e: (swz(e >> 1) << 4) |
+        // ((e & 1) << 3), linear over GF(2) in the bits of e; the row (lane)
+        // and column bits of an element are disjoint, so its address is the
+        // XOR of a per-lane part and a per-column part
+        auto saddr = [](int ec) { return (stage_swz(ec >> 1) << 4) | ((ec & 1) << 3); };
+        int erow = 0;  // compressed bits of this lane's row
+#pragma unroll
+        for (int b = 0; b < 5; ++b)
+            if ((lane >> b) & 1) erow |= 1 << mp.rank[b];
+        const int arow = saddr(erow);
+        int acol[4];  // staging address parts of column bits 0-3
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acol[j] = saddr(1 << mp.rank[5 + j]);
+        const int alane = stage_swz(lane) << 4;  // store rounds read unit lane + 32 i
+        int64_t offL = 0;  // compressed bits 1-5 = lane in the store rounds
+        int colL = 0;
+#pragma unroll
+        for (int k = 1; k <= 5; ++k)
+            if ((lane >> (k - 1)) & 1) {
+                offL += mp.doff[k];
+                colL += mp.dcol[k];
+            }
+        const int64_t doff0 = mp.doff[0];
+        const int dcol0 = mp.dcol[0];
+        const bool pair = mp.pair != 0;
+        const bool rows_ok = lanegrp * 32 < mp.nrows;  // M = 64: quadrants 2 and 3 hold no rows
+        const int64_t qoff = mp.qoff[lanegrp];
+        for (int64_t l = 0; l < my_tiles; ++l) {
+            const int acc = int(l & 1), slot = int(l % MS);
+            bool w = mbar_wait(&X.mfull[slot], uint32_t(l / MS) & 1u);
+            w = w && mbar_wait(&X.tfull[acc], uint32_t(l >> 1) & 1u);
+            if (!__all_sync(0xffffffffu, w) || __any_sync(0xffffffffu, *abort_flag != 0)) {
+                give_up();
+                break;
+            }
             tc_fence_after();
-            const int64_t m = m0 + row;
-            const int64_t offc = m < M ? dep(m, d.pCm, d.mb) : -1;
-            // this warp's 32 complex columns = 64 accumulator columns, in two
-            // rounds of 16 complex columns (two x16 loads and one wait each).
-            // Scaled stores, then the per-instance max-|x|: each column's
-            // warp maximum lands in lane j = column, and runs of min(N, 32)
-            // lanes (one instance's columns) are combined with xor-shuffles.
-            // No branch depends on the column, so the loop pipelines.
-            uint32_t colmax = 0;
+            const EpiMeta &em = X.epi[slot];
+            const int ncv = em.ncv;
+            const int nh = ncv > TBN / 2 ? 2 : 1;
+            for (int h = 0; h < nh; ++h) {
+                const int c0 = h * 32 + sub * 16;      // first column of this warp's block
+                const bool act = rows_ok && c0 < ncv;  // warp-uniform
+                // two passes of 8 complex columns (16 accumulator columns)
 #pragma unroll
-            for (int rnd = 0; rnd < 2; ++rnd) {
-                float v[32];
-                {
-                    const uint32_t ta = tmem + uint32_t(acc * ACC_COLS + half * 64 + rnd * 32) + (uint32_t(lanegrp * 32) << 16);
-                    uint32_t r[32];
-#pragma unroll
-                    for (int q = 0; q < 2; ++q)
+                for (int p = 0; p < 2; ++p) {
+                    float v[16];
+                    if (act) {
+                        const uint32_t ta = tmem + uint32_t(acc * ACC_COLS + (c0 + 8 * p) * 2) +
+                                            (uint32_t(lanegrp * 32) << 16);
+                        uint32_t r[16];
                         asm volatile(
                             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                            : "=r"(r[16 * q + 0]), "=r"(r[16 * q + 1]), "=r"(r[16 * q + 2]), "=r"(r[16 * q + 3]),
-                              "=r"(r[16 * q + 4]), "=r"(r[16 * q + 5]), "=r"(r[16 * q + 6]), "=r"(r[16 * q + 7]),
-                              "=r"(r[16 * q + 8]), "=r"(r[16 * q + 9]), "=r"(r[16 * q + 10]), "=r"(r[16 * q + 11]),
-                              "=r"(r[16 * q + 12]), "=r"(r[16 * q + 13]), "=r"(r[16 * q + 14]), "=r"(r[16 * q + 15])
-                            : "r"(ta + uint32_t(16 * q)));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                              "=r"(r[14]), "=r"(r[15])
+                            : "r"(ta));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
-                }
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = rnd * 16 + jj;
-                    const int col = half * 32 + j;
-                    const int64_t cb = em.cbase[col];
-                    const float sc = em.sc[col];
-                    const float2 o = make_float2(v[2 * jj] * sc, v[2 * jj + 1] * sc);
-                    const bool ok = offc >= 0 && cb >= 0;
-                    if (ok) d.C[cb + offc] = o;
+                        for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+                    }
+                    if (h == nh - 1 && p == 1) {  // the accumulator is free for the tile after next
+                        tc_fence_before();
+                        mbar_arrive(&X.tempty[acc]);
+                    }
+                    if (!act) continue;
+                    const int cp = c0 + 8 * p;  // first column of this pass
                     if (d.mxC) {
-                        const uint32_t mj = ok ? __float_as_uint(fmaxf(fabsf(o.x), fabsf(o.y))) : 0u;
-                        const uint32_t rj = __reduce_max_sync(0xffffffffu, mj);
-                        colmax = lane == j ? rj : colmax;
+                        // max-|component| of each instance's columns: runs of
+                        // min(N, 8) columns folded in registers, then one warp
+                        // reduction per run; scaled by the run's power of two
+                        // (exact) and merged into the instance's word
+                        const int run = N < 8 ? N : 8;
+                        uint32_t a[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) a[j] = __float_as_uint(fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
+#pragma unroll
+                        for (int s = 1; s < 8; s <<= 1)
+                            if (s < run) {
+#pragma unroll
+                                for (int j = 0; j < 8; j += 2 * s) a[j] = max(a[j], a[j + s]);
+                            }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if ((j & (run - 1)) == 0 && cp + j < ncv) {
+                                const uint32_t r = __reduce_max_sync(0xffffffffu, a[j]);
+                                if (lane == 0 && r)
+                                    record_max(d.mxC + em.inst[cp + j], __float_as_uint(__uint_as_float(r) * em.sc[cp + j]));
+                            }
+                    }
+                    // scale and stage in destination order
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const float4 sc4 = *reinterpret_cast<const float4 *>(&em.sc[cp + 4 * q]);
+                        const float scq[4] = {sc4.x, sc4.y, sc4.z, sc4.w};
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int jj = 8 * p + 4 * q + t;  // column within the warp's block
+                            int a = arow;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if ((jj >> j) & 1) a ^= acol[j];
+                            *reinterpret_cast<float2 *>(wst + a) =
+                                make_float2(v[2 * (4 * q + t)] * scq[t], v[2 * (4 * q + t) + 1] * scq[t]);
+                        }
                     }
                 }
+                if (!act) continue;
+                __syncwarp();
+                const int64_t wb = em.base + qoff + mp.hoff[h * 2 + sub] + offL;
+                const int ncw = ncv - c0;  // valid columns of this block
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    // compressed elements 2u, 2u + 1 with u = lane + 32 i
+                    const float4 val = *reinterpret_cast<const float4 *>(wst + (alane ^ (stage_swz(32 * i) << 4)));
+                    const int c = colL + mp.colI[i];
+                    const bool v0 = c < ncw, v1 = c + dcol0 < ncw;
+                    float2 *dst = d.C + (wb + mp.offI[i]);
+                    if (pair && v0 && v1) {
+                        *reinterpret_cast<float4 *>(dst) = val;
+                    } else {
+                        if (v0) dst[0] = make_float2(val.x, val.y);
+                        if (v1) dst[doff0] = make_float2(val.z, val.w);
+                    }
+                }
+                __syncwarp();  // the staging area is rewritten by the next half
             }
-            if (d.mxC) {
-                const int runlen = N < 32 ? N : 32;
-                for (int sft = 1; sft < runlen; sft <<= 1) colmax = max(colmax, __shfl_xor_sync(0xffffffffu, colmax, sft));
-                if ((lane & (runlen - 1)) == 0 && colmax) atomicMax(&em.mx[half * 32 + lane], colmax);
-            }
-            tc_fence_before();
-            mbar_arrive(&X.tempty[acc]);
-            named_sync(1, NEPI);
-            if (e < TBN && em.inst[e] >= 0) {
-                // exponent of the instance, written once (at its n = 0 column, row tile 0)
-                const int64_t gc_n = em.cbase[e] - em.inst[e] * d.sC;  // dep(n) == 0 iff n == 0
-                if (gc_n == 0 && em.mt == 0) d.EC[em.inst[e]] = em.EA + em.ea + em.EB[e] + em.eb[e];
-                // em.mx[e] != 0 only where a run of this instance's columns
-                // starts (instance start, or the second epilogue half)
-                if (d.mxC && em.mx[e]) record_max(d.mxC + em.inst[e], em.mx[e]);
-            }
-            if (l + 1 < my_tiles) scales(l + 1);  // meta(l + 1) is visible since the last barrier
-            named_sync(1, NEPI);  // em (this parity) is rewritten by meta(l + 2)
+            mbar_arrive(&X.mempty[slot]);
         }
     }
     tc_fence_before();

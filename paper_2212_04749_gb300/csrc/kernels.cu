@@ -56,8 +56,10 @@ __device__ __forceinline__ int64_t dep(int64_t x, const int8_t *pos, int nbits) 
 
 // raise the recorded maximum only when it grows (monotone, so the
 // unsynchronised read is safe)
+// fire-and-forget global max (a reduction, no returned value: the issuing
+// thread never waits on memory)
 __device__ __forceinline__ void record_max(uint32_t *slot, uint32_t v) {
-    if (v > __ldcg(slot)) atomicMax(slot, v);
+    asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(slot), "r"(v) : "memory");
 }
 
 __global__ void k_fill(const FillJobD *__restrict__ jobs, int64_t njobs, const LeafHighD *__restrict__ highs,
