@@ -190,9 +190,96 @@ int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, voi
 /* Override the kernel family of one step (-1: the plan's choice; 0: per-row
  * kernel, valid when N <= 16 and K*N <= 256; 1: grouped GEMM -- tensor
  * cores for TN_TF32 / TN_BF16X3 when the shape allows, CUDA cores
- * otherwise).  Used by the autotuner and the cost model.  TN_EINVAL for a
- * family the step's shape does not allow. */
+ * otherwise), with the first schedule of that family (configuration 0 or
+ * 2 below).  TN_EINVAL for a family the step's shape does not allow. */
 int tn_plan_set_kernel(tn_plan_t plan, int32_t step, int32_t kernel);
+
+/* ---------------------------------------------------------------------
+ * Per-step kernel configuration (config selection; no counterpart in the
+ * paper, whose Sunway kernels are fixed): the autotuner measures, and the
+ * cost model predicts, each step's time under each configuration.
+ *
+ * A configuration c in [0, TN_NCONFIG) is a kernel family and a schedule:
+ *   0  per-row kernel, blocks of up to 16 row passes   (needs N <= 16, K*N <= 256)
+ *   1  per-row kernel, blocks of up to 4 row passes    (same condition)
+ *   2  grouped GEMM, consecutive blocks walk the rows of one column tile
+ *      (SIMT) / the column tiles of one row tile (tensor cores)
+ *   3  grouped GEMM, the other walk order
+ * The GEMM runs on the tensor cores for TN_TF32 / TN_BF16X3 where the shape
+ * allows (K >= 8, 64 <= M < 2^31), on the CUDA cores otherwise. */
+#define TN_NCONFIG 4
+
+/* Set step `step` to configuration `config` (-1: the plan's own choice).
+ * TN_EINVAL for a configuration the step's shape does not allow. */
+int tn_plan_set_config(tn_plan_t plan, int32_t step, int32_t config);
+
+/* Configuration each step will run with (the plan's choice where none was
+ * set); n entries. */
+int tn_plan_get_configs(tn_plan_t plan, int32_t *config, int32_t n);
+
+/* Cost-model features: TN_NFEAT floats per step for configuration `config`
+ * at `precision` (row-major n_steps x TN_NFEAT, host memory), and whether
+ * the configuration is allowed (eligible, n_steps int32, may be NULL).
+ * Host only.  Features, all O(1): the operand and output bit counts
+ * (mb, kb, nb, ranks), log2 of the instance, group and column counts, the
+ * contiguous address runs of A, B and C (the permutation class), log2 of
+ * flops and bytes per pass, one-hot precision, kernel family, schedule, and
+ * log2 of the output rows. */
+#define TN_NFEAT 24
+int tn_plan_features(tn_plan_t plan, int precision, int32_t config, float *feat, int32_t *eligible, int32_t n);
+
+/* Exhaustive autotuner.  For every configuration c, run the whole
+ * contraction (all slice batches, `reps` + 1 times, the first discarded)
+ * with every selected step (step_mask[s] != 0, or all steps if step_mask is
+ * NULL) that allows c set to c, the others unchanged, and time every step
+ * with CUDA events.  times (host, n_steps x TN_NCONFIG, may be NULL)
+ * receives the fastest time per pass of each (step, configuration) in ms,
+ * NaN where not measured.  Afterwards every selected step is set to its
+ * fastest configuration.  amps_scratch: device complex128 buffer of k
+ * entries the runs accumulate into (its contents are meaningless
+ * afterwards).  Needs a bound workspace; synchronises `stream`. */
+int tn_plan_autotune(tn_plan_t plan, int precision, int32_t reps, const uint8_t *step_mask, double *amps_scratch,
+                     double *times, void *stream);
+
+/* Cost-model selection: predict log2(ms per pass) of every (step, allowed
+ * configuration) with the FP16 network params16 (device, TN_MLP_NPARAMS
+ * halves, see tn_mlp_to_half), set each step to its predicted fastest
+ * configuration, and flag in uncertain (host, n_steps int32, may be NULL)
+ * the steps whose two best predictions lie within `margin` (log2 units):
+ * those are the steps to hand to tn_plan_autotune (its step_mask) as the
+ * fallback.  scratch: device buffer of at least
+ * n_steps * TN_NCONFIG * (TN_NFEAT + 1) * 4 bytes.  Synchronises `stream`. */
+int tn_plan_select(tn_plan_t plan, int precision, const uint16_t *params16, float margin, void *scratch,
+                   size_t scratch_bytes, int32_t *uncertain, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Cost-model network: MLP, TN_MLP_IN inputs, two ReLU hidden layers of
+ * TN_MLP_HIDDEN units, one output.  Parameters: one flat FP32 device array
+ * of TN_MLP_NPARAMS floats, in order W1 [H][D] (row j = hidden unit j), b1
+ * [H], W2 [H][H], b2 [H], w3 [H], b3 [1].  X: device, n x TN_MLP_IN FP32,
+ * row-major.  All calls are asynchronous on `stream` and allocate nothing. */
+#define TN_MLP_IN TN_NFEAT
+#define TN_MLP_HIDDEN 128
+#define TN_MLP_NPARAMS (TN_MLP_HIDDEN * TN_MLP_IN + TN_MLP_HIDDEN + TN_MLP_HIDDEN * TN_MLP_HIDDEN + 2 * TN_MLP_HIDDEN + 1)
+
+/* y[i] = network(X[i]) in FP32. */
+int tn_mlp_forward(const float *params, const float *X, int64_t n, float *y, void *stream);
+/* Gradient of L = (1/n) sum_i (y_i - t_i)^2 with respect to the parameters
+ * (grad: device, TN_MLP_NPARAMS floats) and L itself (loss: device float,
+ * may be NULL); deterministic (per-block partials summed in a fixed order
+ * in `scratch`, device, >= tn_mlp_grad_scratch_bytes(n) bytes). */
+size_t tn_mlp_grad_scratch_bytes(int64_t n);
+int tn_mlp_grad(const float *params, const float *X, const float *t, int64_t n, float *grad, float *loss,
+                void *scratch, size_t scratch_bytes, void *stream);
+/* One Adam step (bias-corrected first and second moments m, v: device,
+ * TN_MLP_NPARAMS floats each, zero before step 1; step counts from 1). */
+int tn_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr, float beta1,
+                float beta2, float eps, void *stream);
+/* FP16 copy of the parameters (round to nearest) for inference. */
+int tn_mlp_to_half(const float *params, uint16_t *params16, void *stream);
+/* y[i] = network(X[i]) with FP16 weights and activations (FP32 sums every
+ * 16 products). */
+int tn_mlp_forward_f16(const uint16_t *params16, const float *X, int64_t n, float *y, void *stream);
 
 /* Synchronise `stream` and report device-side failures of earlier calls on
  * this plan: TN_ETIMEOUT if a bounded wait inside a kernel gave up (the

@@ -47,7 +47,7 @@ struct PlanObj {
     std::vector<int> ev_step;             // step of each recorded pair
     size_t ev_used = 0;
     std::vector<int32_t> step_kernel;     // kernel family each step ran last (0 row, 1 SIMT GEMM, 2 TC GEMM)
-    std::vector<int32_t> kernel_override; // per step: -1 plan choice, 0 row, 1 GEMM
+    std::vector<int32_t> config_override; // per step: -1 plan choice, else a configuration (tn.h)
     struct GraphKey {
         int precision;
         int64_t lo, hi;
@@ -135,14 +135,25 @@ void build_descs(PlanObj *o) {
     }
 }
 
+// Configurations (tn.h): 0, 1 per-row kernel (schedule 0, 1); 2, 3 grouped
+// GEMM (schedule 0, 1).
+bool config_allowed(const tnp::Step &S, int c) {
+    if (c < 0 || c >= TN_NCONFIG) return false;
+    return c >= 2 || (S.nb <= 4 && S.kb + S.nb <= 8);
+}
+
+int effective_config(const PlanObj *o, int s) {
+    if (s < (int)o->config_override.size() && o->config_override[s] >= 0) return o->config_override[s];
+    return o->P.steps[s].kernel == 0 ? 0 : 2;
+}
+
 int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
-    const tnp::Step &S = o->P.steps[s];
-    const tnk::StepDesc &d = o->desc[s];
+    const int cfg = effective_config(o, s);
+    tnk::StepDesc d = o->desc[s];
+    d.sched = cfg & 1;
     cudaError_t e;
     int fam;
-    int want = S.kernel;
-    if (s < (int)o->kernel_override.size() && o->kernel_override[s] >= 0) want = o->kernel_override[s];
-    if (want == 0) {
+    if (cfg < 2) {
         fam = 0;
         e = tnk::launch_step_row(d, st);
     } else if (precision != TN_FP32 && tnk::gemm_tc_supports(d)) {
@@ -158,6 +169,53 @@ int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
     if (e != cudaSuccess)
         return set_err(TN_ECUDA, "step " + std::to_string(s) + ": " + cudaGetErrorString(e));
     return TN_OK;
+}
+
+// Cost-model features of step s under configuration c (tn.h, TN_NFEAT).
+void step_features(const tnp::Plan &P, int s, int precision, int c, float *f) {
+    const tnp::Step &S = P.steps[s];
+    const tnp::Node &nd = P.nodes[S.node], &A = P.nodes[S.a], &B = P.nodes[S.b];
+    auto lg = [](double x) { return float(std::log2(x > 1.0 ? x : 1.0)); };
+    auto run = [](const std::vector<int8_t> &pos) {
+        int j = 0;
+        while (j < (int)pos.size() && pos[j] == j) ++j;
+        return j;
+    };
+    int crun = 0;  // lowest C address bits held by consecutive m bits
+    while (crun < S.mb && S.pCm[crun] == crun) ++crun;
+    tnk::StepDesc t;
+    std::memset(&t, 0, sizeof(t));
+    t.mb = S.mb;
+    t.kb = S.kb;
+    t.nb = S.nb;
+    const bool gemm = c >= 2;
+    const bool tc = gemm && precision != TN_FP32 && tnk::gemm_tc_supports(t);
+    const double ng = double(S.n_groups > 0 ? S.n_groups : 1);
+    int i = 0;
+    f[i++] = S.mb / 32.f;
+    f[i++] = S.kb / 32.f;
+    f[i++] = S.nb / 32.f;
+    f[i++] = A.rank / 32.f;
+    f[i++] = B.rank / 32.f;
+    f[i++] = lg(double(nd.n_inst)) / 32.f;
+    f[i++] = lg(double(A.n_inst)) / 32.f;
+    f[i++] = lg(double(B.n_inst)) / 32.f;
+    f[i++] = lg(ng) / 32.f;
+    f[i++] = lg(double(nd.n_inst) / ng * std::ldexp(1.0, S.nb)) / 32.f;
+    f[i++] = run(S.pAm) / 32.f;
+    f[i++] = run(S.pAk) / 32.f;
+    f[i++] = run(S.pBk) / 32.f;
+    f[i++] = run(S.pBn) / 32.f;
+    f[i++] = crun / 32.f;
+    f[i++] = lg(S.flops) / 64.f;
+    f[i++] = lg(S.bytes) / 64.f;
+    f[i++] = precision == TN_TF32 ? 1.f : 0.f;
+    f[i++] = precision == TN_BF16X3 ? 1.f : 0.f;
+    f[i++] = gemm ? 0.f : 1.f;
+    f[i++] = tc ? 1.f : 0.f;
+    f[i++] = gemm && !tc ? 1.f : 0.f;
+    f[i++] = float(c & 1);
+    f[i++] = lg(double(nd.n_inst) * std::ldexp(1.0, S.mb)) / 64.f;
 }
 
 // Batches [b_lo, b_hi) in order.  The first batch of the call runs every
@@ -508,16 +566,185 @@ int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream
 
 int tn_plan_set_kernel(tn_plan_t plan, int32_t step, int32_t kernel) {
     if (!plan) return set_err(TN_EINVAL, "tn_plan_set_kernel: null plan");
+    if (kernel < -1 || kernel > 1) return set_err(TN_EINVAL, "tn_plan_set_kernel: bad kernel family");
+    return tn_plan_set_config(plan, step, kernel < 0 ? -1 : 2 * kernel);
+}
+
+int tn_plan_set_config(tn_plan_t plan, int32_t step, int32_t config) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_set_config: null plan");
     PlanObj *o = reinterpret_cast<PlanObj *>(plan);
     const tnp::Plan &P = o->P;
-    if (step < 0 || step >= (int32_t)P.steps.size()) return set_err(TN_EINVAL, "tn_plan_set_kernel: bad step");
-    if (kernel < -1 || kernel > 1) return set_err(TN_EINVAL, "tn_plan_set_kernel: bad kernel family");
-    const tnp::Step &st = P.steps[step];
-    if (kernel == 0 && !(st.nb <= 4 && st.kb + st.nb <= 8))
-        return set_err(TN_EINVAL, "tn_plan_set_kernel: per-row kernel needs N <= 16 and K*N <= 256");
-    o->kernel_override.resize(P.steps.size(), -1);
-    o->kernel_override[step] = kernel;
+    if (step < 0 || step >= (int32_t)P.steps.size()) return set_err(TN_EINVAL, "tn_plan_set_config: bad step");
+    if (config < -1 || config >= TN_NCONFIG) return set_err(TN_EINVAL, "tn_plan_set_config: bad configuration");
+    if (config >= 0 && !config_allowed(P.steps[step], config))
+        return set_err(TN_EINVAL, "tn_plan_set_config: per-row kernel needs N <= 16 and K*N <= 256");
+    o->config_override.resize(P.steps.size(), -1);
+    o->config_override[step] = config;
     o->drop_graphs();
+    return TN_OK;
+}
+
+int tn_plan_get_configs(tn_plan_t plan, int32_t *config, int32_t n) {
+    if (!plan || (n > 0 && !config)) return set_err(TN_EINVAL, "tn_plan_get_configs: null argument");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    for (int32_t s = 0; s < n && s < (int32_t)o->P.steps.size(); ++s) config[s] = effective_config(o, s);
+    return TN_OK;
+}
+
+int tn_plan_features(tn_plan_t plan, int precision, int32_t config, float *feat, int32_t *eligible, int32_t n) {
+    if (!plan || (n > 0 && !feat)) return set_err(TN_EINVAL, "tn_plan_features: null argument");
+    if (precision < TN_FP32 || precision > TN_BF16X3) return set_err(TN_EINVAL, "tn_plan_features: bad precision");
+    if (config < 0 || config >= TN_NCONFIG) return set_err(TN_EINVAL, "tn_plan_features: bad configuration");
+    const tnp::Plan &P = reinterpret_cast<PlanObj *>(plan)->P;
+    for (int32_t s = 0; s < n && s < (int32_t)P.steps.size(); ++s) {
+        step_features(P, s, precision, config, feat + int64_t(s) * TN_NFEAT);
+        if (eligible) eligible[s] = config_allowed(P.steps[s], config) ? 1 : 0;
+    }
+    return TN_OK;
+}
+
+int tn_plan_autotune(tn_plan_t plan, int precision, int32_t reps, const uint8_t *step_mask, double *amps_scratch,
+                     double *times, void *stream) {
+    if (!plan || !amps_scratch) return set_err(TN_EINVAL, "tn_plan_autotune: null argument");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    if (!o->ws) return set_err(TN_ESTATE, "tn_plan_autotune: no workspace bound");
+    if (precision < TN_FP32 || precision > TN_BF16X3) return set_err(TN_EINVAL, "tn_plan_autotune: bad precision");
+    if (reps < 1) return set_err(TN_EINVAL, "tn_plan_autotune: reps must be >= 1");
+    const tnp::Plan &P = o->P;
+    const int ns = (int)P.steps.size();
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<int32_t> cur(ns);
+    for (int s = 0; s < ns; ++s) cur[s] = effective_config(o, s);
+    std::vector<double> best(size_t(ns) * TN_NCONFIG, NAN), ms(ns);
+    const bool prof = o->profile;
+    o->profile = true;  // CUDA events around every step launch
+    o->config_override.assign(ns, -1);
+    int rc = TN_OK;
+    for (int c = 0; c < TN_NCONFIG && rc == TN_OK; ++c) {
+        bool any = false;
+        for (int s = 0; s < ns; ++s) {
+            const bool sel = (!step_mask || step_mask[s]) && config_allowed(P.steps[s], c);
+            o->config_override[s] = sel ? c : cur[s];
+            any = any || sel;
+        }
+        if (!any) continue;
+        for (int r = 0; r <= reps && rc == TN_OK; ++r) {
+            rc = tn_contract(plan, precision, 0, P.n_batches, amps_scratch, stream);
+            if (rc == TN_OK) rc = tn_plan_step_times(plan, ms.data(), nullptr, ns);
+            if (rc != TN_OK || r == 0) continue;  // the first run warms up
+            for (int s = 0; s < ns; ++s) {
+                if (o->config_override[s] != c || (step_mask && !step_mask[s]) || P.steps[s].runs <= 0) continue;
+                const double t = ms[s] / P.steps[s].runs;
+                double &b = best[size_t(s) * TN_NCONFIG + c];
+                if (std::isnan(b) || t < b) b = t;
+            }
+        }
+    }
+    if (rc == TN_OK) rc = tn_plan_check(plan, stream);
+    o->profile = prof;
+    const std::string msg = g_err;
+    for (int s = 0; s < ns; ++s) {
+        int pick = cur[s];
+        if (rc == TN_OK && (!step_mask || step_mask[s])) {
+            double bt = NAN;
+            for (int c = 0; c < TN_NCONFIG; ++c) {
+                const double t = best[size_t(s) * TN_NCONFIG + c];
+                if (!std::isnan(t) && (std::isnan(bt) || t < bt)) {
+                    bt = t;
+                    pick = c;
+                }
+            }
+        }
+        o->config_override[s] = pick;
+    }
+    o->drop_graphs();
+    if (times) std::copy(best.begin(), best.end(), times);
+    g_err = rc == TN_OK ? std::string() : msg;
+    return rc;
+}
+
+int tn_plan_select(tn_plan_t plan, int precision, const uint16_t *params16, float margin, void *scratch,
+                   size_t scratch_bytes, int32_t *uncertain, void *stream) {
+    if (!plan || !params16 || !scratch) return set_err(TN_EINVAL, "tn_plan_select: null argument");
+    if (precision < TN_FP32 || precision > TN_BF16X3) return set_err(TN_EINVAL, "tn_plan_select: bad precision");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    const tnp::Plan &P = o->P;
+    const int ns = (int)P.steps.size();
+    const int64_t rows = int64_t(ns) * TN_NCONFIG;
+    const size_t need = size_t(rows) * (TN_NFEAT + 1) * sizeof(float);
+    if (scratch_bytes < need)
+        return set_err(TN_ENOMEM, "tn_plan_select: scratch needs " + std::to_string(need) + " bytes");
+    std::vector<float> X(size_t(rows) * TN_NFEAT), y(rows);
+    for (int s = 0; s < ns; ++s)
+        for (int c = 0; c < TN_NCONFIG; ++c) step_features(P, s, precision, c, &X[(size_t(s) * TN_NCONFIG + c) * TN_NFEAT]);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    float *dX = static_cast<float *>(scratch), *dy = dX + rows * TN_NFEAT;
+    CU(cudaMemcpyAsync(dX, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    CU(tnk::mlp_forward_f16(params16, dX, rows, dy, st));
+    CU(cudaMemcpyAsync(y.data(), dy, y.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    o->config_override.resize(ns, -1);
+    for (int s = 0; s < ns; ++s) {
+        int b1 = -1;
+        float y1 = 0.f, y2 = 0.f;
+        bool have2 = false;
+        for (int c = 0; c < TN_NCONFIG; ++c) {
+            if (!config_allowed(P.steps[s], c)) continue;
+            const float v = y[size_t(s) * TN_NCONFIG + c];
+            if (b1 < 0 || v < y1) {
+                if (b1 >= 0) {
+                    y2 = y1;
+                    have2 = true;
+                }
+                y1 = v;
+                b1 = c;
+            } else if (!have2 || v < y2) {
+                y2 = v;
+                have2 = true;
+            }
+        }
+        o->config_override[s] = b1;
+        if (uncertain) uncertain[s] = (have2 && y2 - y1 < margin) ? 1 : 0;
+    }
+    o->drop_graphs();
+    g_err.clear();
+    return TN_OK;
+}
+
+size_t tn_mlp_grad_scratch_bytes(int64_t n) { return tnk::mlp_grad_scratch_bytes(n); }
+
+int tn_mlp_forward(const float *params, const float *X, int64_t n, float *y, void *stream) {
+    if (!params || n < 0 || (n > 0 && (!X || !y))) return set_err(TN_EINVAL, "tn_mlp_forward: bad arguments");
+    CU(tnk::mlp_forward(params, X, n, y, reinterpret_cast<cudaStream_t>(stream)));
+    return TN_OK;
+}
+
+int tn_mlp_grad(const float *params, const float *X, const float *t, int64_t n, float *grad, float *loss,
+                void *scratch, size_t scratch_bytes, void *stream) {
+    if (!params || !X || !t || !grad || !scratch || n <= 0) return set_err(TN_EINVAL, "tn_mlp_grad: bad arguments");
+    if (scratch_bytes < tnk::mlp_grad_scratch_bytes(n))
+        return set_err(TN_ENOMEM, "tn_mlp_grad: scratch needs " + std::to_string(tnk::mlp_grad_scratch_bytes(n)) +
+                                      " bytes");
+    CU(tnk::mlp_grad(params, X, t, n, grad, loss, static_cast<float *>(scratch), reinterpret_cast<cudaStream_t>(stream)));
+    return TN_OK;
+}
+
+int tn_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr, float beta1,
+                float beta2, float eps, void *stream) {
+    if (!params || !grad || !m || !v || step < 1) return set_err(TN_EINVAL, "tn_mlp_adam: bad arguments");
+    CU(tnk::mlp_adam(params, grad, m, v, step, lr, beta1, beta2, eps, reinterpret_cast<cudaStream_t>(stream)));
+    return TN_OK;
+}
+
+int tn_mlp_to_half(const float *params, uint16_t *params16, void *stream) {
+    if (!params || !params16) return set_err(TN_EINVAL, "tn_mlp_to_half: null argument");
+    CU(tnk::mlp_to_half(params, params16, reinterpret_cast<cudaStream_t>(stream)));
+    return TN_OK;
+}
+
+int tn_mlp_forward_f16(const uint16_t *params16, const float *X, int64_t n, float *y, void *stream) {
+    if (!params16 || n < 0 || (n > 0 && (!X || !y))) return set_err(TN_EINVAL, "tn_mlp_forward_f16: bad arguments");
+    CU(tnk::mlp_forward_f16(params16, X, n, y, reinterpret_cast<cudaStream_t>(stream)));
     return TN_OK;
 }
 

@@ -289,14 +289,19 @@ constexpr size_t smem_bytes() {
 }
 static_assert(smem_bytes<1>() <= 232448 && smem_bytes<2>() <= 232448, "shared memory above 227 KB");
 
-// Tile T of a step.  The tiles of one group (its column tiles x row tiles)
-// are numbered row tile major, column tile minor, so the column tiles that
-// share an A row tile run on neighbouring CTAs and A is read from DRAM
-// about once.  Returns the column-tile record with its first column, and
+// Tile T of a step.  Schedule 0: the tiles of one group (its column tiles
+// x row tiles) are numbered row tile major, column tile minor, so the
+// column tiles that share an A row tile run on neighbouring CTAs and A is
+// read from DRAM about once.  Schedule 1: column tile major, row tile minor
+// (the B columns of a column tile stay in L2 across its row tiles).  Returns the column-tile record with its first column, and
 // the row tile in mt.
 __device__ __forceinline__ int4 tile_decode(const StepDesc &d, int64_t T, int64_t mtiles, int64_t &mt) {
     const int64_t e0 = T / mtiles;  // some column tile of T's group
     int4 r = __ldg(d.trec + e0);
+    if (d.sched != 0) {  // schedule 1: the row tiles of one column tile run consecutively
+        mt = T - e0 * mtiles;
+        return r;
+    }
     const int64_t nct = ((int64_t(r.y) << d.nb) + TBN - 1) / TBN;
     const int64_t f = e0 - r.w / TBN;  // the group's first column tile
     const int64_t local = T - f * mtiles;

@@ -310,10 +310,22 @@ __global__ void __launch_bounds__(256) k_step_gemm_simt(const StepDesc d, int ct
     __shared__ int s_ea;
     const int tid = threadIdx.x;
     const int64_t bid = blockIdx.x;
-    const int mt = int(bid % mtiles);
-    const int64_t rest = bid / mtiles;
-    const int ct = int(rest % ctiles);
-    const int64_t g = rest / ctiles;
+    // schedule 0: row tiles of a column tile on consecutive blocks (the
+    // group's B columns stay in L2); 1: column tiles of a row tile on
+    // consecutive blocks (the A rows stay in L2)
+    int mt, ct;
+    int64_t g;
+    if (d.sched == 0) {
+        mt = int(bid % mtiles);
+        const int64_t rest = bid / mtiles;
+        ct = int(rest % ctiles);
+        g = rest / ctiles;
+    } else {
+        ct = int(bid % ctiles);
+        const int64_t rest = bid / ctiles;
+        mt = int(rest % mtiles);
+        g = rest / mtiles;
+    }
     const int64_t i0 = d.gfirst[g];
     const int64_t icount = d.gfirst[g + 1] - i0;
     const int N = 1 << d.nb;
@@ -489,9 +501,10 @@ cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
     const int64_t M = int64_t(1) << d.mb;
     int64_t blocks, mblocks = 1;
     int rows_per_block;
-    if (M >= 8 * R) {  // blocks inside one group: up to 16 passes of 8 warps x R rows
+    if (M >= 8 * R) {  // blocks inside one group: up to 16 (schedule 1: 4) passes of 8 warps x R rows
         int64_t passes = M / (8 * R);
-        passes = passes > 16 ? 16 : passes;
+        const int64_t cap = d.sched == 0 ? 16 : 4;
+        passes = passes > cap ? cap : passes;
         rows_per_block = int(8 * R * passes);
         mblocks = M / rows_per_block;
         blocks = d.n_groups * mblocks;

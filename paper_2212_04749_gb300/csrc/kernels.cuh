@@ -25,7 +25,7 @@ struct StepDesc {
     const int32_t *sigA, *sigB;   // [n_sig]
     const int32_t *outA, *outB;   // [nOut]
     int32_t nOutA, nOutB, nOut;
-    int32_t pad0;
+    int32_t sched;                // schedule variant of the step's kernel (0 or 1; the autotuner's choice)
     int64_t nInst;
     const int32_t *EA, *EB;       // accumulated exponents of the operands
     int32_t *EC;
@@ -78,5 +78,15 @@ cudaError_t init_kernels();
 cudaError_t make_a_map(const StepDesc &d, int64_t n_inst_a, CUtensorMap *map);
 cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int precision, int32_t *err_flag,
                                 cudaStream_t s);
+
+// Cost-model MLP (mlp.cu); sizes and parameter layout in include/tn.h.
+size_t mlp_grad_scratch_bytes(int64_t n);
+cudaError_t mlp_forward(const float *params, const float *X, int64_t n, float *y, cudaStream_t s);
+cudaError_t mlp_grad(const float *params, const float *X, const float *t, int64_t n, float *grad, float *loss,
+                     float *scratch, cudaStream_t s);
+cudaError_t mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr, float beta1,
+                     float beta2, float eps, cudaStream_t s);
+cudaError_t mlp_to_half(const float *params, uint16_t *params16, cudaStream_t s);
+cudaError_t mlp_forward_f16(const uint16_t *params16, const float *X, int64_t n, float *y, cudaStream_t s);
 
 }  // namespace tnk

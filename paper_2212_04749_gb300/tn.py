@@ -21,9 +21,15 @@ PRECISIONS = {"fp32": TN_FP32, "tf32": TN_TF32, "bf16x3": TN_BF16X3}
 
 EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_plan_widths", "tn_plan_steps",
            "tn_plan_bind", "tn_contract", "tn_contract_slices", "tn_xeb", "tn_plan_profile",
-           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_check", "tn_contract_static", "tn_destroy",
-           "tn_last_error")
+           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_get_configs",
+           "tn_plan_features", "tn_plan_autotune", "tn_plan_select", "tn_mlp_grad_scratch_bytes",
+           "tn_mlp_forward", "tn_mlp_grad", "tn_mlp_adam", "tn_mlp_to_half", "tn_mlp_forward_f16",
+           "tn_plan_check", "tn_contract_static", "tn_destroy", "tn_last_error")
 TN_STATIC_SCRATCH_BYTES = 64 << 20
+TN_NCONFIG = 4
+TN_NFEAT = TN_MLP_IN = 24
+TN_MLP_HIDDEN = 128
+TN_MLP_NPARAMS = TN_MLP_HIDDEN * TN_MLP_IN + TN_MLP_HIDDEN + TN_MLP_HIDDEN * TN_MLP_HIDDEN + 2 * TN_MLP_HIDDEN + 1
 
 
 class TnError(RuntimeError):
@@ -103,6 +109,18 @@ def load(build_if_missing: bool = False):
         "tn_xeb": (ctypes.c_int, [vp, i64, i32, vp, vp]),
         "tn_plan_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "tn_plan_set_kernel": (ctypes.c_int, [vp, i32, i32]),
+        "tn_plan_set_config": (ctypes.c_int, [vp, i32, i32]),
+        "tn_plan_get_configs": (ctypes.c_int, [vp, vp, i32]),
+        "tn_plan_features": (ctypes.c_int, [vp, ctypes.c_int, i32, vp, vp, i32]),
+        "tn_plan_autotune": (ctypes.c_int, [vp, ctypes.c_int, i32, vp, vp, vp, vp]),
+        "tn_plan_select": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_float, vp, ctypes.c_size_t, vp, vp]),
+        "tn_mlp_grad_scratch_bytes": (ctypes.c_size_t, [i64]),
+        "tn_mlp_forward": (ctypes.c_int, [vp, vp, i64, vp, vp]),
+        "tn_mlp_grad": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp, ctypes.c_size_t, vp]),
+        "tn_mlp_adam": (ctypes.c_int, [vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, vp]),
+        "tn_mlp_to_half": (ctypes.c_int, [vp, vp, vp]),
+        "tn_mlp_forward_f16": (ctypes.c_int, [vp, vp, i64, vp, vp]),
         "tn_plan_check": (ctypes.c_int, [vp, vp]),
         "tn_contract_static": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "tn_plan_step_times": (ctypes.c_int, [vp, vp, vp, i32]),
@@ -261,6 +279,48 @@ class Plan:
     def tn_plan_set_kernel(self, step, kernel):
         _check(self._lib.tn_plan_set_kernel(self.h, int(step), int(kernel)))
 
+    def tn_plan_set_config(self, step, config):
+        _check(self._lib.tn_plan_set_config(self.h, int(step), int(config)))
+
+    def tn_plan_get_configs(self):
+        n = self.info["n_steps"]
+        c = np.zeros(max(n, 1), np.int32)
+        _check(self._lib.tn_plan_get_configs(self.h, c.ctypes.data, n))
+        return c[:n]
+
+    def tn_plan_features(self, precision, config):
+        """(features n_steps x TN_NFEAT float32, eligible n_steps bool) for one configuration."""
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        n = self.info["n_steps"]
+        f = np.zeros((max(n, 1), TN_NFEAT), np.float32)
+        e = np.zeros(max(n, 1), np.int32)
+        _check(self._lib.tn_plan_features(self.h, int(precision), int(config), f.ctypes.data, e.ctypes.data, n))
+        return f[:n], e[:n].astype(bool)
+
+    def tn_plan_autotune(self, precision, amps_scratch, reps=2, step_mask=None, stream=None):
+        """Exhaustive autotuner: returns ms per pass, n_steps x TN_NCONFIG (NaN: not measured)."""
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        n = self.info["n_steps"]
+        t = np.full((max(n, 1), TN_NCONFIG), np.nan)
+        mask = None if step_mask is None else np.ascontiguousarray(np.asarray(step_mask, np.uint8))
+        _check(self._lib.tn_plan_autotune(self.h, int(precision), int(reps),
+                                          None if mask is None else mask.ctypes.data, _ptr(amps_scratch),
+                                          t.ctypes.data, _stream(stream)))
+        return t[:n]
+
+    def tn_plan_select(self, precision, params16, scratch, margin=0.0, stream=None):
+        """Cost-model selection; returns the per-step 'uncertain' flags (bool)."""
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        n = self.info["n_steps"]
+        u = np.zeros(max(n, 1), np.int32)
+        nbytes = scratch.numel() * scratch.element_size()
+        _check(self._lib.tn_plan_select(self.h, int(precision), _ptr(params16), float(margin), _ptr(scratch),
+                                        int(nbytes), u.ctypes.data, _stream(stream)))
+        return u[:n].astype(bool)
+
     def tn_plan_check(self, stream=None):
         _check(self._lib.tn_plan_check(self.h, _stream(stream)))
 
@@ -278,3 +338,30 @@ class Plan:
 
 def tn_xeb(amps, k, n_qubits, out, stream=None):
     _check(load().tn_xeb(_ptr(amps), int(k), int(n_qubits), _ptr(out), _stream(stream)))
+
+
+def tn_mlp_grad_scratch_bytes(n):
+    return int(load().tn_mlp_grad_scratch_bytes(int(n)))
+
+
+def tn_mlp_forward(params, X, n, y, stream=None):
+    _check(load().tn_mlp_forward(_ptr(params), _ptr(X), int(n), _ptr(y), _stream(stream)))
+
+
+def tn_mlp_grad(params, X, t, n, grad, loss, scratch, stream=None):
+    nbytes = scratch.numel() * scratch.element_size()
+    _check(load().tn_mlp_grad(_ptr(params), _ptr(X), _ptr(t), int(n), _ptr(grad), _ptr(loss), _ptr(scratch),
+                              int(nbytes), _stream(stream)))
+
+
+def tn_mlp_adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().tn_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), float(beta1),
+                              float(beta2), float(eps), _stream(stream)))
+
+
+def tn_mlp_to_half(params, params16, stream=None):
+    _check(load().tn_mlp_to_half(_ptr(params), _ptr(params16), _stream(stream)))
+
+
+def tn_mlp_forward_f16(params16, X, n, y, stream=None):
+    _check(load().tn_mlp_forward_f16(_ptr(params16), _ptr(X), int(n), _ptr(y), _stream(stream)))

@@ -27,7 +27,7 @@ def tn():
 
 def test_library_exports_every_declared_entry_point(tn, root):
     hdr = open(os.path.join(root, "include", "tn.h")).read()
-    declared = set(re.findall(r"^\s*(?:int|void|const char \*)\s*(tn_\w+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^\s*(?:int|void|size_t|const char \*)\s*(tn_\w+)\s*\(", hdr, re.M))
     assert declared, "no declarations parsed"
     lib = tn.load()
     for name in sorted(declared):
@@ -180,3 +180,53 @@ def test_contract_before_bind_is_a_state_error(tn):
     with pytest.raises(tn.TnError) as ei:
         p.tn_contract(12345, "fp32")
     assert ei.value.code == tn.TN_ESTATE
+
+
+def _row_allowed(st):
+    return st["nb"] <= 4 and st["kb"] + st["nb"] <= 8
+
+
+@pytest.mark.parametrize("name", ["grid3x4_m8", "grid5x6_m14"])
+def test_features_and_config_eligibility(tn, name):
+    # one row of TN_NFEAT features per step; the per-row configurations are
+    # allowed exactly where the per-row kernel's shape condition holds, the
+    # GEMM ones everywhere; the one-hot blocks are one-hot
+    w = make_workload(name)
+    p = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced)
+    steps = p.tn_plan_steps()
+    for prec in ("fp32", "tf32", "bf16x3"):
+        for c in range(tn.TN_NCONFIG):
+            f, ok = p.tn_plan_features(prec, c)
+            assert f.shape == (len(steps), tn.TN_NFEAT)
+            assert np.all(np.isfinite(f)) and np.all(np.abs(f) <= 2.0)
+            want = np.array([c >= 2 or _row_allowed(st) for st in steps])
+            assert np.array_equal(ok, want)
+            assert np.all(f[:, 19] + f[:, 20] + f[:, 21] == 1.0)  # exactly one kernel family
+            assert np.all(f[:, 22] == (c & 1))
+            assert np.all(f[:, 17] == (prec == "tf32")) and np.all(f[:, 18] == (prec == "bf16x3"))
+            if prec == "fp32":
+                assert not np.any(f[:, 20])  # no tensor cores in FP32
+            np.testing.assert_allclose(f[:, 0] * 32, [st["mb"] for st in steps])
+            np.testing.assert_allclose(f[:, 1] * 32, [st["kb"] for st in steps])
+            np.testing.assert_allclose(f[:, 2] * 32, [st["nb"] for st in steps])
+
+
+def test_config_override_rules(tn):
+    w = make_workload("grid5x6_m14")
+    p = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced)
+    steps = p.tn_plan_steps()
+    base = p.tn_plan_get_configs()
+    assert np.array_equal(base, [0 if st["kernel"] == 0 else 2 for st in steps])
+    big = next(i for i, st in enumerate(steps) if not _row_allowed(st))
+    with pytest.raises(tn.TnError) as ei:
+        p.tn_plan_set_config(big, 1)
+    assert ei.value.code == tn.TN_EINVAL
+    for bad in (-2, tn.TN_NCONFIG):
+        with pytest.raises(tn.TnError):
+            p.tn_plan_set_config(0, bad)
+    p.tn_plan_set_config(big, 3)
+    p.tn_plan_set_kernel(0, 1)
+    got = p.tn_plan_get_configs()
+    assert got[big] == 3 and got[0] == 2
+    p.tn_plan_set_config(big, -1)
+    assert p.tn_plan_get_configs()[big] == base[big]

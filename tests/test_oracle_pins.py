@@ -11,7 +11,7 @@ on the wrong side of a gate) fails a pin.
 import numpy as np
 import pytest
 
-from oracle import brute, sv, tn, xeb
+from oracle import brute, mlp, sv, tn, xeb
 from rqc import grid_layout, make_workload, network_structure, random_circuit
 from rqc.bitstrings import bitstrings_from_indices, uniform_bitstrings
 from rqc.circuit import Circuit, Gate, inverse_circuit, product_circuit
@@ -220,3 +220,71 @@ def test_planted_wrong_slice_wire_fails_projector_pin():
     amps = sv.amplitudes(w.circuit, w.bits)
     assert np.max(np.abs(parts_bad.sum(axis=0) - amps)) < 1e-13
     assert net.n_groups == 34
+
+
+# cost-model network (oracle/mlp.py) ------------------------------------------
+def _mlp_case(d=5, h=7, n=11, seed=3):
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0, 0.7, mlp.n_params(d, h))
+    X = rng.normal(0, 1, (n, d))
+    t = rng.normal(0, 1, n)
+    return p, X, t
+
+
+def test_mlp_gradient_matches_central_differences():
+    d, h = 5, 7
+    p, X, t = _mlp_case(d, h)
+    g, L = mlp.grad(p, X, t, d, h)
+    assert abs(L - mlp.loss(p, X, t, d, h)) < 1e-14
+    eps = 1e-6
+    fd = np.empty_like(p)
+    for i in range(p.size):
+        e = np.zeros_like(p)
+        e[i] = eps
+        fd[i] = (mlp.loss(p + e, X, t, d, h) - mlp.loss(p - e, X, t, d, h)) / (2 * eps)
+    assert np.max(np.abs(fd - g)) <= 1e-7 * max(1.0, np.max(np.abs(g)))
+
+
+def test_mlp_forward_hand_evaluated():
+    # D = 2, H = 2, evaluated by hand (x -> z1 -> a1 -> z2 -> a2 -> y):
+    #   x = (3, 1):  z1 = (2, 2.5), z2 = (5, 3),   y = 2*5 - 3 + 0.25 = 7.25
+    #   x = (0, 1):  z1 = (-1, 1), a1 = (0, 1), z2 = (1.5, 2), y = 3 - 2 + 0.25 = 1.25
+    #   x = (-2, 0): z1 = (-2, -2), a1 = 0, z2 = (0.5, 0), y = 1 + 0.25 = 1.25
+    p = mlp.pack([[1, -1], [0.5, 2]], [0, -1], [[1, 1], [-1, 2]], [0.5, 0], [2, -1], 0.25)
+    y = mlp.forward(p, [[3, 1], [0, 1], [-2, 0]], 2, 2)
+    np.testing.assert_allclose(y, [7.25, 1.25, 1.25], rtol=0, atol=1e-15)
+
+
+def test_mlp_first_adam_step_moves_by_lr_times_sign():
+    # after one step the bias-corrected ratio m_hat / sqrt(v_hat) is g / |g|
+    d, h = 5, 7
+    p, X, t = _mlp_case(d, h)
+    g, _ = mlp.grad(p, X, t, d, h)
+    lr = 1e-3
+    p1, m, v = mlp.adam_step(p, g, np.zeros_like(p), np.zeros_like(p), 1, lr)
+    big = np.abs(g) > 1e-4
+    np.testing.assert_allclose((p - p1)[big], lr * np.sign(g[big]), rtol=1e-4)
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_planted_missing_relu_mask_fails_finite_differences():
+    # the backward pass with relu'(z2) dropped is a plausible slip: the
+    # finite-difference pin must catch it
+    d, h = 5, 7
+    p, X, t = _mlp_case(d, h)
+    W1, b1, W2, b2, w3, b3 = mlp.unpack(p, d, h)
+    y, (Xk, z1, a1, z2, a2) = mlp.forward(p, X, d, h, keep=True)
+    dy = 2.0 * (y - t) / X.shape[0]
+    dz2_wrong = np.outer(dy, w3)  # mask missing
+    g_wrong_W2 = dz2_wrong.T @ a1
+    assert np.any(z2 <= 0)
+    off = h * d + h  # W2 block of the flat parameter vector
+    eps = 1e-6
+    fd = np.empty(h * h)
+    for i in range(h * h):
+        e = np.zeros_like(p)
+        e[off + i] = eps
+        fd[i] = (mlp.loss(p + e, X, t, d, h) - mlp.loss(p - e, X, t, d, h)) / (2 * eps)
+    # the pin's tolerance (as in the finite-difference test) rejects it
+    assert np.max(np.abs(fd - g_wrong_W2.ravel())) > 1e-7 * max(1.0, np.max(np.abs(fd))) * 100
