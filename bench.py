@@ -219,6 +219,25 @@ def run_ours(args, world, rank, local):
     amps = torch.zeros(2 * k, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
 
+    def select(prec):
+        """Configure every step for `prec`; returns the selection record."""
+        for s_ in range(info["n_steps"]):
+            plan.tn_plan_set_config(s_, -1)
+        if args.select == "rule":
+            return {"mode": "rule"}
+        rule_ms = statistics.median(one_step(prec) for _ in range(2))
+        t0 = time.perf_counter()
+        if args.select == "autotune":
+            plan.tn_plan_autotune(prec, amps, reps=2, stream=stream)
+        else:
+            from paper_2212_04749_gb300 import costmodel
+            tr = costmodel.Trainer.load(args.model)
+            costmodel.select(costmodel.Bound(None, plan, ws, amps, stream), prec, tr)
+        sel_s = time.perf_counter() - t0
+        cfg = plan.tn_plan_get_configs()
+        return {"mode": args.select, "rule_ms": rule_ms, "selection_s": sel_s,
+                "configs": np.bincount(cfg, minlength=tn.TN_NCONFIG).tolist()}
+
     def one_step(prec, profile=False):
         amps.zero_()
         flush.fill_(1)
@@ -231,19 +250,16 @@ def run_ours(args, world, rank, local):
         e1.synchronize()
         return e0.elapsed_time(e1)
 
+    selection = select(args.precision)
     for _ in range(args.warmup):
         one_step(args.precision)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     times = []
-    step_ms = np.zeros(info["n_steps"])
-    kernels = None
     with Clocks(torch.cuda.current_device()) as clk:
         for _ in range(args.steps):
-            times.append(one_step(args.precision, profile=True))
-            ms, kernels = plan.tn_plan_step_times()
-            step_ms += ms
+            times.append(one_step(args.precision))
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -255,6 +271,15 @@ def run_ours(args, world, rank, local):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = tt.item()
     value = k * world / (t_max / 1000.0)
+    # per-step device times: separate runs with CUDA events around every
+    # launch (no graph replay), averaged
+    prof_runs = 2
+    step_ms = np.zeros(info["n_steps"])
+    kernels = None
+    for _ in range(prof_runs):
+        one_step(args.precision, profile=True)
+        ms, kernels = plan.tn_plan_step_times()
+        step_ms += ms / prof_runs
     plan.tn_plan_profile(False)
 
     # accuracy of this run against the stored oracle values
@@ -262,18 +287,22 @@ def run_ours(args, world, rank, local):
     ref = _golden(args.workload) if rank == 0 else None
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref)) if ref is not None and len(ref) == k else None
 
-    # mixed-precision forms on the same workload
-    mixed = {}
+    selection["tuned_ms"] = t_max
+
+    # the other forms on the same workload (each with its own configuration)
+    others = {}
     if args.mixed and rank == 0:
-        for prec in ("bf16x3", "tf32"):
+        for prec in ("fp32", "bf16x3", "tf32"):
             if prec == args.precision:
                 continue
+            sel2 = select(prec)
             one_step(prec)
             ts = [one_step(prec) for _ in range(max(2, args.steps // 2))]
             g2 = amps.cpu().numpy().view(np.complex128)
             e2 = float(np.linalg.norm(g2 - ref) / np.linalg.norm(ref)) if ref is not None else None
-            mixed[prec] = {"amplitudes_per_s": k / (statistics.mean(ts) / 1000.0), "ms_per_step": statistics.mean(ts),
-                           "rel_l2_vs_oracle": e2}
+            others[prec] = {"amplitudes_per_s": k / (statistics.mean(ts) / 1000.0), "ms_per_step": statistics.mean(ts),
+                            "rel_l2_vs_oracle": e2, "selection": sel2}
+        select(args.precision)  # back to the headline form's configuration
 
     # roofline of the dominant kernel family
     peaks, peak_src = _peaks()
@@ -282,7 +311,7 @@ def run_ours(args, world, rank, local):
     fam_ms, fam_bytes, fam_flops, fam_launch = {}, {}, {}, {}
     for s, st in enumerate(steps):
         f = int(kernels[s]) if kernels is not None else 0
-        fam_ms[f] = fam_ms.get(f, 0.0) + step_ms[s] / args.steps
+        fam_ms[f] = fam_ms.get(f, 0.0) + step_ms[s]
         fam_bytes[f] = fam_bytes.get(f, 0.0) + st["bytes"] * st["runs"]
         fam_flops[f] = fam_flops.get(f, 0.0) + st["flops"] * st["runs"]
         fam_launch[f] = fam_launch.get(f, 0) + int(st["runs"])
@@ -290,7 +319,7 @@ def run_ours(args, world, rank, local):
         rows = []
         for s_, st in enumerate(steps):
             r = dict(st)
-            r["ms_per_call"] = float(step_ms[s_] / args.steps)
+            r["ms_per_call"] = float(step_ms[s_])
             r["family"] = int(kernels[s_]) if kernels is not None else -1
             rows.append(r)
         with open(args.dump_steps, "w") as f:
@@ -321,12 +350,15 @@ def run_ours(args, world, rank, local):
     e2e = None
     if args.e2e_steps > 0:
         pinned_out = torch.empty(2 * k, dtype=torch.float64, pin_memory=True)
+        cfg_now = plan.tn_plan_get_configs()
         ws2 = ws
         tw = []
         for _ in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             p2 = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit)
+            for s_, c_ in enumerate(cfg_now):
+                p2.tn_plan_set_config(s_, int(c_))
             p2.tn_plan_bind(ws2, stream=stream)
             amps.zero_()
             p2.tn_contract(amps, args.precision, stream=stream)
@@ -358,7 +390,8 @@ def run_ours(args, world, rank, local):
                    "workspace_gib": info["workspace_bytes"] / 2 ** 30},
         "tflops_algorithmic": tflops,
         "rel_l2_vs_oracle": err,
-        "mixed": mixed or None,
+        "other_forms": others or None,
+        "config_selection": selection,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -379,7 +412,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="grid5x6_m14")
-    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16x3"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16x3"], default="bf16x3",
+                    help="headline form (default: the mixed BF16x3 split form); the others run beside it")
+    ap.add_argument("--select", choices=["autotune", "model", "rule"], default="autotune",
+                    help="per-step kernel configuration: exhaustive autotuner, cost model (--model), or the plan's rule")
+    ap.add_argument("--model", default=None, help="cost-model parameters (npy) for --select model")
     ap.add_argument("--ws-gib", type=float, default=64.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")

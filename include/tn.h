@@ -228,11 +228,11 @@ int tn_plan_get_configs(tn_plan_t plan, int32_t *config, int32_t n);
 #define TN_NFEAT 24
 int tn_plan_features(tn_plan_t plan, int precision, int32_t config, float *feat, int32_t *eligible, int32_t n);
 
-/* Exhaustive autotuner.  For every configuration c, run the whole
- * contraction (all slice batches, `reps` + 1 times, the first discarded)
- * with every selected step (step_mask[s] != 0, or all steps if step_mask is
- * NULL) that allows c set to c, the others unchanged, and time every step
- * with CUDA events.  times (host, n_steps x TN_NCONFIG, may be NULL)
+/* Exhaustive autotuner.  For every configuration c, run the first slice
+ * batch of the contraction (in which every step runs exactly once; `reps` +
+ * 1 times, the first discarded) with every selected step (step_mask[s] !=
+ * 0, or all steps if step_mask is NULL) that allows c set to c, the others
+ * unchanged, and time every step with CUDA events.  times (host, n_steps x TN_NCONFIG, may be NULL)
  * receives the fastest time per pass of each (step, configuration) in ms,
  * NaN where not measured.  Afterwards every selected step is set to its
  * fastest configuration.  amps_scratch: device complex128 buffer of k

@@ -90,6 +90,7 @@ class Bound:
 
 
 def bind(case: Case, ws_limit: int = 4 << 30) -> Optional[Bound]:
+    """Plan and bind a case (None if it needs more than ws_limit bytes)."""
     import torch
     try:
         p = tn.Plan(case.circuit, case.bits, case.ssa, case.sliced, workspace_limit=ws_limit)
@@ -209,6 +210,17 @@ class Trainer:
         torch.cuda.synchronize()
         return hist
 
+    def save(self, path):
+        np.save(path, self.params.cpu().numpy())
+
+    @classmethod
+    def load(cls, path):
+        import torch
+        tr = cls()
+        tr.params.copy_(torch.from_numpy(np.load(path).astype(np.float32)))
+        tr.step = 1
+        return tr
+
     def predict(self, X: np.ndarray, f16: bool = False) -> np.ndarray:
         import torch
         Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
@@ -288,17 +300,34 @@ def main():
     ap = argparse.ArgumentParser(description="collect autotuner timings, train the cost model, report regret")
     ap.add_argument("--cases", type=int, default=60, help="random plans for the corpus")
     ap.add_argument("--eval-cases", type=int, default=6, help="held-out random plans")
-    ap.add_argument("--workloads", default="grid3x4_m8,grid5x6_m14", help="named workloads added to the corpus")
+    ap.add_argument("--workloads", default="grid3x4_m8,grid5x6_m14,grid6x7_m10",
+                    help="named workloads added to the corpus")
+    ap.add_argument("--workload-ws-gib", type=float, default=96.0)
     ap.add_argument("--budget-s", type=float, default=600.0, help="corpus collection time bound")
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--corpus", default=None, help="save the corpus (npz) here")
     ap.add_argument("--out", default=None, help="write the JSON report here")
+    ap.add_argument("--save-model", default=None, help="save the trained parameters (npy) here")
+    ap.add_argument("--precisions", default="fp32,bf16x3,tf32")
     args = ap.parse_args()
     torch.cuda.init()
     log = lambda m: print(m, flush=True)  # noqa: E731
-    cases = [workload_case(w) for w in args.workloads.split(",") if w]
-    cases += [random_case(s) for s in range(args.cases)]
-    corpus = collect(cases, Corpus(), log=log, budget_s=args.budget_s)
+    precs = tuple(args.precisions.split(","))
+    corpus = Corpus()
+    # the named workloads (bound with room for their full workspace; the
+    # autotuner times one slice batch), then random plans
+    for wi, w in enumerate([x for x in args.workloads.split(",") if x]):
+        b = bind(workload_case(w), ws_limit=int(args.workload_ws_gib * 2 ** 30))
+        if b is None:
+            log(f"{w}: does not fit, skipped")
+            continue
+        for prec in precs:
+            X, y, _ = autotune_rows(b, prec)
+            corpus.add(X, y, -1 - wi)
+        log(f"{w}: {len(corpus.y)} rows")
+        del b
+    cases = [random_case(s) for s in range(args.cases)]
+    collect(cases, corpus, precisions=precs, log=log, budget_s=args.budget_s, flops_range=(1e8, 1e15))
     if args.corpus:
         corpus.save(args.corpus)
     # 80/20 split by case seed
@@ -307,14 +336,23 @@ def main():
     vm = np.array([g in val for g in corpus.group])
     tr = Trainer(seed=0)
     hist = tr.fit(corpus.X[~vm], corpus.y[~vm], epochs=args.epochs, log=log)
+    if args.save_model:
+        tr.save(args.save_model)
     pv = tr.predict(corpus.X[vm]) if vm.any() else np.zeros(0)
     val_mse = float(np.mean((pv - corpus.y[vm]) ** 2)) if vm.any() else None
     evals = []
-    for s in range(10000, 10000 + args.eval_cases):
+    n_eval = 0
+    for s in range(10000, 10400):
+        if n_eval >= args.eval_cases:
+            break
         b = bind(random_case(s))
         if b is None:
             continue
-        for prec in PRECS:
+        if not 1e10 <= b.plan.info["flops_exec"] <= 2e12:  # plans where the configuration matters
+            del b
+            continue
+        n_eval += 1
+        for prec in precs:
             evals.append(evaluate(b, prec, tr))
             log(json.dumps(evals[-1]))
         del b

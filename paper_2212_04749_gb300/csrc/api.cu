@@ -629,12 +629,13 @@ int tn_plan_autotune(tn_plan_t plan, int precision, int32_t reps, const uint8_t 
         }
         if (!any) continue;
         for (int r = 0; r <= reps && rc == TN_OK; ++r) {
-            rc = tn_contract(plan, precision, 0, P.n_batches, amps_scratch, stream);
+            // the first slice batch of a call runs every step exactly once
+            rc = tn_contract(plan, precision, 0, P.n_batches > 0 ? 1 : 0, amps_scratch, stream);
             if (rc == TN_OK) rc = tn_plan_step_times(plan, ms.data(), nullptr, ns);
             if (rc != TN_OK || r == 0) continue;  // the first run warms up
             for (int s = 0; s < ns; ++s) {
-                if (o->config_override[s] != c || (step_mask && !step_mask[s]) || P.steps[s].runs <= 0) continue;
-                const double t = ms[s] / P.steps[s].runs;
+                if (o->config_override[s] != c || (step_mask && !step_mask[s])) continue;
+                const double t = ms[s];
                 double &b = best[size_t(s) * TN_NCONFIG + c];
                 if (std::isnan(b) || t < b) b = t;
             }

@@ -846,7 +846,23 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
     int lo = 0, hi = std::min(n_sliced, 20);
     if (P.opt.slice_batch_log2 >= 0) lo = hi = std::min(P.opt.slice_batch_log2, n_sliced);
     int chosen = -1;
+    // Cheap bounds before building a candidate's tables: every instance
+    // costs ~48 bytes of host tables (instance maps, group and tile records),
+    // and one node's instances must fit the workspace by themselves.
+    // Batches that fail either are skipped without being built.
+    auto surely_too_big = [&](int ml) {
+        double inst = 0.0, largest = 0.0;
+        for (const Node &nd : P.nodes) {
+            int low = 0;
+            for (int t : nd.slices) low += t < ml;
+            const double ni = std::ldexp(double(nd.n_out), low);
+            inst += ni;
+            largest = std::max(largest, ni * std::ldexp(8.0, nd.rank));
+        }
+        return inst * 48.0 > double(int64_t(8) << 30) || largest > double(P.opt.workspace_limit);
+    };
     for (int ml = hi; ml >= lo; --ml) {
+        if (ml > lo && surely_too_big(ml)) continue;
         if (!B.schedule(ml)) return false;
         const int64_t ws = B.layout_workspace(false);
         if (ws <= P.opt.workspace_limit || ml == lo) {
