@@ -167,6 +167,59 @@ def cpu_oracle_sample(w, budget_s=20.0):
                       f"for the {k} bitstrings"}
 
 
+def measure_chain(name, precision, torch, tn, stream, fuse_bits, batches=4):
+    """Fused chains (tn_options.fuse) against the unfused steps on a workload
+    whose heaviest chain is worth fusing: per-step CUDA-event times over the
+    first `batches` slice batches, the chain kernel's algorithmic bytes (A_1
+    read, B_j reads, C_L write; its intermediates are never stored) and its
+    HBM roofline."""
+    from rqc import make_workload
+    w = make_workload(name)
+    peaks, _ = _peaks()
+    plans = {f: tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, workspace_limit=200 << 30, fuse=f,
+                        fuse_max_bits=fuse_bits) for f in (0, 1)}
+    need = max(p.info["workspace_bytes"] for p in plans.values())
+    free, _ = torch.cuda.mem_get_info()
+    if need > 0.9 * free:
+        return {"workload": name, "skipped": f"needs {need / 2**30:.1f} GiB"}
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    amps = torch.zeros(2 * w.bits.shape[0], dtype=torch.float64, device="cuda")
+    nb = min(batches, plans[1].info["n_batches"])
+    res = {}
+    for f, p in plans.items():
+        p.tn_plan_bind(ws, stream=stream)
+        p.tn_plan_profile(True)
+        p.tn_contract(amps, precision, 0, nb, stream=stream)  # warm-up
+        p.tn_contract(amps, precision, 0, nb, stream=stream)
+        ms, fam = p.tn_plan_step_times()
+        res[f] = (ms, fam, p.tn_plan_steps())
+        p.tn_plan_profile(False)
+    ms1, fam1, st1 = res[1]
+    ms0, _, st0 = res[0]
+    chains = {}
+    for i, s in enumerate(st1):
+        if s["chain"] >= 0:
+            chains.setdefault(s["chain"], []).append(i)
+    best = max(chains.values(), key=lambda ids: sum(ms0[i] for i in ids))
+    t_unfused = float(sum(ms0[i] for i in best))
+    t_fused = float(ms1[best[-1]])
+    first, last = st1[best[0]], st1[best[-1]]
+    # algorithmic bytes per pass: A_1 + every B_j + C_L
+    a_bytes = 8.0 * first["n_inst_a"] * 2.0 ** first["rank_a"]
+    b_bytes = sum(8.0 * st1[i]["n_inst_b"] * 2.0 ** st1[i]["rank_b"] for i in best)
+    c_bytes = 8.0 * last["n_inst"] * 2.0 ** (last["mb"] + last["nb"])
+    runs = sum(1 for b in range(nb) if b == 0 or st1[best[-1]]["level"] <= (b & -b).bit_length() - 1)
+    alg = (a_bytes + b_bytes + c_bytes) * runs
+    ach = alg / (t_fused / 1e3) / 1e9
+    del ws
+    torch.cuda.empty_cache()
+    return {"workload": name, "precision": precision, "slice_batches": nb, "chains": len(chains), "d_t": fuse_bits,
+            "heaviest_chain_steps": best, "unfused_ms": t_unfused, "fused_ms": t_fused,
+            "speedup": t_unfused / t_fused if t_fused > 0 else None,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes": alg, "kernel": "k_chain"}}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -211,7 +264,8 @@ def run_ours(args, world, rank, local):
     free, _ = torch.cuda.mem_get_info()
     limit = min(int(args.ws_gib * 2 ** 30), int(free * 0.8))
     t0 = time.perf_counter()
-    plan = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit)
+    plan = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit, fuse=args.fuse,
+                   fuse_max_bits=args.fuse_bits)
     t_plan = time.perf_counter() - t0
     info = plan.info
     ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
@@ -307,7 +361,7 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel family
     peaks, peak_src = _peaks()
     steps = plan.tn_plan_steps()
-    fam_names = {0: "k_step_row", 1: "k_step_gemm_simt", 2: "k_step_gemm_tc"}
+    fam_names = {0: "k_step_row", 1: "k_step_gemm_simt", 2: "k_step_gemm_tc", 3: "k_chain"}
     fam_ms, fam_bytes, fam_flops, fam_launch = {}, {}, {}, {}
     for s, st in enumerate(steps):
         f = int(kernels[s]) if kernels is not None else 0
@@ -326,7 +380,7 @@ def run_ours(args, world, rank, local):
             json.dump({"precision": args.precision, "workload": args.workload, "steps": rows}, f)
     dom = max(fam_ms, key=fam_ms.get)
     sec = fam_ms[dom] / 1000.0
-    if dom == 0:
+    if dom in (0, 3):
         ach = fam_bytes[dom] / sec / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     elif dom == 1:
@@ -356,7 +410,8 @@ def run_ours(args, world, rank, local):
         for _ in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            p2 = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit)
+            p2 = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit, fuse=args.fuse,
+                         fuse_max_bits=args.fuse_bits)
             for s_, c_ in enumerate(cfg_now):
                 p2.tn_plan_set_config(s_, int(c_))
             p2.tn_plan_bind(ws2, stream=stream)
@@ -370,6 +425,10 @@ def run_ours(args, world, rank, local):
         e2e_s = statistics.mean(tw[1:])
         e2e = {"value": k * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(info["upload_bytes"]),
                "d2h_bytes_per_step": int(16 * k), "host_plan_s": t_plan}
+
+    chain = None
+    if rank == 0 and args.chain_workload:
+        chain = measure_chain(args.chain_workload, args.precision, torch, tn, stream, args.fuse_bits)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -394,6 +453,7 @@ def run_ours(args, world, rank, local):
         "config_selection": selection,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "fused_chain": chain,
         "e2e": e2e,
         "gpu_launches": int(info["launches_per_call"]) * args.steps,
         "clocks": clocks,
@@ -423,6 +483,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--dump-steps", default=None, help="write per-step features and times (JSON) here")
+    ap.add_argument("--fuse", type=int, choices=[0, 1], default=1, help="fused chains of small-operand steps")
+    ap.add_argument("--fuse-bits", type=int, default=9, help="d^t: largest fused-chain tile, 2^d^t entries")
+    ap.add_argument("--chain-workload", default="grid6x7_m10",
+                    help="workload whose heaviest fused chain is timed against the unfused steps ('' to skip)")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":

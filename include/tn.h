@@ -151,6 +151,8 @@ typedef struct {
                                  consecutive m (resp. k) bits: contiguous runs */
     int32_t b_run_k, b_run_n;
     int64_t n_groups;         /* runs of output instances sharing one A instance */
+    int32_t chain;            /* fused chain holding the step (tn_options.fuse), -1: none */
+    int32_t chain_last;       /* 1 if the chain runs at this step (its last) */
     int8_t c_pos_m[40];       /* address bit of C holding each m bit, and each n bit */
     int8_t c_pos_n[24];
 } tn_step_info;
@@ -291,7 +293,8 @@ int tn_plan_check(tn_plan_t plan, void *stream);
  * events around every launch, read back by tn_plan_step_times, which
  * synchronises the events); ms has n_steps entries.  kernel (may be NULL)
  * receives the kernel family each step last ran: 0 per-row SIMT, 1 tiled
- * SIMT GEMM, 2 tensor-core GEMM. */
+ * SIMT GEMM, 2 tensor-core GEMM, 3 fused chain (the chain's time is booked
+ * on its last step). */
 int tn_plan_profile(tn_plan_t plan, int enable);
 int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t *kernel, int32_t n);
 

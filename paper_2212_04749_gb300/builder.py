@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libtn.so")
 ROOT = os.path.dirname(HERE)
 
-CU_SOURCES = ["kernels.cu", "gemm_tc.cu", "mlp.cu", "api.cu"]
+CU_SOURCES = ["kernels.cu", "gemm_tc.cu", "chain.cu", "mlp.cu", "api.cu"]
 CPP_SOURCES = ["plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

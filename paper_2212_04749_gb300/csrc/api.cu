@@ -41,6 +41,7 @@ struct PlanObj {
         bool ok;
     };
     std::vector<AMap> amap;           // per step: TMA descriptor of A (tensor-core steps)
+    std::vector<tnk::ChainDesc> chain_desc;  // per fused chain
     int32_t *err_flag = nullptr;      // device word for bounded waits
     bool profile = false;
     std::vector<cudaEvent_t> ev;          // pool, two per profiled launch
@@ -125,6 +126,50 @@ void build_descs(PlanObj *o) {
         d.max_group = (int32_t)mg;
         o->desc.push_back(d);
     }
+    // fused chains
+    o->chain_desc.clear();
+    for (const tnp::Chain &c : P.chains) {
+        tnk::ChainDesc cd;
+        std::memset(&cd, 0, sizeof(cd));
+        const int L = (int)c.steps.size();
+        const tnp::Step &s1 = P.steps[c.steps[0]], &sL = P.steps[c.steps[L - 1]];
+        const tnp::Node &A1 = P.nodes[s1.a], &CL = P.nodes[sL.node];
+        const bool rs = P.opt.rescale != 0;
+        cd.A = at<const float2>(o, A1.buf.data);
+        cd.C = at<float2>(o, CL.buf.data);
+        cd.sA = int64_t(1) << A1.rank;
+        cd.sC = int64_t(1) << CL.rank;
+        cd.mxA = rs ? at<const uint32_t>(o, A1.buf.mx) : nullptr;
+        cd.mxC = rs ? at<uint32_t>(o, CL.buf.mx) : nullptr;
+        cd.EA = at<const int32_t>(o, A1.buf.E);
+        cd.EC = at<int32_t>(o, CL.buf.E);
+        cd.tab = at<const int32_t>(o, c.off_tab);
+        cd.idx = at<const unsigned char>(o, c.off_idx);
+        cd.n_inst = CL.n_inst;
+        cd.L = L;
+        cd.tin = c.tin;
+        cd.no = c.no;
+        cd.tmax = c.tin;
+        for (int j = 0; j < L; ++j) {
+            const tnp::Step &st = P.steps[c.steps[j]];
+            const tnp::Node &B = P.nodes[st.b];
+            cd.B[j] = at<const float2>(o, B.buf.data);
+            cd.mxB[j] = rs ? at<const uint32_t>(o, B.buf.mx) : nullptr;
+            cd.EB[j] = at<const int32_t>(o, B.buf.E);
+            cd.kb[j] = st.kb;
+            cd.nb[j] = st.nb;
+            cd.tb[j] = c.tbits[j];
+            cd.tmax = std::max(cd.tmax, c.tbits[j]);
+            for (int b = 0; b < c.tbits[j]; ++b) cd.code[j][b] = c.code[j][b];
+        }
+        for (int b = 0; b < c.tin; ++b) cd.in_pos[b] = c.in_pos[b];
+        for (size_t b = 0; b < c.out_pos.size(); ++b) cd.out_pos[b] = c.out_pos[b];
+        for (int b = 0; b < c.no; ++b) {
+            cd.o_in[b] = c.o_in_pos[b];
+            cd.o_out[b] = c.o_out_pos[b];
+        }
+        o->chain_desc.push_back(cd);
+    }
     // TMA descriptors of the A operands, for every step the tensor-core
     // kernel can take (it may be chosen at run time)
     o->amap.assign(P.steps.size(), PlanObj::AMap{});
@@ -148,6 +193,16 @@ int effective_config(const PlanObj *o, int s) {
 }
 
 int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
+    const tnp::Step &S = o->P.steps[s];
+    if (S.chain >= 0) {  // fused chain: runs whole at its last step
+        if ((int)o->step_kernel.size() <= s) o->step_kernel.resize(o->P.steps.size(), -1);
+        o->step_kernel[s] = 3;
+        if (!S.chain_last) return TN_OK;
+        const cudaError_t e = tnk::launch_chain(o->chain_desc[S.chain], st);
+        if (e != cudaSuccess)
+            return set_err(TN_ECUDA, "fused chain at step " + std::to_string(s) + ": " + cudaGetErrorString(e));
+        return TN_OK;
+    }
     const int cfg = effective_config(o, s);
     tnk::StepDesc d = o->desc[s];
     d.sched = cfg & 1;
@@ -347,7 +402,7 @@ int tn_plan_query(tn_plan_t plan, tn_plan_info *info) {
     for (const auto &u : P.uploads) up += (int64_t)u.second.size();
     info->upload_bytes = up;
     double steps_run = 0;
-    for (const tnp::Step &st : P.steps) steps_run += st.runs;
+    for (const tnp::Step &st : P.steps) steps_run += (st.chain < 0 || st.chain_last) ? st.runs : 0.0;
     info->launches_per_call = (int64_t)steps_run + 2 * P.n_batches;  // + leaf fill and accumulate per batch
     return TN_OK;
 }
@@ -395,6 +450,8 @@ int tn_plan_steps(tn_plan_t plan, tn_step_info *out, int32_t n) {
         r.b_run_k = run(st.pBk);
         r.b_run_n = run(st.pBn);
         r.n_groups = st.n_groups;
+        r.chain = st.chain;
+        r.chain_last = st.chain_last ? 1 : 0;
         for (int j = 0; j < 40; ++j) r.c_pos_m[j] = j < st.mb ? st.pCm[j] : -1;
         for (int j = 0; j < 24; ++j) r.c_pos_n[j] = j < st.nb ? st.pCn[j] : -1;
     }
@@ -411,6 +468,7 @@ int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream) {
                                       std::to_string(o->P.ws_bytes));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     CU(tnk::init_kernels());
+    CU(tnk::init_chain_kernel());
     o->drop_graphs();
     o->ws = static_cast<uint8_t *>(workspace);
     o->ws_bytes = bytes;

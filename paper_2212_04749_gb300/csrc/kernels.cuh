@@ -79,6 +79,35 @@ cudaError_t make_a_map(const StepDesc &d, int64_t n_inst_a, CUtensorMap *map);
 cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int precision, int32_t *err_flag,
                                 cudaStream_t s);
 
+// Fused chain of small-operand steps (chain.cu); the planner's Chain as the
+// kernel sees it.
+constexpr int CH_MAXL = 6;    // steps
+constexpr int CH_MAXT = 10;   // tile bits
+constexpr int CH_MAXO = 40;   // outside bits
+constexpr int CH_MAX_SMEM = 160 * 1024;
+struct ChainDesc {
+    const float2 *A;              // A_1
+    float2 *C;                    // C_L
+    int64_t sA, sC;               // elements per instance
+    const float2 *B[CH_MAXL];     // B_j, 2^(kb_j + nb_j) elements per instance
+    const uint32_t *mxA, *mxB[CH_MAXL];  // max-|component| words (null: no rescale)
+    uint32_t *mxC;
+    const int32_t *EA, *EB[CH_MAXL];
+    int32_t *EC;
+    const int32_t *tab;           // per C_L instance: a_1, b_1 .. b_L
+    const unsigned char *idx;     // index tables (plan.hpp, Chain::off_idx)
+    int64_t n_inst;               // C_L instances
+    int64_t oblocks;              // blocks per instance (set by the launcher)
+    int32_t L, tin, no, tmax;     // steps, A_1 tile bits, outside bits, largest tile bits
+    int32_t kb[CH_MAXL], nb[CH_MAXL], tb[CH_MAXL];
+    int8_t code[CH_MAXL][CH_MAXT];      // per output tile bit: 0x80 | n bit, or A tile bit
+    int8_t in_pos[CH_MAXT], out_pos[CH_MAXT];
+    int8_t o_in[CH_MAXO], o_out[CH_MAXO];
+};
+size_t chain_smem_bytes(const ChainDesc &d);
+cudaError_t init_chain_kernel();
+cudaError_t launch_chain(ChainDesc d, cudaStream_t s);
+
 // Cost-model MLP (mlp.cu); sizes and parameter layout in include/tn.h.
 size_t mlp_grad_scratch_bytes(int64_t n);
 cudaError_t mlp_forward(const float *params, const float *X, int64_t n, float *y, cudaStream_t s);

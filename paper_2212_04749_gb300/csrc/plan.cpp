@@ -411,6 +411,189 @@ struct Builder {
         return true;
     }
 
+    // (A instance, B instance) of output instance i of step st
+    std::pair<int32_t, int32_t> inst_ab(const Step &st, int64_t i) const {
+        const Node &nd = P.nodes[st.node];
+        const bool a_left = st.a == nd.left;
+        const std::vector<int32_t> &sgA = a_left ? nd.sigL : nd.sigR, &otA = a_left ? nd.outL : nd.outR;
+        const std::vector<int32_t> &sgB = a_left ? nd.sigR : nd.sigL, &otB = a_left ? nd.outR : nd.outL;
+        const int64_t sg = i / nd.n_out, bt = i % nd.n_out;
+        return {int32_t(int64_t(sgA[sg]) * P.nodes[st.a].n_out + otA[bt]),
+                int32_t(int64_t(sgB[sg]) * P.nodes[st.b].n_out + otB[bt])};
+    }
+
+    // Bit maps of a candidate chain (see Chain); false if a tile exceeds
+    // 2^dt entries.
+    bool chain_bits(const std::vector<int> &ch, int dt, Chain &c) const {
+        const int L = (int)ch.size();
+        const Step &s1 = P.steps[ch[0]];
+        const Node &A1 = P.nodes[s1.a];
+        c = Chain();
+        // follow every free bit of A_1 through the chain; the ones no step
+        // contracts are the outside bits
+        std::vector<std::vector<int>> opos;  // per outside bit: its address bit in C_1 .. C_L
+        for (int i = 0; i < s1.mb; ++i) {
+            int idx = i;
+            bool alive = true;
+            std::vector<int> at;
+            for (int j = 0; j < L && alive; ++j) {
+                const int p = P.steps[ch[j]].pCm[idx];
+                at.push_back(p);
+                if (j + 1 < L) {
+                    const int kn = P.steps[ch[j + 1]].kb;
+                    if (p < kn) alive = false;
+                    else idx = p - kn;
+                }
+            }
+            if (!alive) continue;
+            c.o_in_pos.push_back(int8_t(s1.kb + i));
+            c.o_out_pos.push_back(int8_t(at.back()));
+            opos.push_back(at);
+        }
+        // widen the tiles: the lowest outside bits (by address in A_1) join
+        // every tile as pass-through rows, until the largest tile reaches
+        // 2^dt entries, so that a warp has enough rows to spread over lanes
+        {
+            int widest = A1.rank - (int)opos.size();
+            for (int j = 0; j < L; ++j)
+                widest = std::max(widest, P.nodes[P.steps[ch[j]].node].rank - (int)opos.size());
+            if (widest > dt) return false;
+            int extra = std::min(dt - widest, (int)opos.size());
+            while (extra-- > 0) {
+                size_t lo = 0;
+                for (size_t q = 1; q < opos.size(); ++q)
+                    if (c.o_in_pos[q] < c.o_in_pos[lo]) lo = q;
+                opos.erase(opos.begin() + lo);
+                c.o_in_pos.erase(c.o_in_pos.begin() + lo);
+                c.o_out_pos.erase(c.o_out_pos.begin() + lo);
+            }
+        }
+        c.no = (int)opos.size();
+        if (c.no > 40) return false;
+        std::vector<int> prev;  // tile bits (address bits, ascending) of the current A operand
+        for (int p = 0; p < A1.rank; ++p)
+            if (std::find(c.o_in_pos.begin(), c.o_in_pos.end(), p) == c.o_in_pos.end()) prev.push_back(p);
+        c.tin = (int)prev.size();
+        if (c.tin > dt) return false;
+        for (int p : prev) c.in_pos.push_back(int8_t(p));
+        for (int j = 0; j < L; ++j) {
+            const Step &st = P.steps[ch[j]];
+            const int rank = P.nodes[st.node].rank;
+            std::vector<int> cur;
+            for (int p = 0; p < rank; ++p) {
+                bool outside = false;
+                for (const auto &at : opos) outside = outside || at[j] == p;
+                if (!outside) cur.push_back(p);
+            }
+            if ((int)cur.size() > dt) return false;
+            std::vector<int8_t> code;
+            for (int p : cur) {
+                int8_t v = -1;
+                for (int i = 0; i < st.nb; ++i)
+                    if (st.pCn[i] == p) v = int8_t(0x80 | i);
+                for (int i = 0; i < st.mb && v == -1; ++i)
+                    if (st.pCm[i] == p) {
+                        const int pa = st.kb + i;  // address bit in A
+                        const auto it = std::find(prev.begin(), prev.end(), pa);
+                        if (it == prev.end()) return false;  // cannot happen: non-outside m bits are tile bits
+                        v = int8_t(it - prev.begin());
+                    }
+                if (v == -1) return false;
+                code.push_back(v);
+            }
+            // the contracted bits are the lowest tile bits of A
+            for (int k = 0; k < st.kb; ++k)
+                if (k >= (int)prev.size() || prev[k] != k) return false;
+            c.tbits.push_back((int)cur.size());
+            c.code.push_back(code);
+            prev = cur;
+        }
+        for (int p : prev) c.out_pos.push_back(int8_t(p));
+        // index tables
+        c.inoff.assign(size_t(1) << c.tin, 0);
+        for (size_t e = 0; e < c.inoff.size(); ++e)
+            for (int b = 0; b < c.tin; ++b)
+                if ((e >> b) & 1) c.inoff[e] += int64_t(1) << c.in_pos[b];
+        c.outoff.assign(size_t(1) << c.tbits.back(), 0);
+        for (size_t t = 0; t < c.outoff.size(); ++t)
+            for (size_t b = 0; b < c.out_pos.size(); ++b)
+                if ((t >> b) & 1) c.outoff[t] += int64_t(1) << c.out_pos[b];
+        c.rowin.assign(L, {});
+        c.rowout.assign(L, {});
+        c.colout.assign(L, {});
+        for (int j = 0; j < L; ++j) {
+            const Step &st = P.steps[ch[j]];
+            const int tb = c.tbits[j];
+            const int rows = 1 << (tb - st.nb);
+            c.rowin[j].assign(rows, 0);
+            c.rowout[j].assign(rows, 0);
+            for (int r = 0; r < rows; ++r) {
+                int qb = 0;
+                for (int b = 0; b < tb; ++b) {
+                    const int cd = c.code[j][b];
+                    if (cd & 0x80) continue;  // n bit
+                    if ((r >> qb) & 1) {
+                        c.rowin[j][r] |= 1 << cd;
+                        c.rowout[j][r] |= 1 << b;
+                    }
+                    ++qb;
+                }
+            }
+            c.colout[j].assign(size_t(1) << st.nb, 0);
+            for (int n = 0; n < (1 << st.nb); ++n)
+                for (int b = 0; b < tb; ++b) {
+                    const int cd = c.code[j][b];
+                    if ((cd & 0x80) && ((n >> (cd & 0x7f)) & 1)) c.colout[j][n] |= 1 << b;
+                }
+        }
+        return true;
+    }
+
+    // Fused chains (opt.fuse): greedy, in step order.
+    void find_chains() {
+        P.chains.clear();
+        for (Step &st : P.steps) {
+            st.chain = -1;
+            st.chain_last = false;
+        }
+        if (!P.opt.fuse) return;
+        const int dt = std::max(1, std::min(P.opt.fuse_max_bits > 0 ? P.opt.fuse_max_bits : 7, CHAIN_MAX_TILE_BITS));
+        const int ns = (int)P.steps.size();
+        std::vector<int> consumer(P.nodes.size(), -1);
+        for (int s = 0; s < ns; ++s) {
+            consumer[P.steps[s].a] = s;
+            consumer[P.steps[s].b] = s;
+        }
+        auto small = [](const Step &st) { return st.kb + st.nb <= 8; };
+        for (int s = 0; s < ns; ++s) {
+            if (P.steps[s].chain >= 0 || !small(P.steps[s])) continue;
+            std::vector<int> ch{s};
+            Chain c;
+            while ((int)ch.size() < CHAIN_MAX_STEPS) {
+                const Step &last = P.steps[ch.back()];
+                const int nx = consumer[last.node];
+                if (nx < 0) break;
+                const Step &nst = P.steps[nx];
+                if (nst.a != last.node || !small(nst) || nst.level != last.level || nst.chain >= 0) break;
+                if (P.nodes[nst.node].n_inst != P.nodes[last.node].n_inst || P.nodes[last.node].persistent) break;
+                std::vector<int> trial = ch;
+                trial.push_back(nx);
+                if (!chain_bits(trial, dt, c)) break;
+                ch = trial;
+            }
+            if (ch.size() < 2) continue;
+            chain_bits(ch, dt, c);
+            c.steps = ch;
+            for (int q : ch) P.steps[q].chain = (int)P.chains.size();
+            P.steps[ch.back()].chain_last = true;
+            // the chain reads A_1 and every B_j when it runs, at its last
+            // step: their buffers must live until then
+            P.nodes[P.steps[ch[0]].a].last_use = ch.back();
+            for (int q : ch) P.nodes[P.steps[q].b].last_use = ch.back();
+            P.chains.push_back(c);
+        }
+    }
+
     // Workspace layout; returns total bytes.
     int64_t layout_workspace(bool emit) {
         Plan &p = P;
@@ -602,6 +785,41 @@ struct Builder {
                 }
                 push_upload(p, st.off_inst_ab, ab);
                 push_upload(p, st.off_tile_rec, rec);
+            }
+        }
+        for (Chain &c : p.chains) {
+            const Step &last = p.steps[c.steps.back()];
+            const int64_t ni = p.nodes[last.node].n_inst;
+            const int L = (int)c.steps.size();
+            c.off_tab = take(ni * (L + 1) * 4);
+            {
+                std::vector<uint8_t> blob;
+                auto put = [&](const void *src, size_t n) {
+                    const uint8_t *b = static_cast<const uint8_t *>(src);
+                    blob.insert(blob.end(), b, b + n);
+                };
+                put(c.inoff.data(), c.inoff.size() * 8);
+                put(c.outoff.data(), c.outoff.size() * 8);
+                for (int j = 0; j < L; ++j) {
+                    put(c.rowin[j].data(), c.rowin[j].size() * 4);
+                    put(c.rowout[j].data(), c.rowout[j].size() * 4);
+                    put(c.colout[j].data(), c.colout[j].size() * 4);
+                }
+                c.off_idx = take((int64_t)blob.size());
+                if (emit) push_upload(p, c.off_idx, blob);
+            }
+            if (emit) {
+                std::vector<int32_t> tab(size_t(ni) * (L + 1));
+                for (int64_t i = 0; i < ni; ++i) {
+                    int64_t cur = i;
+                    for (int j = L - 1; j >= 0; --j) {
+                        const auto ab = inst_ab(p.steps[c.steps[j]], cur);
+                        tab[size_t(i) * (L + 1) + 1 + j] = ab.second;
+                        cur = ab.first;
+                    }
+                    tab[size_t(i) * (L + 1)] = int32_t(cur);
+                }
+                push_upload(p, c.off_tab, tab);
             }
         }
         // transient intermediates: first-fit over one full pass of the steps
@@ -876,6 +1094,7 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
         }
     }
     if (!B.schedule(chosen)) return false;
+    B.find_chains();
     for (Node &nd : P.nodes) { nd.buf = NodeBuf(); }
     P.peak_tensor_bytes = 0;
     P.ws_bytes = B.layout_workspace(true);
@@ -889,7 +1108,16 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
     for (const Step &st : P.steps) {
         const Node &nd = P.nodes[st.node];
         P.flops_exec += st.flops * st.runs;
-        P.bytes_min += st.bytes * st.runs;
+        double bytes = st.bytes;
+        if (st.chain >= 0) {  // a chain's intermediates are never stored
+            const double inner = 8.0 * double(nd.n_inst) * std::ldexp(1.0, nd.rank);
+            if (!st.chain_last) bytes -= inner;  // C_j of a non-final step
+            if (P.steps[P.chains[st.chain].steps[0]].node != st.node) {
+                const Node &A = P.nodes[st.a];
+                bytes -= 8.0 * double(A.n_inst) * std::ldexp(1.0, A.rank);  // A_j, j > 1
+            }
+        }
+        P.bytes_min += bytes * st.runs;
         const double macs = std::ldexp(1.0, st.mb + st.kb + st.nb);
         P.flops_ma += 8.0 * macs * std::ldexp(1.0, (int)nd.slices.size()) * nd.n_out;
         P.flops_sa += 8.0 * macs * std::ldexp(1.0, n_sliced) * double(P.k_unique);

@@ -102,8 +102,39 @@ struct Step {
     int64_t off_tile_rec = -1;         // per column tile: {first instance, count, A instance, first column}
     int64_t off_inst_ab = -1;          // per output instance: {A instance, B instance} (int32 pairs)
     int kernel = 0;          // 0 = per-row SIMT, 1 = tiled SIMT GEMM, 2 = tensor-core GEMM
+    int chain = -1;          // fused chain holding this step (-1: none)
+    bool chain_last = false; // the chain runs at its last step; the others launch nothing
     double flops = 0;        // executed per pass: 8 * n_inst * 2^{mb+kb+nb}
     double bytes = 0;        // A + B reads and C write per pass
+};
+
+// A fused chain (SM Sec. V.C): steps s_1..s_L where each step's A operand is
+// the previous step's output, instance counts do not grow, and every side
+// operand B_j is small.  It runs as one kernel at s_L: per output instance
+// and per value of the "outside" bits O (A_1's free bits that no chain step
+// touches), a tile of A_1 (its other bits) is loaded once, multiplied by
+// B_1 .. B_L in shared memory, and written to C_L; the intermediates
+// C_1 .. C_{L-1} are never stored.
+constexpr int CHAIN_MAX_STEPS = 6;
+constexpr int CHAIN_MAX_TILE_BITS = 10;
+struct Chain {
+    std::vector<int> steps;            // s_1 .. s_L
+    int tin = 0;                       // tile bits of A_1
+    int no = 0;                        // outside bits
+    std::vector<int> tbits;            // tile bits of C_j, j = 1..L
+    std::vector<int8_t> in_pos;        // address bit in A_1 of each A_1 tile bit (ascending)
+    std::vector<int8_t> o_in_pos, o_out_pos;  // address bit of each outside bit in A_1 and C_L
+    std::vector<int8_t> out_pos;       // address bit in C_L of each C_L tile bit (ascending)
+    std::vector<std::vector<int8_t>> code;  // per step, per output tile bit: 0x80|i (n bit i) or r (A tile bit r)
+    int64_t off_tab = -1;              // int32 per C_L instance: a_1, b_1 .. b_L
+    // index tables, uploaded at off_idx (int64 inoff[2^tin], int64
+    // outoff[2^tL], then per step int32 rowin[R_j], rowout[R_j], colout[N_j]):
+    // address offset in A_1 of each input tile entry, in C_L of each output
+    // tile entry, and per step the input / output tile index of each row
+    // (R_j = 2^(tbits_j - nb_j)) and the output tile bits of each column
+    std::vector<int64_t> inoff, outoff;
+    std::vector<std::vector<int32_t>> rowin, rowout, colout;
+    int64_t off_idx = -1;
 };
 
 struct Plan {
@@ -120,6 +151,7 @@ struct Plan {
     int64_t n_batches = 1;
     std::vector<Node> nodes;          // 2T-1
     std::vector<Step> steps;          // SSA order
+    std::vector<Chain> chains;        // fused chains (opt.fuse)
     int n_static_steps = 0;
     int root = -1;
     int max_rank = 0;

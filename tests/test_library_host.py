@@ -230,3 +230,30 @@ def test_config_override_rules(tn):
     assert got[big] == 3 and got[0] == 2
     p.tn_plan_set_config(big, -1)
     assert p.tn_plan_get_configs()[big] == base[big]
+
+
+@pytest.mark.parametrize("name", ["grid3x4_m8", "grid5x6_m14"])
+def test_fused_chains_are_well_formed(tn, name):
+    # every chain: consecutive producer -> consumer steps on the A side,
+    # small side operands, one slice level, equal instance counts; the plan
+    # launches fewer kernels and counts fewer algorithmic bytes
+    w = make_workload(name)
+    p0 = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, fuse=0)
+    p1 = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, fuse=1)
+    st = p1.tn_plan_steps()
+    chains = {}
+    for i, s in enumerate(st):
+        if s["chain"] >= 0:
+            chains.setdefault(s["chain"], []).append(i)
+    assert chains
+    for ids in chains.values():
+        assert 2 <= len(ids) <= 6 and ids == sorted(ids)
+        assert [st[i]["chain_last"] for i in ids] == [0] * (len(ids) - 1) + [1]
+        for i, j in zip(ids, ids[1:]):
+            assert st[j]["a"] == st[i]["node"]
+            assert st[j]["n_inst"] == st[i]["n_inst"] and st[j]["level"] == st[i]["level"]
+        for i in ids:
+            assert st[i]["kb"] + st[i]["nb"] <= 8
+    assert p1.info["launches_per_call"] < p0.info["launches_per_call"]
+    assert p1.info["bytes_min"] < p0.info["bytes_min"]
+    assert p1.info["flops_exec"] == p0.info["flops_exec"]
