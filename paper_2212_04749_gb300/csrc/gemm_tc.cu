@@ -254,6 +254,7 @@ struct Cfg {
 struct alignas(16) EpiMeta {
     int32_t inst[TBN];    // output instance of each column (-1: none)
     float sc[TBN];        // 2^-(ea + eb): the column's power-of-two rescale
+    uint32_t mx[TBN];     // max-|component| of a run of an instance's columns, at the run's first column
     int64_t base;         // element offset of tile element (row 0, column 0) in C
     int32_t ncv, pad;     // valid columns
 };
@@ -625,6 +626,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         // fills tile j's slot (instance and rescale per column, C base
         // offset, valid columns).  The instance exponents E_C are written
         // here as well, once per instance: at its n = 0 column in row tile 0.
+        auto flush_max = [&](const EpiMeta &em) {
+            if (!d.mxC) return;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int c = lane + 32 * q;
+                const uint32_t v = em.mx[c];
+                if (v && em.inst[c] >= 0) record_max(d.mxC + em.inst[c], v);
+            }
+        };
         int64_t mt0 = 0, mt1 = 0, mt2 = 0;
         int4 r0 = make_int4(0, 0, 0, 0), r1 = r0, r2 = r0;
         int ib0[2] = {-1, -1};
@@ -669,6 +679,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 break;
             }
             EpiMeta &em = X.epi[slot];
+            // the slot's previous tile (j - MS) is done: its maxima go to
+            // global memory from here, off the epilogue's path
+            if (j >= MS) flush_max(em);
             const int ea = d.mxA ? exp_of(mxa) : 0;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -676,6 +689,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 const int inst = col_inst(r0, c);
                 const int eb = d.mxB ? exp_of(mxb[q]) : 0;
                 em.inst[c] = inst;
+                em.mx[c] = 0u;
                 em.sc[c] = pow2f(-(ea + eb));
                 if (inst >= 0 && mt0 == 0 && ((int64_t(r0.w) + c) & (N - 1)) == 0) d.EC[inst] = EAv + ea + EBv[q] + eb;
             }
@@ -692,6 +706,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             ib0[1] = ib1[1];
             r1 = r2;
             mt1 = mt2;
+        }
+        // flush the last MS tiles once the epilogue has released them
+        for (int64_t j = my_tiles > MS ? my_tiles - MS : 0; ok && j < my_tiles; ++j) {
+            const int slot = int(j % MS);
+            const bool w = mbar_wait(&X.mempty[slot], uint32_t(j / MS) & 1u);
+            if (!__all_sync(0xffffffffu, w)) {
+                ok = false;
+                break;
+            }
+            flush_max(X.epi[slot]);
         }
         if (!ok) give_up();
         __syncwarp();
@@ -779,8 +803,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     if (d.mxC) {
                         // max-|component| of each instance's columns: runs of
                         // min(N, 8) columns folded in registers, then one warp
-                        // reduction per run; scaled by the run's power of two
-                        // (exact) and merged into the instance's word
+                        // reduction per run, scaled by the run's power of two
+                        // (exact) and merged in the slot (shared memory); the
+                        // metadata warp carries the slot's maxima to global
+                        // memory when it recycles the slot
                         const int run = N < 8 ? N : 8;
                         uint32_t a[8];
 #pragma unroll
@@ -796,7 +822,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                             if ((j & (run - 1)) == 0 && cp + j < ncv) {
                                 const uint32_t r = __reduce_max_sync(0xffffffffu, a[j]);
                                 if (lane == 0 && r)
-                                    record_max(d.mxC + em.inst[cp + j], __float_as_uint(__uint_as_float(r) * em.sc[cp + j]));
+                                    atomicMax(const_cast<uint32_t *>(&em.mx[cp + j]),
+                                              __float_as_uint(__uint_as_float(r) * em.sc[cp + j]));
                             }
                     }
                     // scale and stage in destination order
@@ -817,9 +844,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     }
                 }
                 if (!act) continue;
+                const int ncw = ncv - c0;  // valid columns of this block
                 __syncwarp();
                 const int64_t wb = em.base + qoff + mp.hoff[h * 2 + sub] + offL;
-                const int ncw = ncv - c0;  // valid columns of this block
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     // compressed elements 2u, 2u + 1 with u = lane + 32 i
