@@ -116,11 +116,26 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-// bounded wait (WAIT_NS of wall clock); false on timeout
+// try_wait that may suspend the thread for up to `ns` nanoseconds (it
+// returns as soon as the phase completes)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait (WAIT_NS of wall clock); false on timeout.  Waiting threads
+// sleep in the barrier (suspend hint) instead of spinning on issue slots.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait_sleep(bar, parity, 100000u))
         if (gtimer() - t0 > WAIT_NS) return false;
     return true;
 }
