@@ -336,6 +336,12 @@ def run_ours(args, world, rank, local):
         step_ms += ms / prof_runs
     plan.tn_plan_profile(False)
 
+    # linear XEB of this run's amplitudes (FP64 reduction on the device)
+    xeb_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tn.tn_xeb(amps, k, w.circuit.n_qubits, xeb_dev, stream=stream)
+    torch.cuda.synchronize()
+    xeb = float(xeb_dev.item())
+
     # accuracy of this run against the stored oracle values
     got = amps.cpu().numpy().view(np.complex128)
     ref = _golden(args.workload) if rank == 0 else None
@@ -449,6 +455,7 @@ def run_ours(args, world, rank, local):
                    "workspace_gib": info["workspace_bytes"] / 2 ** 30},
         "tflops_algorithmic": tflops,
         "rel_l2_vs_oracle": err,
+        "xeb": xeb,
         "other_forms": others or None,
         "config_selection": selection,
         "roofline": roof,

@@ -299,3 +299,34 @@ def choose_slices(struct: NetworkStructure, tree: ContractionTree, k: int,
         sliced.append(best_e)
         S |= 1 << best_e
     return sorted(sliced)
+
+
+def refine_slices(struct: NetworkStructure, tree: ContractionTree, k: int, sliced: List[int],
+                  max_rank: Optional[int] = None, rounds: int = 2, max_evals: int = 4000) -> List[int]:
+    """Local search over the sliced-edge set: replace one sliced edge by an
+    unsliced bond edge whenever that lowers the estimated multiple-amplitude
+    cost summed over all slices (Eq. (1)) and keeps the largest per-instance
+    rank within ``max_rank`` (or within the current largest rank).  Every
+    unsliced edge is a candidate; first improvement, at most ``max_evals``
+    cost evaluations."""
+    cur = sorted(sliced)
+    best = estimate_cost(struct, tree.ssa, k, cur)
+    cap = best.max_rank if max_rank is None else max(max_rank, best.max_rank)
+    evals = 0
+    for _ in range(rounds):
+        improved = False
+        for i in range(len(cur)):
+            for e in range(struct.n_edges):
+                if e in cur:
+                    continue
+                if evals >= max_evals:
+                    return cur
+                trial = sorted(cur[:i] + [e] + cur[i + 1:])
+                c = estimate_cost(struct, tree.ssa, k, trial)
+                evals += 1
+                if c.max_rank <= cap and c.flops < best.flops * (1.0 - 1e-9):
+                    best, cur = c, trial
+                    improved = True
+        if not improved:
+            break
+    return cur

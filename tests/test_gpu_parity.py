@@ -10,7 +10,7 @@ depend on which other bitstrings share the pass).
 import numpy as np
 import pytest
 
-from gpu_helpers import rel_l2, run_plan, run_slices
+from gpu_helpers import require_cuda, rel_l2, run_plan, run_slices
 from oracle import sv, tn as otn, xeb
 from rqc import make_workload, grid_layout, random_circuit, network_structure
 from rqc.bitstrings import uniform_bitstrings
@@ -160,3 +160,18 @@ def test_graph_replay_equals_eager_bitwise():
         out[graphs] = res
     for r in out[0] + out[1]:
         assert np.array_equal(r, out[0][0])
+
+
+def test_empty_bitstring_batch_is_a_no_op():
+    # k = 0: planning and contraction succeed and write nothing
+    torch, tn = require_cuda()
+    w = make_workload("grid3x4_m8")
+    p = tn.Plan(w.circuit, w.bits[:0], w.tree.ssa)
+    assert p.info["n_unique"] == 0
+    ws = torch.empty(max(p.info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
+    p.tn_plan_bind(ws, stream=torch.cuda.current_stream())
+    sentinel = torch.full((4,), 7.0, dtype=torch.float64, device="cuda")
+    p.tn_contract(sentinel, "bf16x3", stream=torch.cuda.current_stream())
+    p.tn_plan_check(stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert torch.all(sentinel == 7.0)

@@ -33,23 +33,43 @@ def _gemm_everywhere(st):
     return 1
 
 
-@pytest.fixture(scope="module")
-def case20():
+def _case20(tree):
+    from rqc.tree import ContractionTree
     c = random_circuit(grid_layout(4, 5), 12, seed=21)
     s = network_structure(c)
     bits = uniform_bitstrings(20, 1500, seed=5)
-    ssa = candidate_trees(s, 1500, seed=2, trials=2)[0]
-    from rqc.tree import ContractionTree
+    ssa = candidate_trees(s, 1500, seed=2, trials=2)[tree]
     sl = choose_slices(s, ContractionTree(ssa=ssa), 1500, n_sliced=2)
     return c, bits, ssa, sl, sv.amplitudes(c, bits)
 
 
+@pytest.fixture(scope="module")
+def case20():
+    return _case20(0)
+
+
+@pytest.fixture(scope="module")
+def case20_shapes():
+    # another candidate tree of the same circuit: its GEMM-shaped steps span
+    # M = 2^6 .. 2^16 rows, so the tensor-core path meets its edge shapes
+    return _case20(2)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
-def test_forced_gemm_path_matches_state_vector(case20, prec):
-    c, bits, ssa, sl, ref = case20
+@pytest.mark.parametrize("case", ["case20", "case20_shapes"])
+def test_forced_gemm_path_matches_state_vector(case, prec, request):
+    c, bits, ssa, sl, ref = request.getfixturevalue(case)
     got, p = run_plan(c, bits, ssa, sl, precision=prec, force_kernel=_gemm_everywhere)
+    if case == "case20_shapes" and prec != "fp32":
+        # the tensor-core steps include K = 8 (half a chunk), M = 64 (half a
+        # row tile), partial column tiles, and both N < 16 and N >= 64 per
+        # instance
+        tc = [s for s, k in zip(p.tn_plan_steps(), p.tn_plan_step_times()[1]) if k == 2]
+        assert any(s["kb"] == 3 for s in tc) and any(s["mb"] == 6 for s in tc)
+        assert any(s["nb"] < 4 for s in tc) and any(s["nb"] >= 6 for s in tc)
+        assert any((s["n_inst"] // max(s["n_groups"], 1) << s["nb"]) % 64 for s in tc)
     err = rel_l2(got, ref)
-    print(f"forced GEMM 20q {prec}: rel-L2 {err:.3e}")
+    print(f"forced GEMM 20q {case} {prec}: rel-L2 {err:.3e}")
     assert err <= _tol(prec), err
 
 

@@ -137,3 +137,18 @@ def test_trees_are_valid_ssa_and_sliced_counts():
     assert len(w2.tree.sliced) == 10
     c = estimate_cost(w2.struct, w2.tree.ssa, 4096, w2.tree.sliced)
     assert c.max_rank <= 28
+
+
+def test_refine_slices_keeps_size_and_rank_and_never_raises_cost():
+    from rqc.tree import ContractionTree, choose_slices, refine_slices
+    w = make_workload("grid3x4_m8")
+    for seed in (1, 2):
+        ssa = candidate_trees(w.struct, 64, seed=seed, trials=2)[0]
+        tree = ContractionTree(ssa=ssa)
+        sl = choose_slices(w.struct, tree, 64, n_sliced=2)
+        c0 = estimate_cost(w.struct, ssa, 64, sl)
+        ref = refine_slices(w.struct, tree, 64, sl, max_evals=300)
+        c1 = estimate_cost(w.struct, ssa, 64, ref)
+        assert len(ref) == len(set(ref)) == len(sl)
+        assert all(0 <= e < w.struct.n_edges for e in ref)
+        assert c1.flops <= c0.flops and c1.max_rank <= c0.max_rank
