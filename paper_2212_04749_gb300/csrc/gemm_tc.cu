@@ -17,12 +17,13 @@
 //            accumulator.
 //
 // Tile: 128 rows x 64 complex columns (MMA M = 128, N = 128), K in chunks
-// of 16 complex (32 real).  Shared-memory operands use the canonical K-major
-// no-swizzle layout (core matrix 8 rows x 16 bytes; LBO = distance between
-// K-adjacent core matrices = 128 rows x 16 B, SBO = distance between 8-row
-// groups = 128 B).  A arrives by TMA already in that order (FP32; TF32 uses
-// it as is, BF16x3 splits it into hi/lo planes); B columns are gathered per
-// instance and expanded into the real 2x2 form.  One thread issues the MMAs
+// of 16 complex (32 real).  A arrives by TMA as 128 rows of 128 bytes in
+// the 128-byte swizzled K-major layout (TF32 uses it as is; BF16x3 splits
+// it in place, hi and lo K steps alternating within each row).  B columns
+// are gathered per instance, expanded into the real 2x2 form and stored in
+// the K-major no-swizzle layout (core matrix 8 rows x 16 bytes; LBO =
+// distance between K-adjacent core matrices = 128 rows x 16 B, SBO =
+// distance between 8-row groups = 128 B).  One thread issues the MMAs
 // into an FP32 accumulator in TMEM (two 128-column accumulators), read back
 // with tcgen05.ld for the epilogue: power-of-two scale and max-|x|
 // tracking, then each half tile goes through shared memory, reordered by
@@ -31,6 +32,7 @@
 //
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // code in *err, skips the remaining work, frees its TMEM and returns.
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -81,6 +83,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     d |= uint64_t((sbo >> 4) & 0x3fffu) << 32;
     d |= uint64_t(1) << 46;
     return d;
+}
+
+// shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout: rows of 128 bytes, 8-row atoms of 1024 bytes (SBO), the
+// 16-byte units of row r XOR-permuted by r mod 8.  A K step inside the row
+// starts 32 bytes further on (the swizzle is applied to the address).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return sdesc(saddr, 16, 1024) | (uint64_t(2) << 61);
 }
 
 // instruction descriptor: FP32 accumulate, A/B K-major, M = 128, N = TBNR
@@ -196,14 +206,13 @@ __device__ __forceinline__ void cp_async_wait(int pending) {
     }
 }
 
-// 4-D TMA tile load (shared::cluster destination = this CTA's own memory),
-// completing on an mbarrier with a byte count.
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+// 3-D TMA tile load (shared::cluster destination = this CTA's own memory)
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -215,16 +224,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 
 // Persistent warp-specialised kernel, five warpgroups.
 //   warps 0-7  : B columns by cp.async (LOOK chunks ahead), expanded into the
-//                real 2x2 block form; BF16x3: A split into hi/lo from the
-//                raw ring.  TF32 reads A straight from the raw ring.
+//                real 2x2 block form; BF16x3: A split into hi/lo in place in
+//                the TMA ring.  TF32 reads A straight from the ring.
 //   warps 8-15 : epilogue, two warps per TMEM lane quadrant (warp % 4), each
 //                draining 16 complex columns of each half tile; two
 //                accumulators so that a tile's epilogue overlaps the next
 //                tile's MMAs.
 //   warp 16    : TMEM allocation; lane 0 issues tcgen05.mma and commits.
 //   warp 17    : lane 0 streams A: one TMA tile load per chunk (128 rows x
-//                16 complex k, already in the K-major core-matrix order)
-//                into a ring of RST raw stages, several chunks ahead.
+//                16 complex k, 128-byte rows, swizzled) into a ring of RST
+//                stages, several chunks ahead.
 //   warp 18    : epilogue metadata (instances, rescale, C offsets, E_C),
 //                a ring of MS tiles ahead of the epilogue.
 // The epilogue warpgroups take registers from the others (setmaxnreg).
@@ -245,24 +254,30 @@ constexpr int MS = 4;         // epilogue metadata ring (tiles ahead of the epil
 constexpr int ACC_COLS = 128;
 constexpr int TMEM_COLS2 = 256;
 
-template <int PREC>
+// Shared-memory layout.  Streaming B (BRES = false): A ring, B MMA stages,
+// raw B pieces, epilogue staging.  Resident B (BRES = true): a pool of
+// NSLOT 16 KB slots holding the A ring (first nrs slots) and the current
+// group's whole B operand (the next nct x nch slots), then the staging.
+template <int PREC, bool BRES>
 struct Cfg {
-    static constexpr int ST = PREC == 1 ? 4 : 3;      // MMA stages (B; BF16x3: also A hi/lo)
-    static constexpr int RST = PREC == 1 ? 4 : 3;     // raw A stages filled by TMA
+    static constexpr int ST = PREC == 1 ? 4 : 3;      // MMA stages (streaming B)
+    static constexpr int RST = BRES ? 8 : (PREC == 1 ? 4 : 6);  // A stages (most)
     static constexpr int BRST = 4;                    // raw B stages (per-thread cp.async pieces)
-    static constexpr int LOOK = BRST - 1;             // B chunks issued ahead
-    static constexpr int SLOT_RAW = TBM * TBK * 8;    // FP32 A chunk, [16-byte k column][row]
-    static constexpr int SLOT_A = PREC == 2 ? TBM * TBKR * 4 : 0;
-    static constexpr int SLOT_B = TBNR * TBKR * 4;
+    static constexpr int LOOK = BRST - 1;             // B chunks issued ahead (streaming B)
+    static constexpr int SLOT_RAW = TBM * TBK * 8;    // FP32 A chunk: 128 rows x 128 bytes, 128-byte swizzle
+    static constexpr int SLOT_B = TBNR * TBKR * 4;    // one B chunk in MMA form (TF32, or BF16 hi + lo)
     static constexpr int SLOT_BRAW = TBN * TBK * 8;   // raw complex64 B chunk
     static constexpr int STAGE = 8 * 32 * 16 * 8;     // 4 KB per epilogue warp, in destination order
+    static constexpr int NSLOT = 11;                  // resident-B pool
     static constexpr int OFF_RAW = 0;
-    static constexpr int OFF_A = OFF_RAW + RST * SLOT_RAW;
-    static constexpr int OFF_B = OFF_A + ST * SLOT_A;
-    static constexpr int OFF_BRAW = OFF_B + ST * SLOT_B;
-    static constexpr int OFF_STAGE = OFF_BRAW + BRST * SLOT_BRAW;
+    static constexpr int OFF_B = BRES ? 0 : OFF_RAW + RST * SLOT_RAW;
+    static constexpr int OFF_BRAW = BRES ? 0 : OFF_B + ST * SLOT_B;
+    static constexpr int OFF_STAGE = BRES ? NSLOT * SLOT_RAW : OFF_BRAW + BRST * SLOT_BRAW;
     static constexpr int OFF_CTRL = OFF_STAGE + STAGE;
+    static_assert(SLOT_B == SLOT_RAW, "pool slots hold A or B chunks");
+    static_assert(LOOK < BRST, "B pieces in flight fit the raw ring");
 };
+constexpr int BRES_MAX_B = 8;  // resident B: at most 8 chunks (nct x nch), so at least 3 A stages
 
 // Per-tile epilogue metadata, written by the metadata warp into a ring of
 // MS slots ahead of the epilogue.
@@ -292,18 +307,21 @@ struct EpiMap {
 };
 
 struct Ctrl {
-    uint64_t full[4], empty[4], rfull[8], rempty[8], tfull[2], tempty[2], mfull[MS], mempty[MS];
+    uint64_t full[4], empty[4], rfull[8], rempty[8], afull[8], tfull[2], tempty[2], mfull[MS], mempty[MS];
+    uint64_t bfull, bempty;  // resident B: loaded / no longer read by the MMAs
     uint32_t tmem_base;
     int32_t abort_;
     EpiMeta epi[MS];
     EpiMap map;
 };
 
-template <int PREC>
+template <int PREC, bool BRES>
 constexpr size_t smem_bytes() {
-    return size_t(Cfg<PREC>::OFF_CTRL) + sizeof(Ctrl) + 128;
+    return size_t(Cfg<PREC, BRES>::OFF_CTRL) + sizeof(Ctrl) + 1024;
 }
-static_assert(smem_bytes<1>() <= 232448 && smem_bytes<2>() <= 232448, "shared memory above 227 KB");
+static_assert(smem_bytes<1, false>() <= 232448 && smem_bytes<2, false>() <= 232448 &&
+                  smem_bytes<1, true>() <= 232448 && smem_bytes<2, true>() <= 232448,
+              "shared memory above 227 KB");
 
 // Tile T of a step.  Schedule 0: the tiles of one group (its column tiles
 // x row tiles) are numbered row tile major, column tile minor, so the
@@ -311,15 +329,17 @@ static_assert(smem_bytes<1>() <= 232448 && smem_bytes<2>() <= 232448, "shared me
 // read from DRAM about once.  Schedule 1: column tile major, row tile minor
 // (the B columns of a column tile stay in L2 across its row tiles).  Returns the column-tile record with its first column, and
 // the row tile in mt.
-__device__ __forceinline__ int4 tile_decode(const StepDesc &d, int64_t T, int64_t mtiles, int64_t &mt) {
+__device__ __forceinline__ int4 tile_decode(const StepDesc &d, int64_t T, int64_t mtiles, int64_t &mt,
+                                            int64_t *group = nullptr) {
     const int64_t e0 = T / mtiles;  // some column tile of T's group
     int4 r = __ldg(d.trec + e0);
+    const int64_t f = e0 - r.w / TBN;  // the group's first column tile
+    if (group) *group = f;
     if (d.sched != 0) {  // schedule 1: the row tiles of one column tile run consecutively
         mt = T - e0 * mtiles;
         return r;
     }
     const int64_t nct = ((int64_t(r.y) << d.nb) + TBN - 1) / TBN;
-    const int64_t f = e0 - r.w / TBN;  // the group's first column tile
     const int64_t local = T - f * mtiles;
     mt = local / nct;
     r.w = int((local - mt * nct) * TBN);
@@ -331,19 +351,132 @@ __device__ __forceinline__ int4 tile_decode(const StepDesc &d, int64_t T, int64_
 // spread over the banks
 __device__ __forceinline__ int stage_swz(int u) { return u ^ (((u >> 3) ^ (u >> 6)) & 7); }
 
+// One producer thread's B piece: column bcol, complex k 4 kqb .. 4 kqb + 3
+// of a chunk (p0, p1 = the four values), expanded into the real 2x2 form
+// (rows 2 bcol: Re, -Im; 2 bcol + 1: Im, Re) in the K-major no-swizzle
+// layout of a B slot; BF16x3 stores the hi plane, then the lo plane 8 KB on.
 template <int PREC>
+__device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const float4 p0, const float4 p1) {
+    const float2 t4[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
+                          make_float2(p1.z, p1.w)};
+    const float r0[8] = {t4[0].x, -t4[0].y, t4[1].x, -t4[1].y, t4[2].x, -t4[2].y, t4[3].x, -t4[3].y};
+    const float r1[8] = {t4[0].y, t4[0].x, t4[1].y, t4[1].x, t4[2].y, t4[2].x, t4[3].y, t4[3].x};
+    if (PREC == 1) {
+        *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol, 8 * kqb, 4)) = make_float4(r0[0], r0[1], r0[2], r0[3]);
+        *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol, 8 * kqb + 4, 4)) = make_float4(r0[4], r0[5], r0[6], r0[7]);
+        *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb, 4)) = make_float4(r1[0], r1[1], r1[2], r1[3]);
+        *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb + 4, 4)) = make_float4(r1[4], r1[5], r1[6], r1[7]);
+    } else {
+        __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            h0[q] = __float2bfloat16_rn(r0[q]);
+            l0[q] = __float2bfloat16_rn(r0[q] - __bfloat162float(h0[q]));
+            h1[q] = __float2bfloat16_rn(r1[q]);
+            l1[q] = __float2bfloat16_rn(r1[q] - __bfloat162float(h1[q]));
+        }
+        uint8_t *blo = base + TBNR * TBKR * 2;
+        *reinterpret_cast<uint4 *>(base + kmaj_off(2 * bcol, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(h0);
+        *reinterpret_cast<uint4 *>(blo + kmaj_off(2 * bcol, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(l0);
+        *reinterpret_cast<uint4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(h1);
+        *reinterpret_cast<uint4 *>(blo + kmaj_off(2 * bcol + 1, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(l1);
+    }
+}
+
+// BF16x3: split an FP32 A chunk into hi/lo in place.  The slot holds 128
+// rows of 32 real k (128 bytes, 128-byte swizzle); thread (row, half) reads
+// the 16 values of its half row (logical 16-byte units 4 half .. 4 half + 3)
+// and writes, over the same four units, hi of its first and second 8
+// values, then lo of them.  As a BF16 K-major operand of 64 elements per
+// row, the slot then holds the K steps hi(k 0-15), lo(k 0-15), hi(k 16-31),
+// lo(k 16-31).  Every thread rewrites only the bytes it read.
+__device__ __forceinline__ void split_a_inplace(uint8_t *slot, int tid) {
+    const int row = tid >> 1, half = tid & 1, sw = row & 7;
+    uint8_t *rowp = slot + row * 128;
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 v = *reinterpret_cast<const float4 *>(rowp + (((4 * half + i) ^ sw) << 4));
+        x[4 * i] = v.x;
+        x[4 * i + 1] = v.y;
+        x[4 * i + 2] = v.z;
+        x[4 * i + 3] = v.w;
+    }
+    uint32_t hw[8], lw[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(x[2 * q] - hf.x, x[2 * q + 1] - hf.y);
+        hw[q] = *reinterpret_cast<const uint32_t *>(&h);
+        lw[q] = *reinterpret_cast<const uint32_t *>(&lo);
+    }
+    *reinterpret_cast<uint4 *>(rowp + (((4 * half + 0) ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4 *>(rowp + (((4 * half + 1) ^ sw) << 4)) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+    *reinterpret_cast<uint4 *>(rowp + (((4 * half + 2) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    *reinterpret_cast<uint4 *>(rowp + (((4 * half + 3) ^ sw) << 4)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+}
+
+// Resident B: the producer threads load the whole B operand of a group
+// (its nct column tiles x nch K chunks, zeros past its columns and past K)
+// into pool slots bset[ct * nch + c], two chunks' global loads in flight
+// per thread at a time.
+template <int PREC>
+__device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int nch, int K, uint8_t *bset,
+                                          int bcol, int kqb) {
+    const int64_t ncols = int64_t(r.y) << d.nb;
+    const int nct = int((ncols + TBN - 1) / TBN);
+    const int N = 1 << d.nb;
+    int64_t cb[BRES_MAX_B];  // this thread's column in each column tile: element offset in B, or -1
+#pragma unroll
+    for (int ct = 0; ct < BRES_MAX_B; ++ct) {
+        const int64_t gc = int64_t(ct) * TBN + bcol;
+        cb[ct] = (ct < nct && gc < ncols)
+                     ? int64_t(__ldg(d.instab + r.x + (gc >> d.nb)).y) * d.sB + ((gc & (N - 1)) << d.kb)
+                     : -1;
+    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int ct = 0; ct < BRES_MAX_B; ++ct) {
+        if (ct >= nct) break;
+        const int64_t bb = cb[ct];
+        for (int c = 0; c < nch; c += 2) {
+            float4 p[2][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int k = (c + i) * TBK + 4 * kqb;
+                const bool v = bb >= 0 && c + i < nch && k + 3 < K;
+                const float4 *src = reinterpret_cast<const float4 *>(v ? d.B + bb + k : d.B);
+                p[i][0] = v ? __ldg(src) : z;
+                p[i][1] = v ? __ldg(src + 1) : z;
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+                if (c + i < nch) expand_b<PREC>(bset + (ct * nch + c + i) * (TBNR * TBKR * 4), bcol, kqb, p[i][0], p[i][1]);
+        }
+    }
+}
+
+template <int PREC, bool BRES>
 __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 warps on a sub-partition)
-    k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA) {
-    using C = Cfg<PREC>;
+    k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA, int nrs) {
+    // nrs: A stages in use (C::RST streaming B; resident B: the pool slots
+    // left after the largest group's B)
+    using C = Cfg<PREC, BRES>;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // 1024-byte alignment: the swizzled A slots are whole 8-row atoms
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     Ctrl &X = *reinterpret_cast<Ctrl *>(sm + C::OFF_CTRL);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_tiles = d.n_ctab * mtiles;
     const int N = 1 << d.nb;
     const int K = 1 << d.kb;
     const int nch = (K + TBK - 1) / TBK;
-    const int64_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    // streaming B: tiles blockIdx.x, + gridDim.x, ...; resident B: one
+    // contiguous range of tiles per CTA (a group's tiles run back to back)
+    const int64_t t_begin = BRES ? n_tiles * blockIdx.x / gridDim.x : int64_t(blockIdx.x);
+    const int64_t my_tiles = BRES ? n_tiles * (blockIdx.x + 1) / gridDim.x - t_begin
+                                  : (blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
     const int64_t total_chunks = my_tiles * nch;
 
     if (warp == MMA_WARP) {
@@ -359,8 +492,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         }
         for (int s = 0; s < C::RST; ++s) {
             mbar_init(&X.rfull[s], 1);
-            mbar_init(&X.rempty[s], PREC == 2 ? NPROD : 1);
+            mbar_init(&X.rempty[s], 1);
+            mbar_init(&X.afull[s], NPROD);
         }
+        mbar_init(&X.bfull, NPROD);
+        mbar_init(&X.bempty, 1);
         for (int a = 0; a < 2; ++a) {
             mbar_init(&X.tfull[a], 1);
             mbar_init(&X.tempty[a], NEPI);
@@ -420,7 +556,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         atomicExch(err, 1);
         *abort_flag = 1;
     };
-    auto tile_of = [&](int64_t l) { return int64_t(blockIdx.x) + l * gridDim.x; };
+    auto tile_of = [&](int64_t l) { return BRES ? t_begin + l : t_begin + l * gridDim.x; };
 
     if (warp >= MMA_WARP) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(CTL_REGS));
     if (warp == TMA_WARP) {
@@ -431,30 +567,80 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             bool ok = true;
             int64_t mt_n = 0;
             int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_n) : make_int4(0, 0, 0, 0);
+            int rs = 0;
+            uint32_t rph = 0;
             for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
                 const int4 r = r_n;  // the next tile's record is fetched one tile ahead
                 const int m0 = int(mt_n * TBM);
                 if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_n);
                 for (int c = 0; c < nch; ++c, ++issued) {
-                    const int rs = int(issued % C::RST);
-                    if (!mbar_wait(&X.rempty[rs], (uint32_t(issued / C::RST) & 1u) ^ 1u)) {
+                    if (!mbar_wait(&X.rempty[rs], rph ^ 1u)) {
                         ok = false;
                         break;
                     }
                     mbar_expect_tx(&X.rfull[rs], C::SLOT_RAW);
-                    tma_load_4d(smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), &tmA, 0, m0, 8 * c, r.z, &X.rfull[rs]);
+                    tma_load_3d(smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), &tmA, TBKR * c, m0, r.z, &X.rfull[rs]);
+                    if (++rs == nrs) {
+                        rs = 0;
+                        rph ^= 1u;
+                    }
                 }
             }
             if (!ok) give_up();
             // loads still in flight land before the CTA leaves (bounded)
-            for (int64_t j = issued > C::RST ? issued - C::RST : 0; j < issued; ++j)
-                mbar_wait(&X.rfull[j % C::RST], uint32_t(j / C::RST) & 1u);
+            for (int64_t j = issued > nrs ? issued - nrs : 0; j < issued; ++j)
+                mbar_wait(&X.rfull[j % nrs], uint32_t(j / nrs) & 1u);
         }
         __syncwarp();
     } else if (warp < NPROD / 32) {
         // ------------------------------------------------------------ B loads, A split
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(PROD_REGS));
         const int bcol = tid & 63, kqb = tid >> 6;
+      if constexpr (BRES) {
+        // resident B: at each group switch (once the MMAs stopped reading
+        // the previous group's B) load the group's B into the pool; BF16x3
+        // also splits every A chunk in place
+        int rs = 0;
+        uint32_t rph = 0, u = 0;
+        int64_t gprev = -1, mt_unused, g_n = 0;
+        int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_unused, &g_n) : make_int4(0, 0, 0, 0);
+        for (int64_t l = 0; l < my_tiles && !*abort_flag; ++l) {
+            const int4 r = r_n;
+            const int64_t g = g_n;
+            if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_unused, &g_n);
+            if (g != gprev) {
+                if (u > 0 && !mbar_wait(&X.bempty, (u - 1) & 1u)) {
+                    give_up();
+                    break;
+                }
+                load_bset<PREC>(d, r, nch, K, sm + C::OFF_RAW + nrs * C::SLOT_RAW, bcol, kqb);
+                proxy_fence();
+                mbar_arrive(&X.bfull);
+                ++u;
+                gprev = g;
+            }
+            if (PREC == 2) {
+                bool ok = true;
+                for (int c = 0; c < nch; ++c) {
+                    if (!mbar_wait(&X.rfull[rs], rph)) {
+                        ok = false;
+                        break;
+                    }
+                    split_a_inplace(sm + C::OFF_RAW + rs * C::SLOT_RAW, tid);
+                    proxy_fence();
+                    mbar_arrive(&X.afull[rs]);
+                    if (++rs == nrs) {
+                        rs = 0;
+                        rph ^= 1u;
+                    }
+                }
+                if (!ok) {
+                    give_up();
+                    break;
+                }
+            }
+        }
+      } else {
         int64_t bbase[2] = {-1, -1};
         int64_t issued = 0;
         // metadata pipeline: records two tiles ahead, B instance one tile ahead
@@ -508,129 +694,127 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 give_up();
                 break;
             }
-            if (PREC == 2) {
-                // A: split the raw FP32 chunk into hi/lo (rows 8 at a time,
-                // 16-byte k columns p and p+1 of the raw chunk per item)
+            if (PREC == 2) {  // A: split in place
                 const int rs = int(gch % C::RST);
                 if (!mbar_wait(&X.rfull[rs], uint32_t(gch / C::RST) & 1u)) {
                     give_up();
                     break;
                 }
-                const uint8_t *raw = sm + C::OFF_RAW + rs * C::SLOT_RAW;
-                uint8_t *bh = sm + C::OFF_A + slot * C::SLOT_A, *bl = bh + TBM * TBKR * 2;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int item = tid + NPROD * j;  // 0..511
-                    const int row = item & (TBM - 1), p = item >> 7;
-                    const float4 v0 = *reinterpret_cast<const float4 *>(raw + (2 * p) * (TBM * 16) + row * 16);
-                    const float4 v1 = *reinterpret_cast<const float4 *>(raw + (2 * p + 1) * (TBM * 16) + row * 16);
-                    const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                    __align__(16) __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        hi[q] = __float2bfloat16_rn(x[q]);
-                        lo[q] = __float2bfloat16_rn(x[q] - __bfloat162float(hi[q]));
-                    }
-                    *reinterpret_cast<uint4 *>(bh + kmaj_off(row, 8 * p, 2)) = *reinterpret_cast<uint4 *>(hi);
-                    *reinterpret_cast<uint4 *>(bl + kmaj_off(row, 8 * p, 2)) = *reinterpret_cast<uint4 *>(lo);
-                }
-                mbar_arrive(&X.rempty[rs]);
+                split_a_inplace(sm + C::OFF_RAW + rs * C::SLOT_RAW, tid);
             }
             cp_async_wait(int(issued - gch - 1));
             // B: expand this thread's prefetched piece into the MMA layout
-            const uint8_t *braw = sm + C::OFF_BRAW + int(gch % C::BRST) * C::SLOT_BRAW + tid * 32;
             {
-                const float4 p0 = *reinterpret_cast<const float4 *>(braw);
-                const float4 p1 = *reinterpret_cast<const float4 *>(braw + 16);
-                const float2 t4[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
-                                      make_float2(p1.z, p1.w)};
-                const float r0[8] = {t4[0].x, -t4[0].y, t4[1].x, -t4[1].y, t4[2].x, -t4[2].y, t4[3].x, -t4[3].y};
-                const float r1[8] = {t4[0].y, t4[0].x, t4[1].y, t4[1].x, t4[2].y, t4[2].x, t4[3].y, t4[3].x};
-                uint8_t *base = sm + C::OFF_B + slot * C::SLOT_B;
-                if (PREC == 1) {
-                    *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol, 8 * kqb, 4)) = make_float4(r0[0], r0[1], r0[2], r0[3]);
-                    *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol, 8 * kqb + 4, 4)) = make_float4(r0[4], r0[5], r0[6], r0[7]);
-                    *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb, 4)) = make_float4(r1[0], r1[1], r1[2], r1[3]);
-                    *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb + 4, 4)) = make_float4(r1[4], r1[5], r1[6], r1[7]);
-                } else {
-                    __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        h0[q] = __float2bfloat16_rn(r0[q]);
-                        l0[q] = __float2bfloat16_rn(r0[q] - __bfloat162float(h0[q]));
-                        h1[q] = __float2bfloat16_rn(r1[q]);
-                        l1[q] = __float2bfloat16_rn(r1[q] - __bfloat162float(h1[q]));
-                    }
-                    uint8_t *blo = base + TBNR * TBKR * 2;
-                    *reinterpret_cast<uint4 *>(base + kmaj_off(2 * bcol, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(h0);
-                    *reinterpret_cast<uint4 *>(blo + kmaj_off(2 * bcol, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(l0);
-                    *reinterpret_cast<uint4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(h1);
-                    *reinterpret_cast<uint4 *>(blo + kmaj_off(2 * bcol + 1, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(l1);
-                }
+                const uint8_t *braw = sm + C::OFF_BRAW + int(gch % C::BRST) * C::SLOT_BRAW + tid * 32;
+                expand_b<PREC>(sm + C::OFF_B + slot * C::SLOT_B, bcol, kqb, *reinterpret_cast<const float4 *>(braw),
+                               *reinterpret_cast<const float4 *>(braw + 16));
             }
             proxy_fence();
             mbar_arrive(&X.full[slot]);
         }
         cp_async_wait(0);
+      }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t LBO = TBM * 16, SBO = 128;
-            int64_t gch = 0;
-            for (int64_t l = 0; l < my_tiles && !*abort_flag; ++l) {
-                const int acc = int(l & 1);
-                if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> 1) & 1u) ^ 1u)) {
-                    give_up();
-                    break;
+            // the MMAs of one K chunk: A slot a0 (swizzled rows), B slot b0
+            auto issue_chunk = [&](uint32_t dtm, uint32_t a0, uint32_t b0, bool first) {
+                if (PREC == 1) {
+                    const uint32_t id = idesc(2u);
+#pragma unroll
+                    for (int j = 0; j < TBKR / 8; ++j) {  // K step: 8 tf32 = 32 bytes of an A row
+                        const uint32_t off = uint32_t(2 * j) * LBO;
+                        mma_tf32(dtm, sdesc_sw128(a0 + 32 * j), sdesc(b0 + off, LBO, SBO), id, (!first || j > 0) ? 1u : 0u);
+                    }
+                } else {
+                    // A: hi and lo K steps alternate in the slot (32 bytes
+                    // each, swizzled rows); B: hi plane, lo plane 8 KB on
+                    const uint32_t id = idesc(1u);
+                    const uint32_t bl = b0 + TBNR * TBKR * 2;
+#pragma unroll
+                    for (int j = 0; j < TBKR / 16; ++j) {
+                        const uint32_t off = uint32_t(2 * j) * LBO;
+                        const uint64_t ah = sdesc_sw128(a0 + 64 * j), al = sdesc_sw128(a0 + 64 * j + 32);
+                        mma_f16(dtm, ah, sdesc(b0 + off, LBO, SBO), id, (!first || j > 0) ? 1u : 0u);
+                        mma_f16(dtm, ah, sdesc(bl + off, LBO, SBO), id, 1u);
+                        mma_f16(dtm, al, sdesc(b0 + off, LBO, SBO), id, 1u);
+                    }
                 }
-                tc_fence_after();
-                const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
-                bool ok = true;
-                for (int c = 0; c < nch; ++c, ++gch) {
-                    const int slot = int(gch % C::ST);
-                    const int rs = int(gch % C::RST);
-                    if (!mbar_wait(&X.full[slot], uint32_t(gch / C::ST) & 1u)) {
+            };
+            bool ok = true;
+            if constexpr (BRES) {
+                int rs = 0;
+                uint32_t rph = 0, u = 0;
+                int64_t gprev = -1, mt_unused, g_n = 0;
+                int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_unused, &g_n) : make_int4(0, 0, 0, 0);
+                for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
+                    const int4 r = r_n;
+                    const int64_t g = g_n;
+                    if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_unused, &g_n);
+                    const int acc = int(l & 1);
+                    if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> 1) & 1u) ^ 1u)) {
                         ok = false;
                         break;
                     }
-                    if (PREC == 1 && !mbar_wait(&X.rfull[rs], uint32_t(gch / C::RST) & 1u)) {
+                    if (g != gprev) {  // new group: release the old B once its MMAs are done, wait for the new
+                        if (u > 0) mma_commit(&X.bempty);
+                        if (!mbar_wait(&X.bfull, u & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        ++u;
+                        gprev = g;
+                    }
+                    tc_fence_after();
+                    const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
+                    const uint32_t bset = smem_u32(sm + C::OFF_RAW + (nrs + (r.w / TBN) * nch) * C::SLOT_RAW);
+                    for (int c = 0; c < nch; ++c) {
+                        if (!mbar_wait(PREC == 2 ? &X.afull[rs] : &X.rfull[rs], rph)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        issue_chunk(dtm, smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), bset + c * C::SLOT_RAW, c == 0);
+                        mma_commit(&X.rempty[rs]);
+                        if (++rs == nrs) {
+                            rs = 0;
+                            rph ^= 1u;
+                        }
+                    }
+                    if (ok) mma_commit(&X.tfull[acc]);
+                }
+            } else {
+                int64_t gch = 0;
+                for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
+                    const int acc = int(l & 1);
+                    if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> 1) & 1u) ^ 1u)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    if (PREC == 1) {
-                        const uint32_t id = idesc(2u);
-                        const uint32_t a0 = smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW);
-                        const uint32_t b0 = smem_u32(sm + C::OFF_B + slot * C::SLOT_B);
-#pragma unroll
-                        for (int j = 0; j < TBKR / 8; ++j) {
-                            const uint32_t off = uint32_t(2 * j) * LBO;
-                            mma_tf32(dtm, sdesc(a0 + off, LBO, SBO), sdesc(b0 + off, LBO, SBO), id,
-                                     (c > 0 || j > 0) ? 1u : 0u);
+                    const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
+                    for (int c = 0; c < nch; ++c, ++gch) {
+                        const int slot = int(gch % C::ST);
+                        const int rs = int(gch % C::RST);
+                        if (!mbar_wait(&X.full[slot], uint32_t(gch / C::ST) & 1u)) {
+                            ok = false;
+                            break;
                         }
+                        if (PREC == 1 && !mbar_wait(&X.rfull[rs], uint32_t(gch / C::RST) & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        issue_chunk(dtm, smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW),
+                                    smem_u32(sm + C::OFF_B + slot * C::SLOT_B), c == 0);
                         mma_commit(&X.empty[slot]);
                         mma_commit(&X.rempty[rs]);
-                    } else {
-                        const uint32_t id = idesc(1u);
-                        const uint32_t ah = smem_u32(sm + C::OFF_A + slot * C::SLOT_A), al = ah + TBM * TBKR * 2;
-                        const uint32_t bh = smem_u32(sm + C::OFF_B + slot * C::SLOT_B), bl = bh + TBNR * TBKR * 2;
-#pragma unroll
-                        for (int j = 0; j < TBKR / 16; ++j) {
-                            const uint32_t off = uint32_t(2 * j) * LBO;
-                            mma_f16(dtm, sdesc(ah + off, LBO, SBO), sdesc(bh + off, LBO, SBO), id,
-                                    (c > 0 || j > 0) ? 1u : 0u);
-                            mma_f16(dtm, sdesc(ah + off, LBO, SBO), sdesc(bl + off, LBO, SBO), id, 1u);
-                            mma_f16(dtm, sdesc(al + off, LBO, SBO), sdesc(bh + off, LBO, SBO), id, 1u);
-                        }
-                        mma_commit(&X.empty[slot]);
                     }
+                    if (ok) mma_commit(&X.tfull[acc]);
                 }
-                if (!ok) {
-                    give_up();
-                    break;
-                }
-                mma_commit(&X.tfull[acc]);
             }
+            if (!ok) give_up();
         }
         __syncwarp();
     } else if (warp == META_WARP) {
@@ -896,6 +1080,15 @@ bool gemm_tc_supports(const StepDesc &d) {
     return d.kb >= 3 && d.mb >= 6 && d.mb <= 30 && d.kb <= 24;
 }
 
+int tc_resident_b_chunks(const StepDesc &d) {
+    // B chunks of the largest group (its 64-column tiles x K chunks); 0 when
+    // they do not fit the resident-B pool
+    const int64_t nch = ((int64_t(1) << d.kb) + TBK - 1) / TBK;
+    const int64_t nct = ((int64_t(d.max_group) << d.nb) + TBN - 1) / TBN;
+    const int64_t n = nch * nct;
+    return n >= 1 && n <= BRES_MAX_B ? int(n) : 0;
+}
+
 namespace {
 int g_num_sms = 0;
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -914,25 +1107,33 @@ cudaError_t init_kernels() {
         if (e != cudaSuccess) return e;
         if (q != cudaDriverEntryPointSuccess || !g_encode) return cudaErrorNotSupported;
     }
-    e = cudaFuncSetAttribute(k_step_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
+    e = cudaFuncSetAttribute(k_step_gemm_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<1, false>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_step_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2>());
+    e = cudaFuncSetAttribute(k_step_gemm_tc<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<2, false>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_step_gemm_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<1, true>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_step_gemm_tc<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<2, true>());
 }
 
-// The A operand of a step as a 4-D tensor for TMA: (4 floats = one 16-byte
-// k column of a row, rows m, 16-byte k columns, instances).  The box
-// (4, 128, 8, 1) lands in shared memory as [k column][row][16 bytes], the
-// K-major core-matrix order the MMA descriptors use.  Rows past M and k past
-// K read as zeros.
+// The A operand of a step as a 3-D tensor for TMA: (real k = 2K floats of a
+// row, rows m, instances).  The box (32, 128, 1) lands in shared memory as
+// 128 rows of 128 bytes with the 128-byte swizzle, the K-major layout the
+// MMA descriptors use; each load is 128 row segments of 128 contiguous
+// bytes.  Rows past M and k past K read as zeros.
 cudaError_t make_a_map(const StepDesc &d, int64_t n_inst_a, CUtensorMap *map) {
     if (!g_encode) return cudaErrorNotReady;
     const cuuint64_t K = cuuint64_t(1) << d.kb;
-    const cuuint64_t dims[4] = {4, cuuint64_t(1) << d.mb, K / 2, cuuint64_t(n_inst_a)};
-    const cuuint64_t strides[3] = {K * 8, 16, cuuint64_t(d.sA) * 8};
-    const cuuint32_t box[4] = {4, TBM, TBKR / 4, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2 *>(d.A), dims, strides, box,
-                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const cuuint64_t dims[3] = {2 * K, cuuint64_t(1) << d.mb, cuuint64_t(n_inst_a)};
+    const cuuint64_t strides[2] = {K * 8, cuuint64_t(d.sA) * 8};
+    const cuuint32_t box[3] = {TBKR, TBM, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(d.A), dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -946,10 +1147,20 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
     const int64_t tiles = d.n_ctab * mtiles;
     if (tiles <= 0) return cudaSuccess;
     const int64_t grid = tiles < g_num_sms ? tiles : g_num_sms;
-    if (precision == 1)
-        k_step_gemm_tc<1><<<dim3((unsigned)grid), NTHREADS, smem_bytes<1>(), s>>>(d, mtiles, err, *a_map);
-    else
-        k_step_gemm_tc<2><<<dim3((unsigned)grid), NTHREADS, smem_bytes<2>(), s>>>(d, mtiles, err, *a_map);
+    const dim3 g((unsigned)grid);
+    // schedule 0 keeps each group's B resident when it fits the pool
+    const int nbset = tc_resident_b_chunks(d);
+    if (d.sched == 0 && nbset > 0) {
+        const int nrs = std::min(Cfg<2, true>::RST, Cfg<2, true>::NSLOT - nbset);
+        if (precision == 1)
+            k_step_gemm_tc<1, true><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+        else
+            k_step_gemm_tc<2, true><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+    } else if (precision == 1) {
+        k_step_gemm_tc<1, false><<<g, NTHREADS, smem_bytes<1, false>(), s>>>(d, mtiles, err, *a_map, Cfg<1, false>::RST);
+    } else {
+        k_step_gemm_tc<2, false><<<g, NTHREADS, smem_bytes<2, false>(), s>>>(d, mtiles, err, *a_map, Cfg<2, false>::RST);
+    }
     return cudaGetLastError();
 }
 

@@ -70,6 +70,9 @@ cudaError_t launch_xeb(const double *amps, int64_t k, double scale, double *out,
 // Tensor-core path (gemm_tc.cu).  precision: 1 = TF32, 2 = BF16x3.
 // Returns cudaErrorNotSupported for shapes it does not take.
 bool gemm_tc_supports(const StepDesc &d);
+// Schedule 0 of a tensor-core step keeps each group's B resident in shared
+// memory when the largest group's B fits: its chunk count, else 0.
+int tc_resident_b_chunks(const StepDesc &d);
 // One-time per-device setup (function attributes, SM count); call outside
 // any stream capture.
 cudaError_t init_kernels();

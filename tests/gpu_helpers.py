@@ -12,10 +12,12 @@ def require_cuda():
     return torch, tn
 
 
-def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, force_kernel=None, **opts):
+def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, force_kernel=None, force_config=None,
+             **opts):
     """Amplitudes (complex128, input order) summed over every slice batch.
     force_kernel: a function step_info -> kernel family (or None) applied to
-    every step before the run."""
+    every step before the run; force_config likewise for the step's
+    configuration (family x schedule)."""
     torch, tn = require_cuda()
     p = tn.Plan(circ, bits, ssa, sliced, **opts)
     if force_kernel is not None:
@@ -23,6 +25,11 @@ def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, force_k
             k = force_kernel(st)
             if k is not None:
                 p.tn_plan_set_kernel(s, k)
+    if force_config is not None:
+        for s, st in enumerate(p.tn_plan_steps()):
+            c = force_config(st)
+            if c is not None:
+                p.tn_plan_set_config(s, c)
     ws = torch.empty(max(p.info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
     p.tn_plan_bind(ws, stream=torch.cuda.current_stream())
     amps = torch.zeros(2 * len(bits), dtype=torch.float64, device="cuda")

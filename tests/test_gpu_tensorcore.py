@@ -73,6 +73,20 @@ def test_forced_gemm_path_matches_state_vector(case, prec, request):
     assert err <= _tol(prec), err
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_streaming_b_schedule_matches_state_vector(case20_shapes, prec):
+    # schedule 1 (configuration 3) streams B chunk by chunk next to A;
+    # schedule 0 keeps a group's whole B in shared memory where it fits:
+    # both forms of the tensor-core kernel against the state vector
+    c, bits, ssa, sl, ref = case20_shapes
+    got, p = run_plan(c, bits, ssa, sl, precision=prec, force_kernel=_gemm_everywhere,
+                      force_config=lambda st: 3)
+    assert sum(1 for k in p.tn_plan_step_times()[1] if k == 2) >= 5
+    err = rel_l2(got, ref)
+    print(f"streaming-B tensor-core 20q {prec}: rel-L2 {err:.3e}")
+    assert err <= _tol(prec), err
+
+
 def _row_where_it_fits(st):
     return 0 if (st["nb"] <= 4 and st["kb"] + st["nb"] <= 8) else 1
 
