@@ -420,20 +420,28 @@ __device__ __forceinline__ void split_a_inplace(uint8_t *slot, int tid) {
 // Resident B: the producer threads load the whole B operand of a group
 // (its nct column tiles x nch K chunks, zeros past its columns and past K)
 // into pool slots bset[ct * nch + c], two chunks' global loads in flight
-// per thread at a time.
+// per thread at a time.  Each column is multiplied by its power-of-two
+// rescale 2^-(ea + eb) on the way (exact), so the epilogue stores the
+// accumulators as they are.
 template <int PREC>
 __device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int nch, int K, uint8_t *bset,
                                           int bcol, int kqb) {
     const int64_t ncols = int64_t(r.y) << d.nb;
     const int nct = int((ncols + TBN - 1) / TBN);
     const int N = 1 << d.nb;
+    const int ea = d.mxA ? exp_of(__ldg(d.mxA + r.z)) : 0;
     int64_t cb[BRES_MAX_B];  // this thread's column in each column tile: element offset in B, or -1
+    float sc[BRES_MAX_B];    // its power-of-two rescale 2^-(ea + eb), applied here instead of in the epilogue
 #pragma unroll
     for (int ct = 0; ct < BRES_MAX_B; ++ct) {
         const int64_t gc = int64_t(ct) * TBN + bcol;
-        cb[ct] = (ct < nct && gc < ncols)
-                     ? int64_t(__ldg(d.instab + r.x + (gc >> d.nb)).y) * d.sB + ((gc & (N - 1)) << d.kb)
-                     : -1;
+        cb[ct] = -1;
+        sc[ct] = 1.f;
+        if (ct < nct && gc < ncols) {
+            const int ib = __ldg(d.instab + r.x + (gc >> d.nb)).y;
+            cb[ct] = int64_t(ib) * d.sB + ((gc & (N - 1)) << d.kb);
+            sc[ct] = pow2f(-(ea + (d.mxB ? exp_of(__ldg(d.mxB + ib)) : 0)));
+        }
     }
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -450,10 +458,37 @@ __device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int 
                 p[i][0] = v ? __ldg(src) : z;
                 p[i][1] = v ? __ldg(src + 1) : z;
             }
+            const float s = sc[ct];
 #pragma unroll
             for (int i = 0; i < 2; ++i)
-                if (c + i < nch) expand_b<PREC>(bset + (ct * nch + c + i) * (TBNR * TBKR * 4), bcol, kqb, p[i][0], p[i][1]);
+                if (c + i < nch)
+                    expand_b<PREC>(bset + (ct * nch + c + i) * (TBNR * TBKR * 4), bcol, kqb,
+                                   make_float4(p[i][0].x * s, p[i][0].y * s, p[i][0].z * s, p[i][0].w * s),
+                                   make_float4(p[i][1].x * s, p[i][1].y * s, p[i][1].z * s, p[i][1].w * s));
         }
+    }
+}
+
+// Epilogue max-|component| of one pass (8 complex columns; v: 16
+// accumulator values of this lane's row) over runs of RUN columns (one
+// instance each): folded in registers, one warp reduction per run, scaled
+// by the run's power of two (exact; SCALED: the values carry it already) and
+// merged into the slot's entry at the run's first column.  Columns past the
+// tile's valid ones hold zeros (their B columns are zero) and merge nothing.
+template <int RUN, bool SCALED>
+__device__ __forceinline__ void fold_max8(const float *v, EpiMeta &em, int c0, int lane) {
+    uint32_t a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = __float_as_uint(fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
+#pragma unroll
+    for (int s = 1; s < RUN; s <<= 1)
+#pragma unroll
+        for (int j = 0; j < 8; j += 2 * s) a[j] = max(a[j], a[j + s]);
+#pragma unroll
+    for (int j = 0; j < 8; j += RUN) {
+        const uint32_t r = __reduce_max_sync(0xffffffffu, a[j]);
+        if (lane == 0 && r)
+            atomicMax(&em.mx[c0 + j], SCALED ? r : __float_as_uint(__uint_as_float(r) * em.sc[c0 + j]));
     }
 }
 
@@ -969,7 +1004,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 break;
             }
             tc_fence_after();
-            const EpiMeta &em = X.epi[slot];
+            EpiMeta &em = X.epi[slot];
             const int ncv = em.ncv;
             const int nh = ncv > TBN / 2 ? 2 : 1;
             for (int h = 0; h < nh; ++h) {
@@ -1000,30 +1035,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     if (!act) continue;
                     const int cp = c0 + 8 * p;  // first column of this pass
                     if (d.mxC) {
-                        // max-|component| of each instance's columns: runs of
-                        // min(N, 8) columns folded in registers, then one warp
-                        // reduction per run, scaled by the run's power of two
-                        // (exact) and merged in the slot (shared memory); the
-                        // metadata warp carries the slot's maxima to global
-                        // memory when it recycles the slot
-                        const int run = N < 8 ? N : 8;
-                        uint32_t a[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) a[j] = __float_as_uint(fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
-#pragma unroll
-                        for (int s = 1; s < 8; s <<= 1)
-                            if (s < run) {
-#pragma unroll
-                                for (int j = 0; j < 8; j += 2 * s) a[j] = max(a[j], a[j + s]);
-                            }
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if ((j & (run - 1)) == 0 && cp + j < ncv) {
-                                const uint32_t r = __reduce_max_sync(0xffffffffu, a[j]);
-                                if (lane == 0 && r)
-                                    atomicMax(const_cast<uint32_t *>(&em.mx[cp + j]),
-                                              __float_as_uint(__uint_as_float(r) * em.sc[cp + j]));
-                            }
+                        switch (N < 8 ? N : 8) {
+                            case 1: fold_max8<1, BRES>(v, em, cp, lane); break;
+                            case 2: fold_max8<2, BRES>(v, em, cp, lane); break;
+                            case 4: fold_max8<4, BRES>(v, em, cp, lane); break;
+                            default: fold_max8<8, BRES>(v, em, cp, lane); break;
+                        }
                     }
                     // scale and stage in destination order
 #pragma unroll
@@ -1037,8 +1054,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
                                 if ((jj >> j) & 1) a ^= acol[j];
+                            // resident B carries the rescale already
+                            const float s = BRES ? 1.f : scq[t];
                             *reinterpret_cast<float2 *>(wst + a) =
-                                make_float2(v[2 * (4 * q + t)] * scq[t], v[2 * (4 * q + t) + 1] * scq[t]);
+                                make_float2(v[2 * (4 * q + t)] * s, v[2 * (4 * q + t) + 1] * s);
                         }
                     }
                 }
@@ -1046,18 +1065,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 const int ncw = ncv - c0;  // valid columns of this block
                 __syncwarp();
                 const int64_t wb = em.base + qoff + mp.hoff[h * 2 + sub] + offL;
+                if (pair && ncw >= 16) {  // whole block valid, 16-byte runs: straight-line stores
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    // compressed elements 2u, 2u + 1 with u = lane + 32 i
-                    const float4 val = *reinterpret_cast<const float4 *>(wst + (alane ^ (stage_swz(32 * i) << 4)));
-                    const int c = colL + mp.colI[i];
-                    const bool v0 = c < ncw, v1 = c + dcol0 < ncw;
-                    float2 *dst = d.C + (wb + mp.offI[i]);
-                    if (pair && v0 && v1) {
-                        *reinterpret_cast<float4 *>(dst) = val;
-                    } else {
-                        if (v0) dst[0] = make_float2(val.x, val.y);
-                        if (v1) dst[doff0] = make_float2(val.z, val.w);
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 val = *reinterpret_cast<const float4 *>(wst + (alane ^ (stage_swz(32 * i) << 4)));
+                        *reinterpret_cast<float4 *>(d.C + (wb + mp.offI[i])) = val;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        // compressed elements 2u, 2u + 1 with u = lane + 32 i
+                        const float4 val = *reinterpret_cast<const float4 *>(wst + (alane ^ (stage_swz(32 * i) << 4)));
+                        const int c = colL + mp.colI[i];
+                        const bool v0 = c < ncw, v1 = c + dcol0 < ncw;
+                        float2 *dst = d.C + (wb + mp.offI[i]);
+                        if (pair && v0 && v1) {
+                            *reinterpret_cast<float4 *>(dst) = val;
+                        } else {
+                            if (v0) dst[0] = make_float2(val.x, val.y);
+                            if (v1) dst[doff0] = make_float2(val.z, val.w);
+                        }
                     }
                 }
                 __syncwarp();  // the staging area is rewritten by the next half
