@@ -215,6 +215,15 @@ int tn_plan_set_kernel(tn_plan_t plan, int32_t step, int32_t kernel);
  * TN_EINVAL for a configuration the step's shape does not allow. */
 int tn_plan_set_config(tn_plan_t plan, int32_t step, int32_t config);
 
+/* Tensor-core form of the grouped GEMM.  enable = 1 (the default): where B
+ * fits in shared memory (configuration 2: a group's whole B, configuration
+ * 3: one 64-column tile's, at most 8 K chunks of 16), each CTA takes a
+ * contiguous range of tiles and keeps B resident, streaming only A;
+ * elsewhere, and for every step with enable = 0, B is gathered chunk by
+ * chunk next to A.  Both forms compute the same values; the switch exists
+ * to measure and test the streaming form.  TN_EINVAL for a null plan. */
+int tn_plan_set_tc_resident_b(tn_plan_t plan, int32_t enable);
+
 /* Configuration each step will run with (the plan's choice where none was
  * set); n entries. */
 int tn_plan_get_configs(tn_plan_t plan, int32_t *config, int32_t n);

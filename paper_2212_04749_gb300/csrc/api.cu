@@ -43,6 +43,7 @@ struct PlanObj {
     std::vector<AMap> amap;           // per step: TMA descriptor of A (tensor-core steps)
     std::vector<tnk::ChainDesc> chain_desc;  // per fused chain
     int32_t *err_flag = nullptr;      // device word for bounded waits
+    bool tc_resident_b = true;        // tensor-core GEMM keeps B in shared memory where it fits
     bool profile = false;
     std::vector<cudaEvent_t> ev;          // pool, two per profiled launch
     std::vector<int> ev_step;             // step of each recorded pair
@@ -206,6 +207,7 @@ int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
     const int cfg = effective_config(o, s);
     tnk::StepDesc d = o->desc[s];
     d.sched = cfg & 1;
+    d.tc_resident_b = o->tc_resident_b ? 1 : 0;
     cudaError_t e;
     int fam;
     if (cfg < 2) {
@@ -638,6 +640,14 @@ int tn_plan_set_config(tn_plan_t plan, int32_t step, int32_t config) {
         return set_err(TN_EINVAL, "tn_plan_set_config: per-row kernel needs N <= 16 and K*N <= 256");
     o->config_override.resize(P.steps.size(), -1);
     o->config_override[step] = config;
+    o->drop_graphs();
+    return TN_OK;
+}
+
+int tn_plan_set_tc_resident_b(tn_plan_t plan, int32_t enable) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_set_tc_resident_b: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    o->tc_resident_b = enable != 0;
     o->drop_graphs();
     return TN_OK;
 }

@@ -334,7 +334,8 @@ __device__ __forceinline__ int4 tile_decode(const StepDesc &d, int64_t T, int64_
     const int64_t e0 = T / mtiles;  // some column tile of T's group
     int4 r = __ldg(d.trec + e0);
     const int64_t f = e0 - r.w / TBN;  // the group's first column tile
-    if (group) *group = f;
+    // resident-B unit: the group (schedule 0) or the column tile (schedule 1)
+    if (group) *group = d.sched != 0 ? e0 : f;
     if (d.sched != 0) {  // schedule 1: the row tiles of one column tile run consecutively
         mt = T - e0 * mtiles;
         return r;
@@ -417,24 +418,26 @@ __device__ __forceinline__ void split_a_inplace(uint8_t *slot, int tid) {
     *reinterpret_cast<uint4 *>(rowp + (((4 * half + 3) ^ sw) << 4)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
 }
 
-// Resident B: the producer threads load the whole B operand of a group
-// (its nct column tiles x nch K chunks, zeros past its columns and past K)
-// into pool slots bset[ct * nch + c], two chunks' global loads in flight
-// per thread at a time.  Each column is multiplied by its power-of-two
+// Resident B: the producer threads load the B operand of a group's column
+// tiles ct0 .. ct0 + nct - 1 (schedule 0: all of the group's; schedule 1:
+// the tile's own), nch K chunks each, zeros past its columns and past K,
+// into pool slots bset[(ct - ct0) * nch + c], two chunks' global loads in
+// flight per thread at a time.  Each column is multiplied by its power-of-two
 // rescale 2^-(ea + eb) on the way (exact), so the epilogue stores the
 // accumulators as they are.
 template <int PREC>
 __device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int nch, int K, uint8_t *bset,
                                           int bcol, int kqb) {
     const int64_t ncols = int64_t(r.y) << d.nb;
-    const int nct = int((ncols + TBN - 1) / TBN);
+    const int ct0 = d.sched != 0 ? r.w / TBN : 0;
+    const int nct = d.sched != 0 ? 1 : int((ncols + TBN - 1) / TBN);
     const int N = 1 << d.nb;
     const int ea = d.mxA ? exp_of(__ldg(d.mxA + r.z)) : 0;
     int64_t cb[BRES_MAX_B];  // this thread's column in each column tile: element offset in B, or -1
     float sc[BRES_MAX_B];    // its power-of-two rescale 2^-(ea + eb), applied here instead of in the epilogue
 #pragma unroll
     for (int ct = 0; ct < BRES_MAX_B; ++ct) {
-        const int64_t gc = int64_t(ct) * TBN + bcol;
+        const int64_t gc = int64_t(ct0 + ct) * TBN + bcol;
         cb[ct] = -1;
         sc[ct] = 1.f;
         if (ct < nct && gc < ncols) {
@@ -496,7 +499,7 @@ template <int PREC, bool BRES>
 __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 warps on a sub-partition)
     k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA, int nrs) {
     // nrs: A stages in use (C::RST streaming B; resident B: the pool slots
-    // left after the largest group's B)
+    // left after the largest resident B)
     using C = Cfg<PREC, BRES>;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment: the swizzled A slots are whole 8-row atoms
@@ -803,7 +806,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     }
                     tc_fence_after();
                     const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
-                    const uint32_t bset = smem_u32(sm + C::OFF_RAW + (nrs + (r.w / TBN) * nch) * C::SLOT_RAW);
+                    const int ctl = d.sched != 0 ? 0 : r.w / TBN;  // the tile's column tile within the resident B
+                    const uint32_t bset = smem_u32(sm + C::OFF_RAW + (nrs + ctl * nch) * C::SLOT_RAW);
                     for (int c = 0; c < nch; ++c) {
                         if (!mbar_wait(PREC == 2 ? &X.afull[rs] : &X.rfull[rs], rph)) {
                             ok = false;
@@ -1108,10 +1112,12 @@ bool gemm_tc_supports(const StepDesc &d) {
 }
 
 int tc_resident_b_chunks(const StepDesc &d) {
-    // B chunks of the largest group (its 64-column tiles x K chunks); 0 when
-    // they do not fit the resident-B pool
+    // B chunks resident at a time: schedule 0, the largest group's (its
+    // 64-column tiles x K chunks); schedule 1, one column tile's; 0 when they
+    // do not fit the resident-B pool
+    if (!d.tc_resident_b) return 0;
     const int64_t nch = ((int64_t(1) << d.kb) + TBK - 1) / TBK;
-    const int64_t nct = ((int64_t(d.max_group) << d.nb) + TBN - 1) / TBN;
+    const int64_t nct = d.sched != 0 ? 1 : ((int64_t(d.max_group) << d.nb) + TBN - 1) / TBN;
     const int64_t n = nch * nct;
     return n >= 1 && n <= BRES_MAX_B ? int(n) : 0;
 }
@@ -1175,9 +1181,9 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
     if (tiles <= 0) return cudaSuccess;
     const int64_t grid = tiles < g_num_sms ? tiles : g_num_sms;
     const dim3 g((unsigned)grid);
-    // schedule 0 keeps each group's B resident when it fits the pool
+    // B stays resident (per group, or per column tile) when it fits the pool
     const int nbset = tc_resident_b_chunks(d);
-    if (d.sched == 0 && nbset > 0) {
+    if (nbset > 0) {
         const int nrs = std::min(Cfg<2, true>::RST, Cfg<2, true>::NSLOT - nbset);
         if (precision == 1)
             k_step_gemm_tc<1, true><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs);

@@ -26,6 +26,7 @@ struct StepDesc {
     const int32_t *outA, *outB;   // [nOut]
     int32_t nOutA, nOutB, nOut;
     int32_t sched;                // schedule variant of the step's kernel (0 or 1; the autotuner's choice)
+    int32_t tc_resident_b;        // tensor cores: keep B resident in shared memory where it fits
     int64_t nInst;
     const int32_t *EA, *EB;       // accumulated exponents of the operands
     int32_t *EC;
@@ -70,8 +71,9 @@ cudaError_t launch_xeb(const double *amps, int64_t k, double scale, double *out,
 // Tensor-core path (gemm_tc.cu).  precision: 1 = TF32, 2 = BF16x3.
 // Returns cudaErrorNotSupported for shapes it does not take.
 bool gemm_tc_supports(const StepDesc &d);
-// Schedule 0 of a tensor-core step keeps each group's B resident in shared
-// memory when the largest group's B fits: its chunk count, else 0.
+// A tensor-core step keeps B resident in shared memory (schedule 0: a
+// group's whole B; schedule 1: one column tile's) when it fits: the chunk
+// count, else 0.
 int tc_resident_b_chunks(const StepDesc &d);
 // One-time per-device setup (function attributes, SM count); call outside
 // any stream capture.

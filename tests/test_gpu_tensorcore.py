@@ -13,7 +13,7 @@ K below one chunk); the 30-qubit workload checks all 4096 amplitudes.
 import numpy as np
 import pytest
 
-from gpu_helpers import rel_l2, run_plan
+from gpu_helpers import rel_l2, require_cuda, run_plan
 from oracle import sv
 from rqc import grid_layout, make_workload, network_structure, random_circuit
 from rqc.bitstrings import uniform_bitstrings
@@ -74,16 +74,30 @@ def test_forced_gemm_path_matches_state_vector(case, prec, request):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
-def test_streaming_b_schedule_matches_state_vector(case20_shapes, prec):
-    # schedule 1 (configuration 3) streams B chunk by chunk next to A;
-    # schedule 0 keeps a group's whole B in shared memory where it fits:
-    # both forms of the tensor-core kernel against the state vector
+@pytest.mark.parametrize("resident", [True, False])
+@pytest.mark.parametrize("config", [2, 3])
+def test_tensor_core_forms_match_state_vector(case20_shapes, prec, resident, config):
+    # configuration 2 walks a group's tiles row tile by row tile, 3 column
+    # tile by column tile; with resident B each CTA takes a contiguous range
+    # of tiles and keeps B in shared memory (a group's, or a column tile's),
+    # without it B is gathered chunk by chunk: all four forms against the
+    # state vector
+    torch, tn = require_cuda()
     c, bits, ssa, sl, ref = case20_shapes
-    got, p = run_plan(c, bits, ssa, sl, precision=prec, force_kernel=_gemm_everywhere,
-                      force_config=lambda st: 3)
+    p = tn.Plan(c, bits, ssa, sl)
+    for s, st in enumerate(p.tn_plan_steps()):
+        p.tn_plan_set_config(s, config)
+    p.tn_plan_set_tc_resident_b(resident)
+    ws = torch.empty(max(p.info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    p.tn_plan_bind(ws, stream=stream)
+    amps = torch.zeros(2 * len(bits), dtype=torch.float64, device="cuda")
+    p.tn_contract(amps, prec, stream=stream)
+    p.tn_plan_check(stream=stream)
+    torch.cuda.synchronize()
     assert sum(1 for k in p.tn_plan_step_times()[1] if k == 2) >= 5
-    err = rel_l2(got, ref)
-    print(f"streaming-B tensor-core 20q {prec}: rel-L2 {err:.3e}")
+    err = rel_l2(amps.cpu().numpy().view(np.complex128), ref)
+    print(f"tensor-core 20q config {config} resident-B {resident} {prec}: rel-L2 {err:.3e}")
     assert err <= _tol(prec), err
 
 
