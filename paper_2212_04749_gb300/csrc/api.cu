@@ -97,6 +97,7 @@ void build_descs(PlanObj *o) {
         d.nOutB = B.n_out;
         d.nOut = nd.n_out;
         d.nInst = nd.n_inst;
+        d.nInstB = B.n_inst;
         d.EA = at<const int32_t>(o, A.buf.E);
         d.EB = at<const int32_t>(o, B.buf.E);
         d.EC = at<int32_t>(o, nd.buf.E);

@@ -285,6 +285,7 @@ struct alignas(16) EpiMeta {
     int32_t inst[TBN];    // output instance of each column (-1: none)
     float sc[TBN];        // 2^-(ea + eb): the column's power-of-two rescale
     uint32_t mx[TBN];     // max-|component| of a run of an instance's columns, at the run's first column
+    int16_t acol[TBN];    // B dictionary: accumulator (complex) column holding tile column c
     int64_t base;         // element offset of tile element (row 0, column 0) in C
     int32_t ncv, pad;     // valid columns
 };
@@ -420,19 +421,22 @@ __device__ __forceinline__ void split_a_inplace(uint8_t *slot, int tid) {
 
 // Resident B: the producer threads load the B operand of a group's column
 // tiles ct0 .. ct0 + nct - 1 (schedule 0: all of the group's; schedule 1:
-// the tile's own), nch K chunks each, zeros past its columns and past K,
+// the tile's own; dictionary: every B instance of the step, instance j in
+// columns jN .. jN + N - 1), nch K chunks each, zeros past its columns and past K,
 // into pool slots bset[(ct - ct0) * nch + c], two chunks' global loads in
 // flight per thread at a time.  Each column is multiplied by its power-of-two
 // rescale 2^-(ea + eb) on the way (exact), so the epilogue stores the
 // accumulators as they are.
-template <int PREC>
+template <int PREC, bool DICT>
 __device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int nch, int K, uint8_t *bset,
                                           int bcol, int kqb) {
-    const int64_t ncols = int64_t(r.y) << d.nb;
-    const int ct0 = d.sched != 0 ? r.w / TBN : 0;
-    const int nct = d.sched != 0 ? 1 : int((ncols + TBN - 1) / TBN);
+    const int64_t ncols = DICT ? (d.nInstB << d.nb) : int64_t(r.y) << d.nb;
+    const int ct0 = (!DICT && d.sched != 0) ? r.w / TBN : 0;
+    const int nct = (DICT || d.sched != 0) ? 1 : int((ncols + TBN - 1) / TBN);
     const int N = 1 << d.nb;
-    const int ea = d.mxA ? exp_of(__ldg(d.mxA + r.z)) : 0;
+    // dictionary: column gc is column gc mod N of B instance gc / N, scaled
+    // by 2^-eb only (the A exponent changes from group to group)
+    const int ea = (!DICT && d.mxA) ? exp_of(__ldg(d.mxA + r.z)) : 0;
     int64_t cb[BRES_MAX_B];  // this thread's column in each column tile: element offset in B, or -1
     float sc[BRES_MAX_B];    // its power-of-two rescale 2^-(ea + eb), applied here instead of in the epilogue
 #pragma unroll
@@ -441,7 +445,7 @@ __device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int 
         cb[ct] = -1;
         sc[ct] = 1.f;
         if (ct < nct && gc < ncols) {
-            const int ib = __ldg(d.instab + r.x + (gc >> d.nb)).y;
+            const int ib = DICT ? int(gc >> d.nb) : __ldg(d.instab + r.x + (gc >> d.nb)).y;
             cb[ct] = int64_t(ib) * d.sB + ((gc & (N - 1)) << d.kb);
             sc[ct] = pow2f(-(ea + (d.mxB ? exp_of(__ldg(d.mxB + ib)) : 0)));
         }
@@ -472,6 +476,47 @@ __device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int 
     }
 }
 
+// tcgen05.ld of NR consecutive 32-bit accumulator columns (32x32b shape:
+// lane i of the warp gets row i of its lane quadrant)
+template <int NR>
+__device__ __forceinline__ void tmem_ld(uint32_t ta, uint32_t *r) {
+    if constexpr (NR == 2) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(ta));
+    } else if constexpr (NR == 4) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                     : "r"(ta));
+    } else if constexpr (NR == 8) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(ta));
+    } else {
+        static_assert(NR == 16, "16 columns at most");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(ta));
+    }
+}
+
+// B dictionary epilogue: the 8 tile columns cp .. cp + 7 of a pass, in runs
+// of R (one instance each), each run read from the accumulator columns its
+// instance's B occupies; runs past the tile's valid columns read as zeros.
+template <int R>
+__device__ __forceinline__ void tmem_gather(float (&v)[16], uint32_t tb, const EpiMeta &em, int cp, int ncv) {
+    uint32_t r[16];
+#pragma unroll
+    for (int j = 0; j < 8 / R; ++j) tmem_ld<2 * R>(tb + 2u * uint32_t(em.acol[cp + j * R]), r + 2 * j * R);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8 / R; ++j) {
+        const bool ok = cp + j * R < ncv;
+#pragma unroll
+        for (int q = 0; q < 2 * R; ++q) v[2 * j * R + q] = ok ? __uint_as_float(r[2 * j * R + q]) : 0.f;
+    }
+}
+
 // Epilogue max-|component| of one pass (8 complex columns; v: 16
 // accumulator values of this lane's row) over runs of RUN columns (one
 // instance each): folded in registers, one warp reduction per run, scaled
@@ -495,11 +540,16 @@ __device__ __forceinline__ void fold_max8(const float *v, EpiMeta &em, int c0, i
     }
 }
 
-template <int PREC, bool BRES>
+template <int PREC, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 warps on a sub-partition)
     k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA, int nrs) {
+    // MODE 0: B streamed chunk by chunk; 1: B resident (a group's or a
+    // column tile's), rescale folded into it; 2: B dictionary, every B
+    // instance of the step (at most 64 columns) resident for the whole
+    // launch, each tile's columns gathered from the accumulator.
     // nrs: A stages in use (C::RST streaming B; resident B: the pool slots
     // left after the largest resident B)
+    constexpr bool BRES = MODE != 0;
     using C = Cfg<PREC, BRES>;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment: the swizzled A slots are whole 8-row atoms
@@ -644,14 +694,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_unused, &g_n) : make_int4(0, 0, 0, 0);
         for (int64_t l = 0; l < my_tiles && !*abort_flag; ++l) {
             const int4 r = r_n;
-            const int64_t g = g_n;
+            const int64_t g = MODE == 2 ? 0 : g_n;  // the dictionary is loaded once
             if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_unused, &g_n);
             if (g != gprev) {
                 if (u > 0 && !mbar_wait(&X.bempty, (u - 1) & 1u)) {
                     give_up();
                     break;
                 }
-                load_bset<PREC>(d, r, nch, K, sm + C::OFF_RAW + nrs * C::SLOT_RAW, bcol, kqb);
+                load_bset<PREC, MODE == 2>(d, r, nch, K, sm + C::OFF_RAW + nrs * C::SLOT_RAW, bcol, kqb);
                 proxy_fence();
                 mbar_arrive(&X.bfull);
                 ++u;
@@ -788,7 +838,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_unused, &g_n) : make_int4(0, 0, 0, 0);
                 for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
                     const int4 r = r_n;
-                    const int64_t g = g_n;
+                    const int64_t g = MODE == 2 ? 0 : g_n;
                     if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_unused, &g_n);
                     const int acc = int(l & 1);
                     if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> 1) & 1u) ^ 1u)) {
@@ -806,7 +856,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     }
                     tc_fence_after();
                     const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
-                    const int ctl = d.sched != 0 ? 0 : r.w / TBN;  // the tile's column tile within the resident B
+                    const int ctl = (MODE == 2 || d.sched != 0) ? 0 : r.w / TBN;  // the tile's column tile within the resident B
                     const uint32_t bset = smem_u32(sm + C::OFF_RAW + (nrs + ctl * nch) * C::SLOT_RAW);
                     for (int c = 0; c < nch; ++c) {
                         if (!mbar_wait(PREC == 2 ? &X.afull[rs] : &X.rfull[rs], rph)) {
@@ -928,7 +978,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 const int eb = d.mxB ? exp_of(mxb[q]) : 0;
                 em.inst[c] = inst;
                 em.mx[c] = 0u;
-                em.sc[c] = pow2f(-(ea + eb));
+                em.sc[c] = pow2f(-(ea + (MODE == 2 ? 0 : eb)));  // the dictionary carries 2^-eb
+                if (MODE == 2) em.acol[c] = int16_t(inst >= 0 ? (ib0[q] << d.nb) + ((r0.w + c) & (N - 1)) : 0);
                 if (inst >= 0 && mt0 == 0 && ((int64_t(r0.w) + c) & (N - 1)) == 0) d.EC[inst] = EAv + ea + EBv[q] + eb;
             }
             if (lane == 0) {
@@ -1018,7 +1069,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
                     float v[16];
-                    if (act) {
+                    if (act && MODE == 2) {
+                        // dictionary: each run of the pass from its own accumulator columns
+                        const uint32_t tb = tmem + uint32_t(acc * ACC_COLS) + (uint32_t(lanegrp * 32) << 16);
+                        const int cp = c0 + 8 * p;
+                        switch (N < 8 ? N : 8) {
+                            case 1: tmem_gather<1>(v, tb, em, cp, ncv); break;
+                            case 2: tmem_gather<2>(v, tb, em, cp, ncv); break;
+                            case 4: tmem_gather<4>(v, tb, em, cp, ncv); break;
+                            default: tmem_gather<8>(v, tb, em, cp, ncv); break;
+                        }
+                    } else if (act) {
                         const uint32_t ta = tmem + uint32_t(acc * ACC_COLS + (c0 + 8 * p) * 2) +
                                             (uint32_t(lanegrp * 32) << 16);
                         uint32_t r[16];
@@ -1040,10 +1101,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     const int cp = c0 + 8 * p;  // first column of this pass
                     if (d.mxC) {
                         switch (N < 8 ? N : 8) {
-                            case 1: fold_max8<1, BRES>(v, em, cp, lane); break;
-                            case 2: fold_max8<2, BRES>(v, em, cp, lane); break;
-                            case 4: fold_max8<4, BRES>(v, em, cp, lane); break;
-                            default: fold_max8<8, BRES>(v, em, cp, lane); break;
+                            case 1: fold_max8<1, MODE == 1>(v, em, cp, lane); break;
+                            case 2: fold_max8<2, MODE == 1>(v, em, cp, lane); break;
+                            case 4: fold_max8<4, MODE == 1>(v, em, cp, lane); break;
+                            default: fold_max8<8, MODE == 1>(v, em, cp, lane); break;
                         }
                     }
                     // scale and stage in destination order
@@ -1059,7 +1120,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                             for (int j = 0; j < 4; ++j)
                                 if ((jj >> j) & 1) a ^= acol[j];
                             // resident B carries the rescale already
-                            const float s = BRES ? 1.f : scq[t];
+                            const float s = MODE == 1 ? 1.f : scq[t];
                             *reinterpret_cast<float2 *>(wst + a) =
                                 make_float2(v[2 * (4 * q + t)] * s, v[2 * (4 * q + t) + 1] * s);
                         }
@@ -1111,6 +1172,14 @@ bool gemm_tc_supports(const StepDesc &d) {
     return d.kb >= 3 && d.mb >= 6 && d.mb <= 30 && d.kb <= 24;
 }
 
+int tc_dictionary_chunks(const StepDesc &d) {
+    // schedule 0 with every B instance of the step in one 64-column tile
+    // (and K within the pool): the B dictionary's chunk count, else 0
+    if (!d.tc_resident_b || d.sched != 0 || (d.nInstB << d.nb) > TBN) return 0;
+    const int64_t nch = ((int64_t(1) << d.kb) + TBK - 1) / TBK;
+    return nch <= BRES_MAX_B ? int(nch) : 0;
+}
+
 int tc_resident_b_chunks(const StepDesc &d) {
     // B chunks resident at a time: schedule 0, the largest group's (its
     // 64-column tiles x K chunks); schedule 1, one column tile's; 0 when they
@@ -1140,17 +1209,19 @@ cudaError_t init_kernels() {
         if (e != cudaSuccess) return e;
         if (q != cudaDriverEntryPointSuccess || !g_encode) return cudaErrorNotSupported;
     }
-    e = cudaFuncSetAttribute(k_step_gemm_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<1, false>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_step_gemm_tc<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<2, false>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_step_gemm_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<1, true>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_step_gemm_tc<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<2, true>());
+    const void *fns[6] = {reinterpret_cast<const void *>(k_step_gemm_tc<1, 0>),
+                          reinterpret_cast<const void *>(k_step_gemm_tc<2, 0>),
+                          reinterpret_cast<const void *>(k_step_gemm_tc<1, 1>),
+                          reinterpret_cast<const void *>(k_step_gemm_tc<2, 1>),
+                          reinterpret_cast<const void *>(k_step_gemm_tc<1, 2>),
+                          reinterpret_cast<const void *>(k_step_gemm_tc<2, 2>)};
+    const int bytes[6] = {(int)smem_bytes<1, false>(), (int)smem_bytes<2, false>(), (int)smem_bytes<1, true>(),
+                          (int)smem_bytes<2, true>(),  (int)smem_bytes<1, true>(),  (int)smem_bytes<2, true>()};
+    for (int i = 0; i < 6; ++i) {
+        e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[i]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // The A operand of a step as a 3-D tensor for TMA: (real k = 2K floats of a
@@ -1181,18 +1252,25 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
     if (tiles <= 0) return cudaSuccess;
     const int64_t grid = tiles < g_num_sms ? tiles : g_num_sms;
     const dim3 g((unsigned)grid);
-    // B stays resident (per group, or per column tile) when it fits the pool
-    const int nbset = tc_resident_b_chunks(d);
-    if (nbset > 0) {
-        const int nrs = std::min(Cfg<2, true>::RST, Cfg<2, true>::NSLOT - nbset);
+    // B as a dictionary (every instance resident for the launch), else
+    // resident per group or column tile when it fits the pool, else streamed
+    const int ndict = tc_dictionary_chunks(d);
+    const int nbset = ndict > 0 ? ndict : tc_resident_b_chunks(d);
+    const int nrs = std::min(Cfg<2, true>::RST, Cfg<2, true>::NSLOT - nbset);
+    if (ndict > 0) {
         if (precision == 1)
-            k_step_gemm_tc<1, true><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+            k_step_gemm_tc<1, 2><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs);
         else
-            k_step_gemm_tc<2, true><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+            k_step_gemm_tc<2, 2><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+    } else if (nbset > 0) {
+        if (precision == 1)
+            k_step_gemm_tc<1, 1><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+        else
+            k_step_gemm_tc<2, 1><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs);
     } else if (precision == 1) {
-        k_step_gemm_tc<1, false><<<g, NTHREADS, smem_bytes<1, false>(), s>>>(d, mtiles, err, *a_map, Cfg<1, false>::RST);
+        k_step_gemm_tc<1, 0><<<g, NTHREADS, smem_bytes<1, false>(), s>>>(d, mtiles, err, *a_map, Cfg<1, false>::RST);
     } else {
-        k_step_gemm_tc<2, false><<<g, NTHREADS, smem_bytes<2, false>(), s>>>(d, mtiles, err, *a_map, Cfg<2, false>::RST);
+        k_step_gemm_tc<2, 0><<<g, NTHREADS, smem_bytes<2, false>(), s>>>(d, mtiles, err, *a_map, Cfg<2, false>::RST);
     }
     return cudaGetLastError();
 }

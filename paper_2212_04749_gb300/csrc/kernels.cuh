@@ -28,6 +28,7 @@ struct StepDesc {
     int32_t sched;                // schedule variant of the step's kernel (0 or 1; the autotuner's choice)
     int32_t tc_resident_b;        // tensor cores: keep B resident in shared memory where it fits
     int64_t nInst;
+    int64_t nInstB;               // B instances (tensor-core B dictionary)
     const int32_t *EA, *EB;       // accumulated exponents of the operands
     int32_t *EC;
     const uint32_t *mxA, *mxB;    // max-|component| bits of the operands (null: no rescale)
@@ -75,6 +76,10 @@ bool gemm_tc_supports(const StepDesc &d);
 // group's whole B; schedule 1: one column tile's) when it fits: the chunk
 // count, else 0.
 int tc_resident_b_chunks(const StepDesc &d);
+// Schedule 0 of a tensor-core step whose B instances all fit one 64-column
+// tile keeps them resident for the whole launch (a dictionary): the chunk
+// count, else 0.
+int tc_dictionary_chunks(const StepDesc &d);
 // One-time per-device setup (function attributes, SM count); call outside
 // any stream capture.
 cudaError_t init_kernels();

@@ -79,9 +79,10 @@ def test_forced_gemm_path_matches_state_vector(case, prec, request):
 def test_tensor_core_forms_match_state_vector(case20_shapes, prec, resident, config):
     # configuration 2 walks a group's tiles row tile by row tile, 3 column
     # tile by column tile; with resident B each CTA takes a contiguous range
-    # of tiles and keeps B in shared memory (a group's, or a column tile's),
-    # without it B is gathered chunk by chunk: all four forms against the
-    # state vector
+    # of tiles and keeps B in shared memory (configuration 2: all of the
+    # step's B instances when they fit one 64-column tile, else the group's;
+    # 3: a column tile's), without it B is gathered chunk by chunk: all the
+    # forms against the state vector
     torch, tn = require_cuda()
     c, bits, ssa, sl, ref = case20_shapes
     p = tn.Plan(c, bits, ssa, sl)
@@ -95,7 +96,14 @@ def test_tensor_core_forms_match_state_vector(case20_shapes, prec, resident, con
     p.tn_contract(amps, prec, stream=stream)
     p.tn_plan_check(stream=stream)
     torch.cuda.synchronize()
-    assert sum(1 for k in p.tn_plan_step_times()[1] if k == 2) >= 5
+    kinds = p.tn_plan_step_times()[1]
+    assert sum(1 for k in kinds if k == 2) >= 5
+    if config == 2 and resident:
+        # B dictionaries (every B instance of the step in one 64-column
+        # tile) whose groups hold several instances: their columns are
+        # gathered from the accumulator
+        assert any((s["n_inst_b"] << s["nb"]) <= 64 and s["n_inst"] > s["n_groups"]
+                   for s, k in zip(p.tn_plan_steps(), kinds) if k == 2)
     err = rel_l2(amps.cpu().numpy().view(np.complex128), ref)
     print(f"tensor-core 20q config {config} resident-B {resident} {prec}: rel-L2 {err:.3e}")
     assert err <= _tol(prec), err
