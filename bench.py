@@ -377,8 +377,10 @@ def run_ours(args, world, rank, local):
         fam_launch[f] = fam_launch.get(f, 0) + int(st["runs"])
     if args.dump_steps and rank == 0:
         rows = []
+        cfgs = plan.tn_plan_get_configs()
         for s_, st in enumerate(steps):
             r = dict(st)
+            r["config"] = int(cfgs[s_])
             r["ms_per_call"] = float(step_ms[s_])
             r["family"] = int(kernels[s_]) if kernels is not None else -1
             rows.append(r)
