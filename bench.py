@@ -265,7 +265,7 @@ def run_ours(args, world, rank, local):
     limit = min(int(args.ws_gib * 2 ** 30), int(free * 0.8))
     t0 = time.perf_counter()
     plan = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit, fuse=args.fuse,
-                   fuse_max_bits=args.fuse_bits)
+                   fuse_max_bits=args.fuse_bits, rescale=args.rescale)
     t_plan = time.perf_counter() - t0
     info = plan.info
     ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
@@ -396,11 +396,34 @@ def run_ours(args, world, rank, local):
         ach = fam_flops[dom] / sec / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
     else:
+        # tensor-core steps: bound by the tensor pipe or by HBM, whichever
+        # takes longer for the family's algorithmic flops and bytes
         base = peaks["bf16_tflops_sustained"]
         pk = base / 3.0 if args.precision == "bf16x3" else base * (1.1 / 2.25)
         ach = fam_flops[dom] / sec / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
+        t_tensor = fam_flops[dom] / (pk * 1e12)
+        t_hbm = fam_bytes[dom] / (peaks["hbm_gbs"] * 1e9)
+        if t_hbm >= t_tensor:
+            roof = {"bound": "hbm", "achieved": fam_bytes[dom] / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "tensor_tflops": ach, "tensor_frac": ach / pk}
+        else:
+            roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # per-step bound: each of the family's steps takes at least the longer of
+    # its flops at the compute peak and its bytes at the HBM peak
+    t_bound = 0.0
+    for s, st in enumerate(steps):
+        if (int(kernels[s]) if kernels is not None else 0) != dom:
+            continue
+        tb = st["bytes"] * st["runs"] / (peaks["hbm_gbs"] * 1e9)
+        if dom == 1:
+            tb = max(tb, st["flops"] * st["runs"] / (SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6))
+        elif dom == 2:
+            base = peaks["bf16_tflops_sustained"]
+            pk2 = base / 3.0 if args.precision == "bf16x3" else base * (1.1 / 2.25)
+            tb = max(tb, st["flops"] * st["runs"] / (pk2 * 1e12))
+        t_bound += tb
+    roof["step_bound_frac"] = t_bound / sec
     roof["traffic"] = None
     roof["kernel"] = fam_names[dom]
     roof["launches_per_step"] = fam_launch[dom]
@@ -419,7 +442,7 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             p2 = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit, fuse=args.fuse,
-                         fuse_max_bits=args.fuse_bits)
+                         fuse_max_bits=args.fuse_bits, rescale=args.rescale)
             for s_, c_ in enumerate(cfg_now):
                 p2.tn_plan_set_config(s_, int(c_))
             p2.tn_plan_bind(ws2, stream=stream)
@@ -454,7 +477,7 @@ def run_ours(args, world, rank, local):
                    "l2": "512 MiB write between steps; intermediates exceed L2",
                    "flops_eq1": info["flops_ma"], "flops_single_amplitude_x_k": info["flops_sa"],
                    "bytes_algorithmic": info["bytes_min"], "max_rank": info["max_rank"],
-                   "workspace_gib": info["workspace_bytes"] / 2 ** 30},
+                   "workspace_gib": info["workspace_bytes"] / 2 ** 30, "rescale": bool(args.rescale)},
         "tflops_algorithmic": tflops,
         "rel_l2_vs_oracle": err,
         "xeb": xeb,
@@ -493,6 +516,9 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--dump-steps", default=None, help="write per-step features and times (JSON) here")
     ap.add_argument("--fuse", type=int, choices=[0, 1], default=1, help="fused chains of small-operand steps")
+    ap.add_argument("--rescale", type=int, choices=[0, 1], default=0,
+                    help="per-instance power-of-two rescaling (a safety net of this library, not part of the "
+                         "paper's method; off: the paper's plain arithmetic)")
     ap.add_argument("--fuse-bits", type=int, default=9, help="d^t: largest fused-chain tile, 2^d^t entries")
     ap.add_argument("--chain-workload", default="grid6x7_m10",
                     help="workload whose heaviest fused chain is timed against the unfused steps ('' to skip)")
