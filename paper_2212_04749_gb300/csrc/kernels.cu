@@ -90,7 +90,10 @@ constexpr int ROW_CH = 32;    // most instances staged at once
 //     staged in shared memory, ROW_SB entries at a time; max-|x| words and
 //     exponents are recorded once per instance.
 //   small instances (M < 8R): a block = rows_per_block consecutive rows of
-//     consecutive groups; B comes through the L1 cache.
+//     consecutive groups, each row looping over its group's instances; B
+//     comes through the L1 cache.  Schedule 1: rows_per_block consecutive
+//     (instance, row) pairs, one per lane group, so that the instances of
+//     large groups run in parallel.
 template <int NB, int KL>
 __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int rows_per_block, int64_t mblocks) {
     constexpr int N = 1 << NB;
@@ -247,6 +250,41 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int 
                 if (d.mxC && s_mx[tid]) record_max(d.mxC + i, s_mx[tid]);
             }
             __syncthreads();
+        }
+    } else if (d.sched == 1) {
+        // small instances, schedule 1: one output instance row per lane
+        // group (instances of large groups run in parallel; their shared A
+        // rows come through the caches)
+        const int64_t total = d.nInst << mb;
+        for (int it = 0; it < passes; ++it) {
+            const int64_t gid = int64_t(blockIdx.x) * rows_per_block + (int64_t(it) * 8 + warp) * R + sub;
+            const bool valid = gid < total;
+            const int64_t gr = valid ? gid : 0;
+            const int64_t i = gr >> mb, m = gr & (M - 1);
+            const int2 ab = d.instab[i];
+            const int ea = d.mxA ? exp_of(d.mxA[ab.x]) : 0;
+            const int eb = d.mxB ? exp_of(d.mxB[ab.y]) : 0;
+            float2 a[KL];
+            load_row(a, ab.x, m, valid);
+            float2 acc[N];
+            row_times_b(acc, a, d.B + int64_t(ab.y) * d.sB);
+            const float sc = pow2f(-(ea + eb));
+            uint32_t mx = 0;
+            if (valid) {
+                float2 *C = d.C + i * d.sC + (mb > 8 ? dep(m >> 8, s_pCm + 8, mb - 8) : 0) + s_mloC[m & 255];
+                if (store_lane) {
+#pragma unroll
+                    for (int h = 0; h < N; ++h) {
+                        if (h >= n_held) break;
+                        const float2 v = make_float2(acc[h].x * sc, acc[h].y * sc);
+                        C[s_offCn[n0 + h]] = v;
+                        mx = max(mx, absmax_bits(v));
+                    }
+                }
+                if (m == 0 && kl == 0) d.EC[i] = d.EA[ab.x] + ea + d.EB[ab.y] + eb;
+            }
+            for (int o = L >> 1; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (d.mxC && valid && kl == 0 && mx) record_max(d.mxC + i, mx);
         }
     } else {
         const int64_t total = d.n_groups << mb;
@@ -508,9 +546,9 @@ cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
         rows_per_block = int(8 * R * passes);
         mblocks = M / rows_per_block;
         blocks = d.n_groups * mblocks;
-    } else {  // small instances: 4 passes over consecutive groups' rows
+    } else {  // small instances: 4 passes over consecutive (group, row) / schedule 1: (instance, row) pairs
         rows_per_block = 8 * R * 4;
-        blocks = ((d.n_groups << d.mb) + rows_per_block - 1) / rows_per_block;
+        blocks = (((d.sched == 1 ? d.nInst : d.n_groups) << d.mb) + rows_per_block - 1) / rows_per_block;
     }
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
