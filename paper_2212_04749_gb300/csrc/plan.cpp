@@ -1066,18 +1066,30 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
     int chosen = -1;
     // Cheap bounds before building a candidate's tables: every instance
     // costs ~48 bytes of host tables (instance maps, group and tile records),
-    // and one node's instances must fit the workspace by themselves.
-    // Batches that fail either are skipped without being built.
+    // and the tensors kept across slice batches (a node whose parent is
+    // recomputed more often than it is, and the leaves) plus the largest of
+    // the others must fit the workspace together.  Batches that fail either
+    // are skipped without being built.
     auto surely_too_big = [&](int ml) {
-        double inst = 0.0, largest = 0.0;
-        for (const Node &nd : P.nodes) {
+        std::vector<int> level(NN);
+        for (int v = 0; v < NN; ++v) {
+            int lv = 64;
+            for (int t : P.nodes[v].slices)
+                if (t >= ml) lv = std::min(lv, t - ml);
+            level[v] = lv;
+        }
+        double inst = 0.0, kept = 0.0, largest = 0.0;
+        for (int v = 0; v < NN; ++v) {
+            const Node &nd = P.nodes[v];
             int low = 0;
             for (int t : nd.slices) low += t < ml;
             const double ni = std::ldexp(double(nd.n_out), low);
+            const double bytes = ni * std::ldexp(8.0, nd.rank);
             inst += ni;
-            largest = std::max(largest, ni * std::ldexp(8.0, nd.rank));
+            if (v < T || (nd.parent >= 0 && level[v] > level[nd.parent])) kept += bytes;
+            else largest = std::max(largest, bytes);
         }
-        return inst * 48.0 > double(int64_t(8) << 30) || largest > double(P.opt.workspace_limit);
+        return inst * 48.0 > double(int64_t(8) << 30) || kept + largest > double(P.opt.workspace_limit);
     };
     for (int ml = hi; ml >= lo; --ml) {
         if (ml > lo && surely_too_big(ml)) continue;
@@ -1093,7 +1105,8 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
             break;
         }
     }
-    if (!B.schedule(chosen)) return false;
+    // the loop's last schedule() was for `chosen` (layout_workspace(false)
+    // only sets offsets that the final layout recomputes)
     B.find_chains();
     for (Node &nd : P.nodes) { nd.buf = NodeBuf(); }
     P.peak_tensor_bytes = 0;
