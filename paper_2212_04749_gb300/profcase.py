@@ -20,6 +20,7 @@ def main():
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--fuse", type=int, default=0)
     ap.add_argument("--ws-gib", type=float, default=4.0)
+    ap.add_argument("--list-steps", action="store_true", help="print each step's shape, bytes and flops")
     args = ap.parse_args()
     import torch
     from . import builder, costmodel, tn
@@ -37,6 +38,14 @@ def main():
     torch.cuda.synchronize()
     p.tn_plan_check(stream=st)
     print(f"ok {case.name} workspace {p.info['workspace_bytes']} bytes, {p.info['n_steps']} steps")
+    if args.list_steps:
+        # the steps in launch order with their shapes and algorithmic bytes
+        # and flops per launch (one slice batch), to match profiler records
+        ms, kinds = p.tn_plan_step_times()
+        for s, st in enumerate(p.tn_plan_steps()):
+            print(f"step {s} family {int(kinds[s])} mb {st['mb']} kb {st['kb']} nb {st['nb']} "
+                  f"inst {st['n_inst']} groups {st['n_groups']} inst_b {st['n_inst_b']} runs {st['runs']:.0f} "
+                  f"bytes {st['bytes']:.0f} flops {st['flops']:.0f}")
     return 0
 
 
