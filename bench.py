@@ -428,6 +428,20 @@ def run_ours(args, world, rank, local):
             tb = max(tb, st["flops"] * st["runs"] / (pk2 * 1e12))
         t_bound += tb
     roof["step_bound_frac"] = t_bound / sec
+    # the whole path: every step's bound (its bytes at the HBM peak, or its
+    # flops at its kernel's compute peak when longer) over the step's time
+    t_path = 0.0
+    for s, st in enumerate(steps):
+        fam = int(kernels[s]) if kernels is not None else 0
+        tb = st["bytes"] * st["runs"] / (peaks["hbm_gbs"] * 1e9)
+        if fam == 1:
+            tb = max(tb, st["flops"] * st["runs"] / (SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6))
+        elif fam == 2:
+            base = peaks["bf16_tflops_sustained"]
+            pk2 = base / 3.0 if args.precision == "bf16x3" else base * (1.1 / 2.25)
+            tb = max(tb, st["flops"] * st["runs"] / (pk2 * 1e12))
+        t_path += tb
+    path_bound_frac = t_path / (sum(fam_ms.values()) / 1000.0)
     roof["traffic"] = None
     roof["kernel"] = fam_names[dom]
     roof["launches_per_step"] = fam_launch[dom]
@@ -477,6 +491,7 @@ def run_ours(args, world, rank, local):
                    "bytes_algorithmic": info["bytes_min"], "max_rank": info["max_rank"],
                    "workspace_gib": info["workspace_bytes"] / 2 ** 30, "rescale": bool(args.rescale)},
         "tflops_algorithmic": tflops,
+        "path_bound_frac": path_bound_frac,
         "rel_l2_vs_oracle": err,
         "xeb": xeb,
         "other_forms": others or None,
