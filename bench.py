@@ -340,11 +340,15 @@ def run_ours(args, world, rank, local):
         step_ms += ms / prof_runs
     plan.tn_plan_profile(False)
 
-    # linear XEB of this run's amplitudes (FP64 reduction on the device)
+    # linear XEB of this run's amplitudes (FP64 reduction on the device) and
+    # the maximum-likelihood fidelity under Eq. (fxeb) with error bars (the
+    # stand-in bitstrings are uniform: both near 0)
     xeb_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
     tn.tn_xeb(amps, k, w.circuit.n_qubits, xeb_dev, stream=stream)
     torch.cuda.synchronize()
     xeb = float(xeb_dev.item())
+    from paper_2212_04749_gb300.xeb import porter_thomas_fit
+    xeb_fit = porter_thomas_fit(amps, k, w.circuit.n_qubits, stream=stream)
 
     # accuracy of this run against the stored oracle values
     got = amps.cpu().numpy().view(np.complex128)
@@ -494,6 +498,7 @@ def run_ours(args, world, rank, local):
         "path_bound_frac": path_bound_frac,
         "rel_l2_vs_oracle": err,
         "xeb": xeb,
+        "xeb_fit": xeb_fit,
         "other_forms": others or None,
         "config_selection": selection,
         "roofline": roof,

@@ -189,6 +189,32 @@ int tn_contract_slices(tn_plan_t plan, int precision, const int64_t *slice_ids, 
  * asynchronous on `stream`. */
 int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, void *stream);
 
+/* Porter-Thomas fit of the fidelity (analysis over tn_xeb's input).  With
+ * x_b = 2^n |amp_b|^2, bitstrings drawn from a depolarised ideal output
+ * distribution have the density p(x) = e^-x (1 + F (x - 1)) (Eq. (fxeb):
+ * the mixture of F x e^-x and (1 - F) e^-x).  tn_pt_moments writes five
+ * FP64 sums over the k device complex128 amplitudes to the caller's device
+ * words out_dev[0..4]: sum g, sum g^2 with g = (x - 1) / (1 + F (x - 1))
+ * (the derivative of the log-likelihood in F and minus its second
+ * derivative, the Fisher information), sum log(1 + F (x - 1)), sum x and
+ * sum x^2 (the linear XEB F = mean(x) - 1 and its standard error).  One
+ * block, fixed summation order.  TN_EINVAL for F outside [0, 1), k <= 0 or
+ * null pointers; asynchronous on `stream`. */
+int tn_pt_moments(const double *amps, int64_t k, int32_t n_qubits, double fidelity, double *out_dev,
+                  void *stream);
+
+/* Histogram of x_b = 2^n |amp_b|^2: counts_dev[j] (device, uint64, nbins + 1
+ * words, caller-zeroed, accumulated into) gains the b with
+ * floor(x_b / (x_max / nbins)) = j for j < nbins, and counts_dev[nbins]
+ * those with x_b >= x_max.  x_b, the bin width and the division are
+ * correctly rounded FP64 operations (no fused multiply-add), so a host
+ * computing re*re + im*im, times 2^n, divided by x_max / nbins, floored,
+ * gets the same bins.  TN_EINVAL for nbins outside [1, TN_PT_MAX_BINS],
+ * x_max <= 0, k <= 0 or null pointers. */
+#define TN_PT_MAX_BINS 8192
+int tn_pt_histogram(const double *amps, int64_t k, int32_t n_qubits, double x_max, int32_t nbins,
+                    uint64_t *counts_dev, void *stream);
+
 /* Override the kernel family of one step (-1: the plan's choice; 0: per-row
  * kernel, valid when N <= 16 and K*N <= 256; 1: grouped GEMM -- tensor
  * cores for TN_TF32 / TN_BF16X3 when the shape allows, CUDA cores

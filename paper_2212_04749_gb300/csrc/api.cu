@@ -593,6 +593,31 @@ int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, voi
     return TN_OK;
 }
 
+int tn_pt_moments(const double *amps, int64_t k, int32_t n_qubits, double fidelity, double *out_dev, void *stream) {
+    if (!amps || !out_dev || k <= 0 || n_qubits < 1 || n_qubits > 1000)
+        return set_err(TN_EINVAL, "tn_pt_moments: need k > 0, amplitudes and 5 output words");
+    if (!(fidelity >= 0.0 && fidelity < 1.0)) return set_err(TN_EINVAL, "tn_pt_moments: fidelity outside [0, 1)");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = tnk::launch_pt_moments(amps, k, std::ldexp(1.0, n_qubits), fidelity, out_dev, st);
+    if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("pt_moments: ") + cudaGetErrorString(e));
+    g_err.clear();
+    return TN_OK;
+}
+
+int tn_pt_histogram(const double *amps, int64_t k, int32_t n_qubits, double x_max, int32_t nbins,
+                    uint64_t *counts_dev, void *stream) {
+    if (!amps || !counts_dev || k <= 0 || n_qubits < 1 || n_qubits > 1000)
+        return set_err(TN_EINVAL, "tn_pt_histogram: need k > 0, amplitudes and a count array");
+    if (nbins < 1 || nbins > TN_PT_MAX_BINS || !(x_max > 0.0))
+        return set_err(TN_EINVAL, "tn_pt_histogram: need 1 <= nbins <= TN_PT_MAX_BINS and x_max > 0");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = tnk::launch_pt_hist(amps, k, std::ldexp(1.0, n_qubits), x_max, nbins,
+                                        reinterpret_cast<unsigned long long *>(counts_dev), st);
+    if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("pt_histogram: ") + cudaGetErrorString(e));
+    g_err.clear();
+    return TN_OK;
+}
+
 int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream) {
     if (!plan) return set_err(TN_EINVAL, "tn_contract_static: null plan");
     PlanObj *o = reinterpret_cast<PlanObj *>(plan);

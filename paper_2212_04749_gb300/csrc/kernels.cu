@@ -14,6 +14,9 @@
 //                    partials times 2^E, complex128, fixed slice order
 //                    (first-level slicing, SM Sec. IV.B)
 //   k_xeb            FP64 fixed-order reduction of sum |amp|^2 (Eq. fxeb)
+//   k_pt_moments     FP64 sums for the Porter-Thomas mixture fit of the
+//                    fidelity (density of Eq. fxeb) and the linear XEB's error
+//   k_pt_hist        histogram of x = N |amp|^2 (integer counts)
 //
 // Power-of-two rescaling: every produced instance records the largest
 // |component| of its entries (as float bits, atomicMax of non-negative
@@ -519,6 +522,66 @@ __global__ void __launch_bounds__(1024) k_xeb(const double2 *__restrict__ amps, 
     if (threadIdx.x == 0) out[0] = scale * s[0] - 1.0;
 }
 
+// x = N |a|^2 in FP64 with explicit round-to-nearest operations (no
+// contraction into an FMA), so that a host computing re*re + im*im, then
+// times N, gets the same bits
+__device__ __forceinline__ double pt_x(double2 a, double n_states) {
+    return __dmul_rn(n_states, __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)));
+}
+
+// Sums over the k amplitudes, for the mixture density
+// p(x) = e^-x (1 + F (x - 1)) of x = N |amp|^2 (fidelity F; Eq. fxeb):
+// out[0] = sum g, out[1] = sum g^2 with g = (x - 1) / (1 + F (x - 1)) (the
+// log-likelihood's first derivative and minus its second), out[2] = sum
+// log(1 + F (x - 1)), out[3] = sum x, out[4] = sum x^2.  One block, fixed
+// order.
+__global__ void __launch_bounds__(1024) k_pt_moments(const double2 *__restrict__ amps, int64_t k, double n_states,
+                                                     double fid, double *__restrict__ out) {
+    __shared__ double s[5][1024];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
+    for (int64_t p = threadIdx.x; p < k; p += 1024) {
+        const double x = pt_x(amps[p], n_states);
+        const double d = 1.0 + fid * (x - 1.0);
+        const double g = (x - 1.0) / d;
+        a0 += g;
+        a1 += g * g;
+        a2 += log(d);
+        a3 += x;
+        a4 += x * x;
+    }
+    s[0][threadIdx.x] = a0;
+    s[1][threadIdx.x] = a1;
+    s[2][threadIdx.x] = a2;
+    s[3][threadIdx.x] = a3;
+    s[4][threadIdx.x] = a4;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int j = 0; j < 5; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[threadIdx.x] = s[threadIdx.x][0];
+}
+
+// counts[j] += #{b : j width <= x_b < (j + 1) width}, j < nbins, with
+// width = x_max / nbins; counts[nbins] gathers x_b >= x_max.  The bin is
+// floor(x / width) in FP64 (correctly rounded division), integer atomics.
+__global__ void k_pt_hist(const double2 *__restrict__ amps, int64_t k, double n_states, double x_max, int nbins,
+                          unsigned long long *__restrict__ counts) {
+    extern __shared__ unsigned int h[];  // nbins + 1 block-local counts
+    for (int j = threadIdx.x; j <= nbins; j += blockDim.x) h[j] = 0u;
+    __syncthreads();
+    const double width = __ddiv_rn(x_max, double(nbins));
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < k; p += int64_t(gridDim.x) * blockDim.x) {
+        const double q = floor(__ddiv_rn(pt_x(amps[p], n_states), width));
+        const int j = q < double(nbins) ? int(q) : nbins;
+        atomicAdd(&h[j], 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j <= nbins; j += blockDim.x)
+        if (h[j]) atomicAdd(&counts[j], (unsigned long long)h[j]);
+}
+
 }  // namespace
 
 cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *highs, int64_t batch, float2 *ws,
@@ -605,6 +668,21 @@ cudaError_t launch_extract(const float2 *root, const int32_t *E, const int32_t *
 
 cudaError_t launch_xeb(const double *amps, int64_t k, double scale, double *out, cudaStream_t s) {
     k_xeb<<<1, 1024, 0, s>>>(reinterpret_cast<const double2 *>(amps), k, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pt_moments(const double *amps, int64_t k, double n_states, double fid, double *out,
+                              cudaStream_t s) {
+    k_pt_moments<<<1, 1024, 0, s>>>(reinterpret_cast<const double2 *>(amps), k, n_states, fid, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pt_hist(const double *amps, int64_t k, double n_states, double x_max, int nbins,
+                           unsigned long long *counts, cudaStream_t s) {
+    const int64_t want = (k + 255) / 256;
+    const int blocks = int(want < 1024 ? (want > 0 ? want : 1) : 1024);
+    k_pt_hist<<<blocks, 256, size_t(nbins + 1) * sizeof(unsigned int), s>>>(reinterpret_cast<const double2 *>(amps),
+                                                                         k, n_states, x_max, nbins, counts);
     return cudaGetLastError();
 }
 

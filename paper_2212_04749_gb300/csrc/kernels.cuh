@@ -68,6 +68,10 @@ cudaError_t launch_accumulate(const float2 *root, const int32_t *E, const int32_
 cudaError_t launch_extract(const float2 *root, const int32_t *E, const int32_t *uniq, int64_t k,
                            int64_t sigma, int32_t n_out, double *out, cudaStream_t s);
 cudaError_t launch_xeb(const double *amps, int64_t k, double scale, double *out, cudaStream_t s);
+cudaError_t launch_pt_moments(const double *amps, int64_t k, double n_states, double fid, double *out,
+                              cudaStream_t s);
+cudaError_t launch_pt_hist(const double *amps, int64_t k, double n_states, double x_max, int nbins,
+                           unsigned long long *counts, cudaStream_t s);
 
 // Tensor-core path (gemm_tc.cu).  precision: 1 = TF32, 2 = BF16x3.
 // Returns cudaErrorNotSupported for shapes it does not take.

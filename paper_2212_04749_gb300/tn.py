@@ -21,11 +21,12 @@ PRECISIONS = {"fp32": TN_FP32, "tf32": TN_TF32, "bf16x3": TN_BF16X3}
 
 EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_plan_widths", "tn_plan_steps",
            "tn_plan_bind", "tn_contract", "tn_contract_slices", "tn_xeb", "tn_plan_profile",
-           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_set_tc_resident_b", "tn_plan_get_configs",
+           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_set_tc_resident_b", "tn_plan_get_configs", "tn_pt_moments", "tn_pt_histogram",
            "tn_plan_features", "tn_plan_autotune", "tn_plan_select", "tn_mlp_grad_scratch_bytes",
            "tn_mlp_forward", "tn_mlp_grad", "tn_mlp_adam", "tn_mlp_to_half", "tn_mlp_forward_f16",
            "tn_plan_check", "tn_contract_static", "tn_destroy", "tn_last_error")
 TN_STATIC_SCRATCH_BYTES = 64 << 20
+TN_PT_MAX_BINS = 8192
 TN_NCONFIG = 4
 TN_NFEAT = TN_MLP_IN = 24
 TN_MLP_HIDDEN = 128
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = False):
         "tn_contract": (ctypes.c_int, [vp, ctypes.c_int, i64, i64, vp, vp]),
         "tn_contract_slices": (ctypes.c_int, [vp, ctypes.c_int, vp, i32, vp, vp]),
         "tn_xeb": (ctypes.c_int, [vp, i64, i32, vp, vp]),
+        "tn_pt_moments": (ctypes.c_int, [vp, i64, i32, ctypes.c_double, vp, vp]),
+        "tn_pt_histogram": (ctypes.c_int, [vp, i64, i32, ctypes.c_double, i32, vp, vp]),
         "tn_plan_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "tn_plan_set_kernel": (ctypes.c_int, [vp, i32, i32]),
         "tn_plan_set_config": (ctypes.c_int, [vp, i32, i32]),
@@ -343,6 +346,15 @@ class Plan:
 
 def tn_xeb(amps, k, n_qubits, out, stream=None):
     _check(load().tn_xeb(_ptr(amps), int(k), int(n_qubits), _ptr(out), _stream(stream)))
+
+
+def tn_pt_moments(amps, k, n_qubits, fidelity, out, stream=None):
+    _check(load().tn_pt_moments(_ptr(amps), int(k), int(n_qubits), float(fidelity), _ptr(out), _stream(stream)))
+
+
+def tn_pt_histogram(amps, k, n_qubits, x_max, nbins, counts, stream=None):
+    _check(load().tn_pt_histogram(_ptr(amps), int(k), int(n_qubits), float(x_max), int(nbins), _ptr(counts),
+                                  _stream(stream)))
 
 
 def tn_mlp_grad_scratch_bytes(n):

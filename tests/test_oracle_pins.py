@@ -119,6 +119,54 @@ def test_xeb_of_exact_samples_and_of_uniform_bitstrings():
     assert abs(xeb.linear_xeb(psi[mix], n) - 0.3) < 4 * np.sqrt(2.0 / k)
 
 
+def test_fidelity_fit_two_point_closed_form():
+    # for x = {a, b} the score (a-1)/(1+F(a-1)) + (b-1)/(1+F(b-1)) vanishes
+    # at F = -(a + b - 2) / (2 (a - 1)(b - 1)); a = 0.5, b = 3 gives 3/4,
+    # where each term of the Fisher information is 0.64
+    r = xeb.pt_fit(np.array([0.5, 3.0]))
+    assert abs(r["fidelity"] - 0.75) < 1e-12
+    assert abs(r["stderr"] - 1.0 / np.sqrt(1.28)) < 1e-12
+    assert abs(r["linear"] - 0.75) < 1e-15  # mean(x) - 1
+    # other pairs against the same closed form
+    for a, b in ((0.2, 2.5), (0.9, 1.7), (0.05, 6.0)):
+        want = -(a + b - 2) / (2 * (a - 1) * (b - 1))
+        if 0.0 < want < 1.0:
+            assert abs(xeb.pt_fit(np.array([a, b]))["fidelity"] - want) < 1e-10
+
+
+def test_fidelity_fit_recovers_the_mixture_fidelity():
+    # x drawn from Eq. (fxeb): with probability F from x e^-x (Gamma(2)),
+    # else from e^-x; the fit lands within 4 of its standard errors, and the
+    # error bar matches the spread of the linear estimator's theory
+    rng = np.random.default_rng(11)
+    k = 200000
+    for f in (0.0, 0.05, 0.3, 0.8):
+        ideal = rng.random(k) < f
+        x = np.where(ideal, rng.gamma(2.0, 1.0, k), rng.exponential(1.0, k))
+        r = xeb.pt_fit(x, start=0.5)
+        assert abs(r["fidelity"] - f) < 4 * r["stderr"] + 1e-9, (f, r)
+        assert abs(r["linear"] - f) < 4 * r["linear_stderr"], (f, r)
+        assert 0.5 / np.sqrt(k) < r["stderr"] < 2.0 / np.sqrt(k)
+        # the likelihood is largest at the fit
+        best = r["loglik"]
+        for g in (max(r["fidelity"] - 0.01, 0.0), min(r["fidelity"] + 0.01, 0.99)):
+            m = xeb.pt_moments(x, g)
+            assert m[2] - m[3] <= best + 1e-6
+
+
+def test_histogram_bins_and_counts():
+    x = np.array([0.0, 0.49, 0.5, 0.99, 1.0, 7.99, 8.0, 100.0])
+    h = xeb.pt_histogram(x, 8.0, 16)  # width 0.5
+    assert h.sum() == x.size and h[0] == 2 and h[1] == 2 and h[2] == 1 and h[15] == 1 and h[16] == 2
+    rng = np.random.default_rng(3)
+    k = 100000
+    y = rng.exponential(1.0, k)
+    counts = xeb.pt_histogram(y, 6.0, 24)
+    edges = np.linspace(0, 6.0, 25)
+    expect = k * np.append(np.diff(1 - np.exp(-edges)), np.exp(-6.0))
+    assert np.all(np.abs(counts - expect) < 5 * np.sqrt(expect) + 5)
+
+
 def test_porter_thomas_pdf_normalised_and_mean():
     x = np.linspace(0, 60, 600001)
     for f in (0.0, 0.002, 0.5, 1.0):
