@@ -83,15 +83,25 @@ typedef struct {
     int32_t slice_batch_log2; /* sliced edges run side by side in one pass;
                                  -1: largest that fits workspace_limit */
     int32_t rescale;          /* 1: per-instance power-of-two rescaling */
-    int32_t fuse;             /* 1: rewrite chains of big x small steps into
-                                 one GEMM against a pre-contracted operator */
-    int32_t fuse_max_bits;    /* d^t: largest K or N bit count of a fused
-                                 chain operator (SM Sec. V.C); 0: default 7 */
+    int32_t fuse;             /* 1: non-branching chains of steps with small
+                                 side operands run as one kernel each, their
+                                 intermediates never stored (SM Sec. V.C) */
+    int32_t fuse_max_bits;    /* d^t: a fused chain's tile holds at most
+                                 2^d^t complex entries (SM Sec. V.C);
+                                 0: default 7 */
     int32_t graphs;           /* 1: tn_contract captures its launch sequence in
                                  a CUDA graph on first use of a (precision,
                                  batch range, output buffer) and replays it */
-    int32_t reserved[9];
+    int32_t pad0;
+    int64_t open_mask;        /* correlated batches: bit q set leaves output
+                                 qubit q open (at most TN_MAX_OPEN); each input
+                                 bitstring then stands for its 2^|open|
+                                 completions (its values at open qubits are
+                                 ignored), see tn_contract */
+    int32_t reserved[6];
 } tn_options;
+
+#define TN_MAX_OPEN 16
 
 typedef struct {
     int32_t n_tensors, n_edges, n_nodes, n_steps;
@@ -108,6 +118,9 @@ typedef struct {
     int64_t peak_tensor_bytes;    /* largest intermediate set (all instances) */
     int64_t upload_bytes;         /* host-to-device bytes tn_plan_bind copies */
     int64_t launches_per_call;    /* kernels one full tn_contract launches */
+    int32_t n_open;               /* open output qubits (tn_options.open_mask) */
+    int32_t pad0;
+    int64_t amps_per_row;         /* 2^n_open complex amplitudes per input row */
 } tn_plan_info;
 
 typedef struct tn_plan_s *tn_plan_t;
@@ -164,8 +177,12 @@ int tn_plan_steps(tn_plan_t plan, tn_step_info *steps, int32_t n);
  * `stream`.  Must precede tn_contract*. */
 int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream);
 
-/* Accumulate into amps (device, complex128, k entries) the partial
- * amplitudes of every slice in slice batches [batch_lo, batch_hi).  The plan
+/* Accumulate into amps (device, complex128, k x amps_per_row entries) the
+ * partial amplitudes of every slice in slice batches [batch_lo, batch_hi).
+ * With open qubits q_0 < ... < q_{r-1} (tn_options.open_mask), entry
+ * p * 2^r + x of input row p is the amplitude of its bitstring with qubit
+ * q_i set to bit r - 1 - i of x (the lowest open qubit is the most
+ * significant, as in the state-vector index); r = 0: one entry per row.  The plan
  * partitions the 2^n_sliced slices into tn_plan_info.n_batches batches of
  * 2^slice_batch_log2 slices each (its own order of the sliced edges:
  * batch b holds the slices whose looped sliced edges take the bits of b);
@@ -177,8 +194,9 @@ int tn_contract(tn_plan_t plan, int precision, int64_t batch_lo, int64_t batch_h
                 double *amps, void *stream);
 
 /* Partial amplitudes of individual slices, for comparison with an oracle:
- * partials (device, complex128) receives ns x k entries, slice-major, each
- * already scaled back by its power-of-two exponent. */
+ * partials (device, complex128) receives ns x k x amps_per_row entries,
+ * slice-major, rows and completions as in tn_contract, each already scaled
+ * back by its power-of-two exponent. */
 int tn_contract_slices(tn_plan_t plan, int precision, const int64_t *slice_ids, int32_t ns,
                        double *partials, void *stream);
 
@@ -188,6 +206,21 @@ int tn_contract_slices(tn_plan_t plan, int precision, const int64_t *slice_ids, 
  * order.  Writes one double to the caller's device word *xeb_dev;
  * asynchronous on `stream`. */
 int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, void *stream);
+
+/* Perfect samples from correlated batches (main text on Fig. 3(b): a small
+ * batch of correlated amplitudes yields one exact sample; SM Sec. II: the
+ * batch leaves some output qubits open).  amps: k x 2^n_open device
+ * complex128 amplitudes as tn_contract writes them with n_open open
+ * qubits; uniform: k device doubles in [0, 1), the caller's random numbers.
+ * picks[p] (device int64) = the smallest completion x whose running sum of
+ * |amp(p, x)|^2, in x order, exceeds uniform[p] times the batch's total
+ * (2^n_open - 1 if none does): x is drawn with probability
+ * |amp(p, x)|^2 / sum_x' |amp(p, x')|^2.  FP64 with correctly rounded
+ * operations (no fused multiply-add), so the choice is reproducible on a
+ * host.  TN_EINVAL for n_open outside [0, TN_MAX_OPEN], k <= 0 or null
+ * pointers; asynchronous on `stream`. */
+int tn_sample_completions(const double *amps, int64_t k, int32_t n_open, const double *uniform, int64_t *picks,
+                          void *stream);
 
 /* Porter-Thomas fit of the fidelity (analysis over tn_xeb's input).  With
  * x_b = 2^n |amp_b|^2, bitstrings drawn from a depolarised ideal output

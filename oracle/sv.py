@@ -60,6 +60,27 @@ def amplitudes(circ, bits: np.ndarray) -> np.ndarray:
     return out.view(np.complex128)
 
 
+def completion_bits(bits: np.ndarray, open_qubits) -> np.ndarray:
+    """Correlated batches (SM Sec. II: some output indices left open): every
+    row of ``bits`` (k x n) expanded into its 2^r completions, r open qubits
+    q_0 < ... < q_{r-1}: row p * 2^r + x is row p with qubit q_i set to bit
+    r - 1 - i of x (k 2^r x n uint8)."""
+    bits = np.ascontiguousarray(bits, np.uint8)
+    oq = sorted(int(q) for q in open_qubits)
+    r = len(oq)
+    out = np.repeat(bits, 1 << r, axis=0)
+    x = np.tile(np.arange(1 << r), bits.shape[0])
+    for i, q in enumerate(oq):
+        out[:, q] = (x >> (r - 1 - i)) & 1
+    return out
+
+
+def correlated_amplitudes(circ, bits: np.ndarray, open_qubits) -> np.ndarray:
+    """Amplitudes of every completion of every row, complex128 (k 2^r,),
+    in completion_bits order."""
+    return amplitudes(circ, completion_bits(bits, open_qubits))
+
+
 def threads() -> int:
     """Threads OpenMP will use (OMP_NUM_THREADS, else all host cores)."""
     v = os.environ.get("OMP_NUM_THREADS")

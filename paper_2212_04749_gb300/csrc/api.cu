@@ -407,6 +407,8 @@ int tn_plan_query(tn_plan_t plan, tn_plan_info *info) {
     double steps_run = 0;
     for (const tnp::Step &st : P.steps) steps_run += (st.chain < 0 || st.chain_last) ? st.runs : 0.0;
     info->launches_per_call = (int64_t)steps_run + 2 * P.n_batches;  // + leaf fill and accumulate per batch
+    info->n_open = (int32_t)P.open_qubits.size();
+    info->amps_per_row = int64_t(1) << P.open_qubits.size();
     return TN_OK;
 }
 
@@ -504,7 +506,7 @@ int tn_contract(tn_plan_t plan, int precision, int64_t batch_lo, int64_t batch_h
     const int32_t *uniq = at<const int32_t>(o, P.off_uniq);
     auto enqueue = [&]() {
         return run_batches(o, precision, batch_lo, batch_hi, st, [&](int64_t) -> int {
-            cudaError_t e = tnk::launch_accumulate(root, E, uniq, P.k, R.n_sig, R.n_out, amps, st);
+            cudaError_t e = tnk::launch_accumulate(root, E, uniq, P.k, R.n_sig, R.n_out, R.rank, amps, st);
             if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("accumulate: ") + cudaGetErrorString(e));
             return TN_OK;
         });
@@ -572,7 +574,8 @@ int tn_contract_slices(tn_plan_t plan, int precision, const int64_t *slice_ids, 
         int rc = run_batches(o, precision, b, b + 1, st, [&](int64_t) -> int {
             for (int32_t i : kv.second) {
                 const int64_t sigma = internal[i] % per;
-                cudaError_t e = tnk::launch_extract(root, E, uniq, P.k, sigma, R.n_out, partials + 2 * P.k * i, st);
+                cudaError_t e = tnk::launch_extract(root, E, uniq, P.k, sigma, R.n_out, R.rank,
+                                                    partials + (2 * P.k * i << R.rank), st);
                 if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("extract: ") + cudaGetErrorString(e));
             }
             return TN_OK;
@@ -589,6 +592,17 @@ int tn_xeb(const double *amps, int64_t k, int32_t n_qubits, double *xeb_dev, voi
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = tnk::launch_xeb(amps, k, std::ldexp(1.0, n_qubits) / double(k), xeb_dev, st);
     if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("xeb: ") + cudaGetErrorString(e));
+    g_err.clear();
+    return TN_OK;
+}
+
+int tn_sample_completions(const double *amps, int64_t k, int32_t n_open, const double *uniform, int64_t *picks,
+                          void *stream) {
+    if (!amps || !uniform || !picks || k <= 0) return set_err(TN_EINVAL, "tn_sample_completions: need k > 0 and buffers");
+    if (n_open < 0 || n_open > TN_MAX_OPEN) return set_err(TN_EINVAL, "tn_sample_completions: n_open outside [0, TN_MAX_OPEN]");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = tnk::launch_sample(amps, k, n_open, uniform, picks, st);
+    if (e != cudaSuccess) return set_err(TN_ECUDA, std::string("sample: ") + cudaGetErrorString(e));
     g_err.clear();
     return TN_OK;
 }

@@ -17,6 +17,9 @@
 //   k_pt_moments     FP64 sums for the Porter-Thomas mixture fit of the
 //                    fidelity (density of Eq. fxeb) and the linear XEB's error
 //   k_pt_hist        histogram of x = N |amp|^2 (integer counts)
+//   k_sample         one completion per correlated batch, drawn with
+//                    probability |amp|^2 / sum over the batch (perfect
+//                    sample from a batch, main text on Fig. 3(b), SM Sec. II)
 //
 // Power-of-two rescaling: every produced instance records the largest
 // |component| of its entries (as float bits, atomicMax of non-negative
@@ -475,34 +478,44 @@ __global__ void __launch_bounds__(256) k_step_gemm_simt(const StepDesc d, int ct
     }
 }
 
+// root entry of completion x: its r bits reversed (root bit t = the t-th
+// lowest open qubit; x's most significant bit = the lowest open qubit)
+__device__ __forceinline__ int64_t root_entry(int64_t x, int r) {
+    return r == 0 ? 0 : int64_t(__brevll(uint64_t(x)) >> (64 - r));
+}
+
+// one thread per (input row, completion): amps[p 2^r + x] += the sum over
+// the pass's slice instances, in slice order, of root entry x times 2^E
 __global__ void k_accumulate(const float2 *__restrict__ root, const int32_t *__restrict__ E,
-                             const int32_t *__restrict__ uniq, int64_t k, int64_t n_sig, int32_t n_out,
+                             const int32_t *__restrict__ uniq, int64_t k, int64_t n_sig, int32_t n_out, int r,
                              double2 *__restrict__ amps) {
-    const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (p >= k) return;
-    const int64_t beta = uniq[p];
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= (k << r)) return;
+    const int64_t p = q >> r, x = q & ((int64_t(1) << r) - 1);
+    const int64_t beta = uniq[p], j = root_entry(x, r);
     double re = 0.0, im = 0.0;
     for (int64_t s = 0; s < n_sig; ++s) {
         const int64_t idx = s * n_out + beta;
-        const float2 v = root[idx];
+        const float2 v = root[(idx << r) + j];
         const int e = E[idx];
         re += ldexp(double(v.x), e);
         im += ldexp(double(v.y), e);
     }
-    double2 a = amps[p];
+    double2 a = amps[q];
     a.x += re;
     a.y += im;
-    amps[p] = a;
+    amps[q] = a;
 }
 
 __global__ void k_extract(const float2 *__restrict__ root, const int32_t *__restrict__ E,
-                          const int32_t *__restrict__ uniq, int64_t k, int64_t sigma, int32_t n_out,
+                          const int32_t *__restrict__ uniq, int64_t k, int64_t sigma, int32_t n_out, int r,
                           double2 *__restrict__ out) {
-    const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (p >= k) return;
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= (k << r)) return;
+    const int64_t p = q >> r, x = q & ((int64_t(1) << r) - 1);
     const int64_t idx = sigma * n_out + uniq[p];
-    const float2 v = root[idx];
-    out[p] = make_double2(ldexp(double(v.x), E[idx]), ldexp(double(v.y), E[idx]));
+    const float2 v = root[(idx << r) + root_entry(x, r)];
+    out[q] = make_double2(ldexp(double(v.x), E[idx]), ldexp(double(v.y), E[idx]));
 }
 
 __global__ void __launch_bounds__(1024) k_xeb(const double2 *__restrict__ amps, int64_t k, double scale,
@@ -582,6 +595,34 @@ __global__ void k_pt_hist(const double2 *__restrict__ amps, int64_t k, double n_
         if (h[j]) atomicAdd(&counts[j], (unsigned long long)h[j]);
 }
 
+// Row p's batch a[p 2^r .. p 2^r + 2^r): with u = uniform[p] in [0, 1), the
+// smallest x whose running sum of |a_x|^2 exceeds u times the batch total
+// (2^r - 1 if none does); FP64, correctly rounded operations in x order.
+__global__ void k_sample(const double2 *__restrict__ amps, int64_t k, int r, const double *__restrict__ uniform,
+                         int64_t *__restrict__ picks) {
+    const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= k) return;
+    const double2 *a = amps + (p << r);
+    const int64_t n = int64_t(1) << r;
+    double tot = 0.0;
+    for (int64_t x = 0; x < n; ++x) {
+        const double2 v = a[x];
+        tot = __dadd_rn(tot, __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)));
+    }
+    const double thr = __dmul_rn(uniform[p], tot);
+    double c = 0.0;
+    int64_t pick = n - 1;
+    for (int64_t x = 0; x < n; ++x) {
+        const double2 v = a[x];
+        c = __dadd_rn(c, __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)));
+        if (c > thr) {
+            pick = x;
+            break;
+        }
+    }
+    picks[p] = pick;
+}
+
 }  // namespace
 
 cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *highs, int64_t batch, float2 *ws,
@@ -651,23 +692,37 @@ cudaError_t launch_step_gemm_simt(const StepDesc &d, cudaStream_t s) {
 }
 
 cudaError_t launch_accumulate(const float2 *root, const int32_t *E, const int32_t *uniq, int64_t k,
-                              int64_t n_sig, int32_t n_out, double *amps, cudaStream_t s) {
+                              int64_t n_sig, int32_t n_out, int r, double *amps, cudaStream_t s) {
     if (k == 0) return cudaSuccess;
-    k_accumulate<<<dim3((unsigned)((k + 255) / 256)), 256, 0, s>>>(root, E, uniq, k, n_sig, n_out,
-                                                                   reinterpret_cast<double2 *>(amps));
+    if (r < 0 || r > 30) return cudaErrorInvalidValue;
+    const int64_t blocks = ((k << r) + 255) / 256;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_accumulate<<<dim3((unsigned)blocks), 256, 0, s>>>(root, E, uniq, k, n_sig, n_out, r,
+                                                        reinterpret_cast<double2 *>(amps));
     return cudaGetLastError();
 }
 
 cudaError_t launch_extract(const float2 *root, const int32_t *E, const int32_t *uniq, int64_t k, int64_t sigma,
-                           int32_t n_out, double *out, cudaStream_t s) {
+                           int32_t n_out, int r, double *out, cudaStream_t s) {
     if (k == 0) return cudaSuccess;
-    k_extract<<<dim3((unsigned)((k + 255) / 256)), 256, 0, s>>>(root, E, uniq, k, sigma, n_out,
-                                                                reinterpret_cast<double2 *>(out));
+    if (r < 0 || r > 30) return cudaErrorInvalidValue;
+    const int64_t blocks = ((k << r) + 255) / 256;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_extract<<<dim3((unsigned)blocks), 256, 0, s>>>(root, E, uniq, k, sigma, n_out, r,
+                                                     reinterpret_cast<double2 *>(out));
     return cudaGetLastError();
 }
 
 cudaError_t launch_xeb(const double *amps, int64_t k, double scale, double *out, cudaStream_t s) {
     k_xeb<<<1, 1024, 0, s>>>(reinterpret_cast<const double2 *>(amps), k, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const double *amps, int64_t k, int r, const double *uniform, int64_t *picks,
+                          cudaStream_t s) {
+    if (k == 0) return cudaSuccess;
+    k_sample<<<dim3((unsigned)((k + 127) / 128)), 128, 0, s>>>(reinterpret_cast<const double2 *>(amps), k, r,
+                                                               uniform, picks);
     return cudaGetLastError();
 }
 

@@ -63,13 +63,18 @@ cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *hi
                         float2 *ws, cudaStream_t s);
 cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s);
 cudaError_t launch_step_gemm_simt(const StepDesc &d, cudaStream_t s);
+// The root holds 2^r entries per instance (r open output qubits, its bit t
+// the t-th lowest); row p's completion x (most significant bit: the lowest
+// open qubit) is root entry bit-reverse_r(x).
 cudaError_t launch_accumulate(const float2 *root, const int32_t *E, const int32_t *uniq, int64_t k,
-                              int64_t n_sig, int32_t n_out, double *amps, cudaStream_t s);
+                              int64_t n_sig, int32_t n_out, int r, double *amps, cudaStream_t s);
 cudaError_t launch_extract(const float2 *root, const int32_t *E, const int32_t *uniq, int64_t k,
-                           int64_t sigma, int32_t n_out, double *out, cudaStream_t s);
+                           int64_t sigma, int32_t n_out, int r, double *out, cudaStream_t s);
 cudaError_t launch_xeb(const double *amps, int64_t k, double scale, double *out, cudaStream_t s);
 cudaError_t launch_pt_moments(const double *amps, int64_t k, double n_states, double fid, double *out,
                               cudaStream_t s);
+cudaError_t launch_sample(const double *amps, int64_t k, int r, const double *uniform, int64_t *picks,
+                          cudaStream_t s);
 cudaError_t launch_pt_hist(const double *amps, int64_t k, double n_states, double x_max, int nbins,
                            unsigned long long *counts, cudaStream_t s);
 

@@ -872,6 +872,31 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
     if (opt) P.opt = *opt;
     else tn_options_default(&P.opt);
     if (P.opt.workspace_limit <= 0) P.opt.workspace_limit = int64_t(64) << 30;
+    // Open output qubits (correlated batches): the output leg of each becomes
+    // a bond edge with one end.  No step contracts it, so it stays in the
+    // index sets up to the root, which then holds 2^|open| amplitudes per
+    // instance (the absorbed final single-qubit gates stay in the leaf).
+    // The bitstrings' values at open qubits are ignored.
+    const int n_edges_closed = P.net.n_edges;
+    {
+        const uint64_t om = uint64_t(P.opt.open_mask);
+        if (n < 64 && (om >> n) != 0) { err = "open_mask: a qubit beyond n_qubits"; return false; }
+        P.open_qubits.clear();
+        for (int q = 0; q < n; ++q)
+            if ((om >> q) & 1u) P.open_qubits.push_back(q);
+        if ((int)P.open_qubits.size() > TN_MAX_OPEN) {
+            err = "open_mask: more than TN_MAX_OPEN open qubits";
+            return false;
+        }
+        for (int q : P.open_qubits) {
+            const int t = P.net.out_tensor[q];
+            LeafTensor &L = P.net.leaves[t];
+            const int slot = (L.legs[0].kind == LEG_OUT && L.legs[0].id == q) ? 0 : 1;
+            const int e = P.net.n_edges++;
+            P.net.edge_ends.push_back({t, -1});
+            L.legs[slot] = Leg{LEG_BOND, e};
+        }
+    }
     if (k < 0 || (k > 0 && !bits)) { err = "bitstrings: need k >= 0 and a buffer"; return false; }
     if (k > (int64_t(1) << 30)) { err = "bitstrings: k too large"; return false; }
     // distinct bitstrings (c6: deduplicate, answer per input row)
@@ -883,6 +908,7 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
             std::string key(reinterpret_cast<const char *>(bits + r * n), n);
             for (int q = 0; q < n; ++q)
                 if (uint8_t(key[q]) > 1) { err = "bitstrings: entries must be 0 or 1"; return false; }
+            for (int q : P.open_qubits) key[q] = 0;
             auto it = seen.find(key);
             if (it == seen.end()) {
                 it = seen.emplace(key, (int32_t)P.ubits.size()).first;
@@ -899,7 +925,7 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
         std::set<int> s(P.sliced.begin(), P.sliced.end());
         if ((int)s.size() != n_sliced) { err = "sliced edges: duplicates"; return false; }
         for (int e : P.sliced)
-            if (e < 0 || e >= P.net.n_edges) { err = "sliced edges: id out of range"; return false; }
+            if (e < 0 || e >= n_edges_closed) { err = "sliced edges: id out of range"; return false; }
     }
     // tree
     const int NN = 2 * T - 1;
@@ -957,7 +983,10 @@ bool make_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k, const int
         std::set_union(a.slices.begin(), a.slices.end(), b.slices.begin(), b.slices.end(),
                        std::back_inserter(nd.slices));
     }
-    if ((int)P.nodes[P.root].outs.size() != n) { err = "tree: root does not hold every output leg"; return false; }
+    if ((int)P.nodes[P.root].outs.size() + (int)P.open_qubits.size() != n) {
+        err = "tree: root does not hold every output leg";
+        return false;
+    }
     // bonds each node shares with its sibling (contracted by its consumer)
     std::vector<std::vector<int>> low_bits(NN);
     for (int v = T; v < NN; ++v) {

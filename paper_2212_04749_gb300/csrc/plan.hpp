@@ -144,7 +144,8 @@ struct Plan {
     int64_t k = 0;                    // input rows
     std::vector<int32_t> uniq_of;     // input row -> distinct bitstring id
     int64_t k_unique = 0;
-    std::vector<std::vector<uint8_t>> ubits;  // distinct bitstrings
+    std::vector<std::vector<uint8_t>> ubits;  // distinct bitstrings (0 at open qubits)
+    std::vector<int> open_qubits;     // output qubits left open, ascending; the root's bit t is open_qubits[t]
     std::vector<int> sliced;          // sliced edge ids, external order (j-th takes bit j of s)
     std::vector<int> perm;            // internal slice index t -> external j
     int m_low = 0;                    // sliced edges batched in one pass

@@ -27,7 +27,8 @@ def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stre
     contractions run on (default: the current stream).  configs: optional
     per-step configurations applied to every plan (all batches must then
     yield plans with the same step count).  The amplitudes are complex128
-    numpy arrays in input order, read from pinned host memory after the
+    numpy arrays in input order (rows x 2^|open qubits| with
+    opts open_qubits / open_mask), read from pinned host memory after the
     batch's contraction finished.
     """
     import torch
@@ -36,9 +37,7 @@ def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stre
     n = len(batches)
     if n == 0:
         return
-    kmax = max(len(b) for b in batches)
-    amps = torch.zeros(2 * max(kmax, 1), dtype=torch.float64, device="cuda")
-    host = torch.empty(2 * max(kmax, 1), dtype=torch.float64, pin_memory=True)
+    amps = host = None  # grown to the largest batch (rows x amplitudes per row)
 
     def plan_of(i):
         return tn.Plan(circ, batches[i], tree_ssa, sliced, **opts)
@@ -52,15 +51,18 @@ def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stre
             if configs is not None:
                 for s, c in enumerate(configs):
                     p.tn_plan_set_config(s, int(c))
-            k = len(batches[i])
+            m = len(batches[i]) * p.info["amps_per_row"]
+            if amps is None or amps.numel() < 2 * m:
+                amps = torch.zeros(2 * max(m, 1), dtype=torch.float64, device="cuda")
+                host = torch.empty(2 * max(m, 1), dtype=torch.float64, pin_memory=True)
             if p.info["workspace_bytes"] > workspace.numel():
                 raise ValueError(f"batch {i}: plan needs {p.info['workspace_bytes']} workspace bytes, "
                                  f"workspace holds {workspace.numel()}")
             p.tn_plan_bind(workspace, stream=stream)
-            a = amps[:2 * k]
+            a = amps[:2 * m]
             a.zero_()
             p.tn_contract(a, precision, stream=stream)
-            h = host[:2 * k]
+            h = host[:2 * m]
             h.copy_(a, non_blocking=True)
             stream.synchronize()
             p.tn_plan_check(stream=stream)

@@ -21,12 +21,13 @@ PRECISIONS = {"fp32": TN_FP32, "tf32": TN_TF32, "bf16x3": TN_BF16X3}
 
 EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_plan_widths", "tn_plan_steps",
            "tn_plan_bind", "tn_contract", "tn_contract_slices", "tn_xeb", "tn_plan_profile",
-           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_set_tc_resident_b", "tn_plan_get_configs", "tn_pt_moments", "tn_pt_histogram",
+           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_set_tc_resident_b", "tn_plan_get_configs", "tn_pt_moments", "tn_pt_histogram", "tn_sample_completions",
            "tn_plan_features", "tn_plan_autotune", "tn_plan_select", "tn_mlp_grad_scratch_bytes",
            "tn_mlp_forward", "tn_mlp_grad", "tn_mlp_adam", "tn_mlp_to_half", "tn_mlp_forward_f16",
            "tn_plan_check", "tn_contract_static", "tn_destroy", "tn_last_error")
 TN_STATIC_SCRATCH_BYTES = 64 << 20
 TN_PT_MAX_BINS = 8192
+TN_MAX_OPEN = 16
 TN_NCONFIG = 4
 TN_NFEAT = TN_MLP_IN = 24
 TN_MLP_HIDDEN = 128
@@ -52,7 +53,8 @@ class tn_circuit(ctypes.Structure):
 class tn_options(ctypes.Structure):
     _fields_ = [("workspace_limit", ctypes.c_int64), ("slice_batch_log2", ctypes.c_int32),
                 ("rescale", ctypes.c_int32), ("fuse", ctypes.c_int32), ("fuse_max_bits", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("graphs", ctypes.c_int32), ("pad0", ctypes.c_int32), ("open_mask", ctypes.c_int64),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class tn_plan_info(ctypes.Structure):
@@ -63,7 +65,8 @@ class tn_plan_info(ctypes.Structure):
                 ("flops_ma", ctypes.c_double), ("flops_sa", ctypes.c_double), ("flops_exec", ctypes.c_double),
                 ("bytes_min", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
                 ("peak_tensor_bytes", ctypes.c_int64), ("upload_bytes", ctypes.c_int64),
-                ("launches_per_call", ctypes.c_int64)]
+                ("launches_per_call", ctypes.c_int64), ("n_open", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("amps_per_row", ctypes.c_int64)]
 
 
 class tn_step_info(ctypes.Structure):
@@ -110,6 +113,7 @@ def load(build_if_missing: bool = False):
         "tn_contract_slices": (ctypes.c_int, [vp, ctypes.c_int, vp, i32, vp, vp]),
         "tn_xeb": (ctypes.c_int, [vp, i64, i32, vp, vp]),
         "tn_pt_moments": (ctypes.c_int, [vp, i64, i32, ctypes.c_double, vp, vp]),
+        "tn_sample_completions": (ctypes.c_int, [vp, i64, i32, vp, vp, vp]),
         "tn_pt_histogram": (ctypes.c_int, [vp, i64, i32, ctypes.c_double, i32, vp, vp]),
         "tn_plan_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "tn_plan_set_kernel": (ctypes.c_int, [vp, i32, i32]),
@@ -178,9 +182,13 @@ def circuit_struct(circ):
 
 
 def options(**kw) -> tn_options:
+    """tn_options with the library's defaults, then the given fields;
+    open_qubits=[...] sets open_mask from a list of qubits."""
     o = tn_options()
     load().tn_options_default(ctypes.byref(o))
     for k, v in kw.items():
+        if k == "open_qubits":
+            k, v = "open_mask", sum(1 << int(q) for q in v)
         setattr(o, k, v)
     return o
 
@@ -346,6 +354,10 @@ class Plan:
 
 def tn_xeb(amps, k, n_qubits, out, stream=None):
     _check(load().tn_xeb(_ptr(amps), int(k), int(n_qubits), _ptr(out), _stream(stream)))
+
+
+def tn_sample_completions(amps, k, n_open, uniform, picks, stream=None):
+    _check(load().tn_sample_completions(_ptr(amps), int(k), int(n_open), _ptr(uniform), _ptr(picks), _stream(stream)))
 
 
 def tn_pt_moments(amps, k, n_qubits, fidelity, out, stream=None):

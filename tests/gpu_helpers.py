@@ -32,7 +32,7 @@ def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, force_k
                 p.tn_plan_set_config(s, c)
     ws = torch.empty(max(p.info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
     p.tn_plan_bind(ws, stream=torch.cuda.current_stream())
-    amps = torch.zeros(2 * len(bits), dtype=torch.float64, device="cuda")
+    amps = torch.zeros(2 * len(bits) * p.info["amps_per_row"], dtype=torch.float64, device="cuda")
     if batches is None:
         p.tn_contract(amps, precision, stream=torch.cuda.current_stream())
     else:

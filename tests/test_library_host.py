@@ -257,3 +257,26 @@ def test_fused_chains_are_well_formed(tn, name):
     assert p1.info["launches_per_call"] < p0.info["launches_per_call"]
     assert p1.info["bytes_min"] < p0.info["bytes_min"]
     assert p1.info["flops_exec"] == p0.info["flops_exec"]
+
+
+def test_open_qubits_plan_structure(tn):
+    # correlated batches: open output qubits reach the root, whose instances
+    # then hold 2^r amplitudes; rows equal up to their open bits share one
+    # distinct bitstring; bad masks and sliced open legs are rejected
+    w = make_workload("grid3x4_m8")
+    bits = w.bits.copy()
+    bits[1] = bits[0]
+    bits[1, 5] ^= 1  # differs from row 0 only at an open qubit
+    p = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, open_qubits=[2, 5, 11])
+    assert p.info["n_open"] == 3 and p.info["amps_per_row"] == 8
+    masked = bits.copy()
+    masked[:, [2, 5, 11]] = 0
+    assert p.info["n_unique"] == len({r.tobytes() for r in masked})
+    assert p.info["n_unique"] < len({r.tobytes() for r in bits})
+    width, rank, _ = p.tn_plan_widths()
+    assert rank[-1] == 3 and width[-1] == p.info["n_unique"]
+    with pytest.raises(Exception):
+        tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, open_mask=1 << 12)
+    nt, ne, ends, outs = tn.tn_network(w.circuit)
+    with pytest.raises(Exception):  # edge id ne would be an open leg: not a bond
+        tn.Plan(w.circuit, bits, w.tree.ssa, [ne], open_qubits=[0])

@@ -336,3 +336,44 @@ def test_planted_missing_relu_mask_fails_finite_differences():
         fd[i] = (mlp.loss(p + e, X, t, d, h) - mlp.loss(p - e, X, t, d, h)) / (2 * eps)
     # the pin's tolerance (as in the finite-difference test) rejects it
     assert np.max(np.abs(fd - g_wrong_W2.ravel())) > 1e-7 * max(1.0, np.max(np.abs(fd))) * 100
+
+
+# Correlated batches and perfect samples from them ------------------------
+def test_correlated_amplitudes_cover_the_state():
+    # every closed assignment of 10 qubits with 3 left open: the completions
+    # enumerate every basis state once, so they reproduce the brute-force
+    # unitary's column (independent of the state-vector code) and sum to 1
+    c = random_circuit(grid_layout(2, 5), 6, seed=8)
+    n, oq = 10, [1, 4, 9]
+    closed = [q for q in range(n) if q not in oq]
+    base = np.zeros((1 << len(closed), n), np.uint8)
+    for r in range(base.shape[0]):
+        for i, q in enumerate(closed):
+            base[r, q] = (r >> (len(closed) - 1 - i)) & 1
+    amps = sv.correlated_amplitudes(c, base, oq)
+    full = brute.unitary(c)[:, 0]
+    rows = sv.completion_bits(base, oq)
+    idx = (rows.astype(np.int64) << np.arange(n - 1, -1, -1)).sum(axis=1)
+    assert np.allclose(amps, full[idx], atol=1e-13)
+    assert abs(np.sum(np.abs(amps) ** 2) - 1.0) < 1e-12
+    assert sorted(idx.tolist()) == list(range(1 << n))
+    # the completion that equals the row itself is the row's own amplitude
+    own = sv.amplitudes(c, base)  # base rows hold 0 at the open qubits: completion 0
+    assert np.allclose(amps.reshape(-1, 8)[:, 0], own)
+
+
+def test_sample_completions_rule_and_frequencies():
+    from oracle.sampling import sample_completions
+    a = np.array([0.5, 0.5j])  # |a|^2 = 1/4 each (exact): total 1/2
+    for u, want in ((0.0, 0), (0.49, 0), (0.5, 1), (0.51, 1), (0.999, 1)):
+        # u = 1/2: the running sum 1/4 does not exceed the threshold 1/4
+        assert sample_completions(a, 1, np.array([u]))[0] == want, u
+    z = np.array([0.0, 0.0, 0.6, 0.8])  # zeros are never drawn
+    assert sample_completions(z, 2, np.array([0.0]))[0] == 2
+    rng = np.random.default_rng(2)
+    amps = rng.normal(size=(1, 16)) + 1j * rng.normal(size=(1, 16))
+    p = np.abs(amps[0]) ** 2 / np.sum(np.abs(amps) ** 2)
+    k = 200000
+    picks = sample_completions(np.repeat(amps, k, axis=0).ravel(), 4, rng.random(k))
+    freq = np.bincount(picks, minlength=16) / k
+    assert np.all(np.abs(freq - p) < 5 * np.sqrt(p * (1 - p) / k) + 1e-4)
