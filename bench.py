@@ -167,6 +167,45 @@ def cpu_oracle_sample(w, budget_s=20.0):
                       f"for the {k} bitstrings"}
 
 
+def measure_correlated(w, precision, torch, tn, stream, ws, limit, rows=256, n_open=4, reps=3):
+    """Correlated batches (SM Sec. II): `rows` of the workload's bitstrings
+    with their last `n_open` qubits left open, so that one contraction
+    yields rows x 2^n_open amplitudes (the same count as the headline
+    batch when rows x 2^n_open = k), then one perfect sample per row
+    (tn_sample_completions, uniform numbers drawn on the host, seed 5).
+    CUDA-event time of the contraction (the plan's rule configuration)
+    and of the sampling."""
+    n = w.circuit.n_qubits
+    oq = list(range(n - n_open, n))
+    p = tn.Plan(w.circuit, w.bits[:rows], w.tree.ssa, w.tree.sliced, workspace_limit=min(limit, ws.numel()),
+                open_qubits=oq)
+    if p.info["workspace_bytes"] > ws.numel():
+        return {"skipped": f"needs {p.info['workspace_bytes'] / 2**30:.1f} GiB"}
+    p.tn_plan_bind(ws, stream=stream)
+    m = rows << n_open
+    amps = torch.zeros(2 * m, dtype=torch.float64, device="cuda")
+    u = torch.from_numpy(np.random.default_rng(5).random(rows)).cuda()
+    picks = torch.empty(rows, dtype=torch.int64, device="cuda")
+    ts, tsamp = [], []
+    for r in range(reps + 1):
+        amps.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        p.tn_contract(amps, precision, stream=stream)
+        e1.record(stream)
+        tn.tn_sample_completions(amps, rows, n_open, u, picks, stream=stream)
+        e2.record(stream)
+        e2.synchronize()
+        if r > 0:
+            ts.append(e0.elapsed_time(e1))
+            tsamp.append(e1.elapsed_time(e2))
+    ms = statistics.mean(ts)
+    return {"rows": rows, "open_qubits": oq, "amplitudes": m, "ms_per_contraction": ms,
+            "amplitudes_per_s": m / (ms / 1000.0), "sampling_ms": statistics.mean(tsamp),
+            "samples_per_s": rows / ((ms + statistics.mean(tsamp)) / 1000.0),
+            "workspace_gib": p.info["workspace_bytes"] / 2 ** 30}
+
+
 def measure_chain(name, precision, torch, tn, stream, fuse_bits, batches=4):
     """Fused chains (tn_options.fuse) against the unfused steps on a workload
     whose heaviest chain is worth fusing: per-step CUDA-event times over the
@@ -473,6 +512,11 @@ def run_ours(args, world, rank, local):
         e2e = {"value": k * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(info["upload_bytes"]),
                "d2h_bytes_per_step": int(16 * k), "host_plan_s": t_plan, "planning": "overlapped"}
 
+    correlated = None
+    if rank == 0 and args.correlated:
+        correlated = measure_correlated(w, args.precision, torch, tn, stream, ws, limit)
+        plan.tn_plan_bind(ws, stream=stream)
+
     chain = None
     if rank == 0 and args.chain_workload:
         chain = measure_chain(args.chain_workload, args.precision, torch, tn, stream, args.fuse_bits)
@@ -499,6 +543,7 @@ def run_ours(args, world, rank, local):
         "rel_l2_vs_oracle": err,
         "xeb": xeb,
         "xeb_fit": xeb_fit,
+        "correlated_batches": correlated,
         "other_forms": others or None,
         "config_selection": selection,
         "roofline": roof,
@@ -534,6 +579,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--dump-steps", default=None, help="write per-step features and times (JSON) here")
     ap.add_argument("--fuse", type=int, choices=[0, 1], default=1, help="fused chains of small-operand steps")
+    ap.add_argument("--correlated", type=int, choices=[0, 1], default=1,
+                    help="also time correlated batches (open qubits) and perfect-sample extraction")
     ap.add_argument("--rescale", type=int, choices=[0, 1], default=0,
                     help="per-instance power-of-two rescaling (a safety net of this library, not part of the "
                          "paper's method; off: the paper's plain arithmetic)")
