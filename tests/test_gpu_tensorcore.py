@@ -165,3 +165,12 @@ def test_grid5x6_mixed_matches_stored_state_vector(prec):
     err = rel_l2(got, ref)
     print(f"grid5x6_m14 {prec}: rel-L2 {err:.3e}")
     assert err <= _tol(prec), err
+    if prec == "bf16x3":
+        # configuration 3 on every GEMM-shaped step: schedule 1 with the
+        # group's two column tiles walked by CTA pairs where every group has
+        # two (M = 2^12 x 4 columns, 2^21 / 2^18 x 64 columns, ...)
+        got3, p3 = run_plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, precision=prec,
+                            force_config=lambda st: 3 if st["kb"] >= 3 and st["mb"] >= 6 else None)
+        err3 = rel_l2(got3, ref)
+        print(f"grid5x6_m14 {prec}, configuration 3: rel-L2 {err3:.3e}")
+        assert err3 <= _tol(prec), err3
