@@ -23,12 +23,15 @@
 // are gathered per instance, expanded into the real 2x2 form and stored in
 // the K-major no-swizzle layout (core matrix 8 rows x 16 bytes; LBO =
 // distance between K-adjacent core matrices = 128 rows x 16 B, SBO =
-// distance between 8-row groups = 128 B).  One thread issues the MMAs
-// into an FP32 accumulator in TMEM (two 128-column accumulators), read back
-// with tcgen05.ld for the epilogue: power-of-two scale and max-|x|
-// tracking, then each half tile goes through shared memory, reordered by
-// C address (the output bit positions), and leaves as coalesced 16-byte
-// stores.
+// distance between 8-row groups = 128 B): chunk by chunk beside A
+// (streaming, MODE 0), once per group or column tile and kept in shared
+// memory (resident, MODE 1, with the power-of-two rescale folded in), or
+// every B instance of the step once per launch (dictionary, MODE 2).  One
+// thread issues the MMAs into an FP32 accumulator in TMEM (two 128-column
+// accumulators), read back with tcgen05.ld for the epilogue: power-of-two
+// scale and max-|x| tracking, then each half tile goes through shared
+// memory, reordered by C address (the output bit positions), and leaves as
+// coalesced 16-byte stores.
 //
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // code in *err, skips the remaining work, frees its TMEM and returns.
@@ -223,9 +226,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 }
 
 // Persistent warp-specialised kernel, five warpgroups.
-//   warps 0-7  : B columns by cp.async (LOOK chunks ahead), expanded into the
-//                real 2x2 block form; BF16x3: A split into hi/lo in place in
-//                the TMA ring.  TF32 reads A straight from the ring.
+//   warps 0-7  : B: streaming, per-thread cp.async pieces LOOK chunks ahead,
+//                expanded chunk by chunk; resident / dictionary, the whole
+//                B loaded and expanded at each group (column tile) switch.
+//                BF16x3: A split into hi/lo in place in the TMA ring; TF32
+//                reads A straight from the ring.
 //   warps 8-15 : epilogue, two warps per TMEM lane quadrant (warp % 4), each
 //                draining 16 complex columns of each half tile; two
 //                accumulators so that a tile's epilogue overlaps the next
