@@ -177,9 +177,11 @@ def test_empty_bitstring_batch_is_a_no_op():
     assert torch.all(sentinel == 7.0)
 
 
-def test_pipelined_batches_match_state_vector():
+@pytest.mark.parametrize("buffers", [1, 2])
+def test_pipelined_batches_match_state_vector(buffers):
     # successive bitstring batches of different sizes through the pipeline
-    # (batch i + 1 planned while batch i runs): each against the state vector
+    # (batch i + 1 planned, with two workspaces also bound, while batch i
+    # runs): each against the state vector
     torch, tn = require_cuda()
     from paper_2212_04749_gb300.pipeline import contract_batches
     from rqc import grid_layout, network_structure, random_circuit
@@ -188,8 +190,8 @@ def test_pipelined_batches_match_state_vector():
     c = random_circuit(grid_layout(3, 4), 8, seed=3)
     batches = [uniform_bitstrings(12, k, seed=s) for s, k in ((1, 300), (2, 77), (3, 512))]
     ssa = candidate_trees(network_structure(c), 300, seed=1, trials=1)[0]
-    ws = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    got = dict(contract_batches(c, batches, ssa, [], "fp32", ws))
+    ws = [torch.empty(256 << 20, dtype=torch.uint8, device="cuda") for _ in range(buffers)]
+    got = dict(contract_batches(c, batches, ssa, [], "fp32", ws[0] if buffers == 1 else tuple(ws)))
     assert sorted(got) == [0, 1, 2]
     for i, b in enumerate(batches):
         assert rel_l2(got[i], sv.amplitudes(c, b)) <= 1e-5
