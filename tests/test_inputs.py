@@ -26,6 +26,26 @@ def test_single_qubit_gates_are_the_printed_square_roots():
     assert np.allclose(SQRT_X, np.sqrt(0.5) * np.array([[1, -1j], [-1j, 1]]))
 
 
+def test_single_qubit_gates_entry_by_entry():
+    # The matrices exactly as printed (SM Sec. I), row = output state: a
+    # transposed sqrt(Y) or sqrt(W) squares to Y or W up to a phase as well,
+    # so each entry is pinned on its own.
+    h = np.sqrt(2.0) / 2.0
+    printed = {
+        "sqrtX": [[h, -1j * h], [-1j * h, h]],
+        "sqrtY": [[h, -h], [h, h]],
+        "sqrtW": [[h, -h * h * (1 + 1j)], [h * h * (1 - 1j), h]],
+    }
+    for g, name in ((SQRT_X, "sqrtX"), (SQRT_Y, "sqrtY"), (SQRT_W, "sqrtW")):
+        for r in range(2):
+            for c in range(2):
+                assert abs(g[r, c] - printed[name][r][c]) < 1e-15, (name, r, c)
+    # applied to |0>: sqrt(Y)|0> = (|0> + |1>)/sqrt(2), sqrt(W)|0> has the
+    # phase (1 - i)/sqrt(2) on |1>
+    assert np.allclose(SQRT_Y @ [1, 0], [h, h], atol=1e-15)
+    assert np.allclose(SQRT_W @ [1, 0], [h, 0.5 * (1 - 1j)], atol=1e-15)
+
+
 def test_fsim_pi2_pi6_closed_form():
     m = fsim(np.pi / 2, np.pi / 6)
     ref = np.zeros((4, 4), complex)

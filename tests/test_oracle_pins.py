@@ -103,6 +103,32 @@ def test_porter_thomas_at_zero_fidelity():
     assert ds > 0.05
 
 
+def test_porter_thomas_cdf_at_fidelity_one_and_a_mixture():
+    # Eq. (fxeb) at F = 1 is the law of x for bitstrings drawn from the exact
+    # output distribution (size-biased Porter-Thomas, x e^-x); at F = 0.3 it
+    # is the 0.3 / 0.7 mixture of exact and uniform draws.  The CDF must
+    # match both empirical laws, vanish at 0, and differentiate to the pdf.
+    psi = _deep_state()
+    n, k = 20, 40000
+    p = np.abs(psi) ** 2
+    rng = np.random.default_rng(11)
+    exact = rng.choice(p.size, size=k, p=p / p.sum())
+    uni = rng.integers(0, p.size, size=k)
+    emp = np.arange(1, k + 1) / k
+    for f, idx in ((1.0, exact), (0.3, np.where(rng.random(k) < 0.3, exact, uni))):
+        x = np.sort((2 ** n) * p[idx])
+        d = np.max(np.abs(emp - xeb.porter_thomas_cdf(x, f)))
+        assert d < 1.63 / np.sqrt(k) + 5e-3, (f, d)  # KS 1 % level plus the finite-n law's deviation
+        # the wrong fidelity is rejected by the same statistic
+        assert np.max(np.abs(emp - xeb.porter_thomas_cdf(x, 0.0 if f > 0.5 else 1.0))) > 0.05
+    assert xeb.porter_thomas_cdf(0.0, 0.7) == 0.0
+    xs = np.linspace(0.05, 8.0, 50)
+    h = 1e-6
+    for f in (0.0, 0.4, 1.0):
+        dcdf = (xeb.porter_thomas_cdf(xs + h, f) - xeb.porter_thomas_cdf(xs - h, f)) / (2 * h)
+        assert np.max(np.abs(dcdf - xeb.porter_thomas_pdf(xs, f))) < 1e-8
+
+
 def test_xeb_of_exact_samples_and_of_uniform_bitstrings():
     psi = _deep_state()
     n, k = 20, 20000
