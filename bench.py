@@ -1,31 +1,44 @@
 """Throughput of the multiple-amplitude contraction on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload grid5x6_m14] [--precision fp32|tf32|bf16x3]
+                    [--workload diamond53_m12] [--precision bf16x3|fp32|tf32]
 
-One step = one full tn_contract over every slice batch of the workload's
-plan: the amplitudes of all its bitstrings (30 qubits, 14 cycles, 4096
-bitstrings, 2^10 slices by default).  Prints one JSON line (rank 0).
+One step = one full tn_contract of the workload's plan: every slice batch,
+the amplitudes of all its bitstrings.  Default workload: the 53-qubit
+diamond (54 sites, one dead), 12 cycles, 8192 bitstrings, contracted with
+the largest per-instance intermediate at 2^26 entries, in the mixed BF16x3
+form with the per-instance power-of-two rescale; FP32 and TF32 run beside
+it on the same plan.  Prints one JSON line (rank 0).
 
-value      amplitudes/s over all ranks: bitstrings x ranks / max-over-ranks
-           device time (CUDA events around each tn_contract; inputs and
-           plan resident in HBM; a 512 MiB write flushes L2 between steps).
-e2e        the same metric through the public API from host data: tn_plan
-           (host), tn_plan_bind (tables up), tn_contract, amplitudes down,
-           timed on the host clock.
-roofline   the kernel family with the largest share of device time,
+value      amplitudes/s over all ranks: bitstrings / max-over-ranks device
+           time (CUDA events around each step on the launching stream;
+           plan and inputs resident in HBM; a 512 MiB write flushes L2
+           between steps).
+e2e        the same metric through the public pipeline from host data:
+           host plan (overlapped), table upload, contraction, amplitudes
+           back to pinned host memory.
+roofline   the kernel family with the largest share of device time:
            algorithmic bytes or flops / its measured launch time, against
-           the measured peak.
-cpu_baseline  the CPU oracle (state vector, complex128) on this host's
-           cores, timed on a bounded sample of its gate passes.
+           the measured peak that binds it.
+peaks      denominators measured in this run on this device: the FP32 FMA
+           rate (tn_fma_probe), the TF32 and FP64 matrix-multiply rates
+           (torch.matmul); HBM and BF16 from the driver's measurements.
+cpu_baseline  the CPU oracle on this host's cores on a bounded sample: the
+           tensor-network contractor on a few of the workload's bitstrings
+           (53 qubits), or the state vector through a prefix of the gates.
 --impl reference times that oracle as the reference arm.
-Multi-GPU (torchrun): each rank contracts its own seeded bitstrings (weak
-scaling, no collective on the data path).
+Multi-GPU (torchrun): strong scaling.  All ranks contract the same
+bitstrings with one plan whose slice batches are split into contiguous
+ranges (the plan is sliced further until it has a batch per rank); the
+k complex128 amplitudes are all-gathered and summed in rank order.
 """
 
 import argparse
+import hashlib
 import json
+import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -39,11 +52,11 @@ import numpy as np  # noqa: E402
 
 METRIC = "amplitudes/sec & TFLOP/s (frac of peak), mixed vs FP32 at stated amp error"
 UNIT = "amplitudes/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+FAMILIES = {0: "k_step_row", 1: "k_step_gemm_simt", 2: "k_step_gemm_tc", 3: "k_chain"}
+TOL = {"fp32": 1e-5, "bf16x3": 1e-3, "tf32": 1e-3}
 
 
-def _peaks():
+def _driver_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
@@ -51,6 +64,55 @@ def _peaks():
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                 "sm_max_mhz": 2070.0}, "fallback"
+
+
+def measure_peaks(torch, tn, stream):
+    """Compute-rate denominators measured now on this device (best of a few
+    runs, CUDA events): FP32 FMA (the library's probe kernel: 152 x 8 blocks
+    of 256 threads, 16 flops per thread per round), TF32 tensor (torch.matmul
+    of 8192^3 FP32 with TF32 allowed: 2 N^3 flops) and FP64 (torch.matmul of
+    4096^3 float64)."""
+    out = {}
+
+    def best(fn, reps):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return min(ts)
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, iters = sms * 8, 1 << 16
+    sink = torch.zeros(blocks, dtype=torch.float32, device="cuda")
+    t = best(lambda: tn.tn_fma_probe(blocks, iters, sink, stream=stream), 5)
+    out["fp32_fma_tflops"] = blocks * 256 * 16 * iters / t / 1e12
+    prev = torch.backends.cuda.matmul.allow_tf32
+    with torch.cuda.stream(stream):
+        n = 8192
+        a = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        b = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        torch.backends.cuda.matmul.allow_tf32 = True
+        t = best(lambda: torch.matmul(a, b), 5)
+        out["tf32_tflops"] = 2 * n ** 3 / t / 1e12
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, b
+        n = 4096
+        a = torch.randn(n, n, device="cuda", dtype=torch.float64)
+        b = torch.randn(n, n, device="cuda", dtype=torch.float64)
+        t = best(lambda: torch.matmul(a, b), 3)
+        out["fp64_tflops"] = 2 * n ** 3 / t / 1e12
+        del a, b
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    out["how"] = ("fp32_fma: tn_fma_probe, %d blocks x 256 threads x 16 x %d flops, best of 5; tf32: torch.matmul "
+                  "8192^3 fp32 with TF32 allowed, best of 5; fp64: torch.matmul 4096^3 float64, best of 3" %
+                  (blocks, iters))
+    return out
 
 
 class Clocks:
@@ -124,35 +186,83 @@ def _dist():
     return world, rank, local
 
 
-def _bits_for_rank(w, rank):
-    from rqc.bitstrings import uniform_bitstrings
-    if rank == 0:
-        return w.bits
-    return uniform_bitstrings(w.circuit.n_qubits, w.bits.shape[0], seed=2000 + w.spec.index + 1000 * rank)
+def _golden_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(ROOT, "tests", "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    return mg
 
 
-def _golden(name):
-    path = os.path.join(ROOT, "tests", "golden", f"{name}_sv.txt")
-    if not os.path.exists(path):
+def reference_values(name, w):
+    """Stored CPU-oracle values of the workload: (rows, complex128 values),
+    rows None for every bitstring (state vector), else the sampled rows
+    (tensor-network oracle); None if nothing is stored or the stored values
+    belong to other inputs."""
+    mg = _golden_module()
+    if os.path.exists(mg.path_for(name)):
+        digest, amps = mg.read(name)
+        rows = None
+    elif os.path.exists(mg.sample_path(name)):
+        rec = mg.read_json(mg.sample_path(name))
+        digest, amps, rows = rec["inputs_sha256"], rec["amplitudes"], rec["rows"]
+    else:
         return None
-    vals = []
-    for line in open(path):
-        if not line.startswith("#"):
-            re_, im_ = line.split()
-            vals.append(complex(float(re_), float(im_)))
-    return np.asarray(vals, np.complex128)
+    if digest != mg.input_digest(w.circuit, w.bits):
+        return None
+    return rows, np.asarray(amps, np.complex128)
 
 
-def cpu_oracle_sample(w, budget_s=20.0):
-    """The complex128 state-vector oracle on a bounded sample: the state is
-    evolved through the first g gates (g grown until ~budget_s of CPU work),
-    and the full run's time is extrapolated per gate pass."""
+def rel_l2_against(got, ref):
+    if ref is None:
+        return None, 0
+    rows, vals = ref
+    g = got if rows is None else got[rows]
+    if len(g) != len(vals):
+        return None, 0
+    return float(np.linalg.norm(g - vals) / np.linalg.norm(vals)), len(vals)
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_oracle_sample(w, budget_s=20.0, max_rows=None):
+    """The CPU oracle as it stands on a bounded sample of the workload.
+
+    Above 30 qubits: the complex128 tensor-network oracle (oracle/tn.py,
+    memo cache over shared sub-networks) contracts the first n bitstrings of
+    the workload, n grown until about budget_s of CPU work; value = n / time
+    (measured, not extrapolated).  Up to 30 qubits: the complex128 state
+    vector through the first g gates, extrapolated per gate pass to the full
+    circuit (value = k / extrapolated time)."""
+    n_q = w.circuit.n_qubits
+    if n_q > 30:
+        from oracle import tn as otn
+        n = 1
+        while True:
+            t0 = time.perf_counter()
+            otn.partial_amplitudes(w.circuit, w.tree.ssa, w.bits[:n], [tuple(int(x) for x in w.struct.edge_wire[e])
+                                                                       for e in w.tree.sliced],
+                                   list(range(1 << len(w.tree.sliced))))
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 3 or n >= w.bits.shape[0] or (max_rows and n >= max_rows):
+                break
+            n = min(w.bits.shape[0], max(n + 1, int(n * min(8.0, budget_s / 2 / max(dt, 1e-3)))))
+            if max_rows:
+                n = min(n, max_rows)
+        return {"value": n / dt, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                "sample": f"tensor-network oracle (complex128, unfused network, memo cache) on the first {n} of the "
+                          f"{w.bits.shape[0]} bitstrings, all {1 << len(w.tree.sliced)} slices, in {dt:.2f} s"}
     from oracle import sv as osv
     from rqc.circuit import Circuit
     total = len(w.circuit.gates)
     g = 8
     while True:
-        c = Circuit(n_qubits=w.circuit.n_qubits, gates=w.circuit.gates[:g])
+        c = Circuit(n_qubits=n_q, gates=w.circuit.gates[:g])
         t0 = time.perf_counter()
         osv.state(c)
         dt = time.perf_counter() - t0
@@ -162,23 +272,118 @@ def cpu_oracle_sample(w, budget_s=20.0):
     t_full = dt * (total + 1) / (g + 1)
     k = w.bits.shape[0]
     return {"value": k / t_full, "unit": UNIT, "cores": osv.threads(), "kind": "oracle",
-            "sample": f"state-vector oracle (complex128, 2^{w.circuit.n_qubits} amplitudes) through the first "
-                      f"{g} of {total} gates in {dt:.2f} s, extrapolated per gate pass to {t_full:.1f} s "
-                      f"for the {k} bitstrings"}
+            "sample": f"state-vector oracle (complex128, 2^{n_q} amplitudes) through the first {g} of {total} gates "
+                      f"in {dt:.2f} s, extrapolated per gate pass to {t_full:.1f} s for the {k} bitstrings"}
 
 
-def measure_correlated(w, precision, torch, tn, stream, ws, limit, rows=256, n_open=4, reps=3):
+def traffic_record(kernel):
+    """DRAM traffic over algorithmic bytes of `kernel` from the committed ncu
+    summary profiles/<kernel>_traffic_small_case.md, if that summary was
+    taken on the current source of the kernel (its sha256 line matches);
+    else None.  The summary's ratio comes from a small case of the same
+    kernel (the bench workload is too large for a counter capture)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic_small_case.md")
+    src = os.path.join(ROOT, "paper_2212_04749_gb300", "csrc", "gemm_tc.cu" if kernel == "k_step_gemm_tc" else
+                       "kernels.cu")
+    try:
+        text = open(path).read()
+        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m = re.search(r"traffic_over_algorithmic:\s*([0-9.]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h or h.group(1) != cur:
+        return None
+    return float(m.group(1))
+
+
+def family_breakdown(steps, step_ms, kernels):
+    fam = {}
+    for s, st in enumerate(steps):
+        f = int(kernels[s]) if kernels is not None else 0
+        r = fam.setdefault(f, {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "launches": 0, "steps": []})
+        r["ms"] += float(step_ms[s])
+        r["bytes"] += st["bytes"] * st["runs"]
+        r["flops"] += st["flops"] * st["runs"]
+        r["launches"] += int(st["runs"])
+        r["steps"].append(s)
+    return fam
+
+
+def compute_peak(family, precision, peaks):
+    """Compute-rate peak (TFLOP/s, algorithmic) of a kernel family at a
+    precision and its source: tensor-core BF16x3 = measured BF16 (sustained)
+    / 3 products; TF32 = measured TF32; SIMT = measured FP32 FMA."""
+    if family == 2:
+        if precision == "bf16x3":
+            return peaks["bf16_tflops_sustained"] / 3.0, "measured bf16 sustained / 3"
+        return peaks.get("tf32_tflops"), "measured tf32"
+    if family in (0, 1, 3):
+        return peaks.get("fp32_fma_tflops"), "measured fp32 fma"
+    return None, None
+
+
+def roofline_of(steps, step_ms, kernels, precision, peaks):
+    """Roofline of the dominant kernel family, the per-step bound fraction
+    and the whole path's bound fraction.  A step's bound time is the longer
+    of its algorithmic bytes at the HBM peak and its flops at its family's
+    compute peak; a family is reported HBM-bound when its summed bytes at
+    the HBM peak take longer than its summed flops at the compute peak."""
+    fam = family_breakdown(steps, step_ms, kernels)
+    hbm = peaks["hbm_gbs"]
+
+    def bound_time(s, st, f):
+        tb = st["bytes"] * st["runs"] / (hbm * 1e9)
+        pk, _ = compute_peak(f, precision, peaks)
+        if pk and f in (1, 2):
+            tb = max(tb, st["flops"] * st["runs"] / (pk * 1e12))
+        return tb
+
+    total_ms = sum(r["ms"] for r in fam.values())
+    dom = max(fam, key=lambda f: fam[f]["ms"])
+    r = fam[dom]
+    sec = r["ms"] / 1e3
+    pk, pk_src = compute_peak(dom, precision, peaks)
+    t_hbm = r["bytes"] / (hbm * 1e9)
+    t_cmp = r["flops"] / (pk * 1e12) if pk and dom in (1, 2) else 0.0
+    if t_hbm >= t_cmp:
+        roof = {"bound": "hbm", "achieved": r["bytes"] / sec / 1e9, "peak": hbm, "unit": "GB/s"}
+        if pk:
+            roof["tensor_tflops" if dom == 2 else "alu_tflops"] = r["flops"] / sec / 1e12
+            roof["tensor_frac" if dom == 2 else "alu_frac"] = r["flops"] / sec / 1e12 / pk
+    else:
+        roof = {"bound": "tensor" if dom == 2 else "alu", "achieved": r["flops"] / sec / 1e12, "peak": pk,
+                "unit": "TFLOP/s", "peak_source": pk_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["step_bound_frac"] = sum(bound_time(s, steps[s], dom) for s in r["steps"]) / sec
+    roof["kernel"] = FAMILIES[dom]
+    roof["launches_per_step"] = r["launches"]
+    roof["algorithmic_bytes_per_launch"] = r["bytes"] / max(r["launches"], 1)
+    roof["share_of_step_time"] = r["ms"] / max(total_ms, 1e-12)
+    roof["per_kernel_ms"] = {FAMILIES[f]: fam[f]["ms"] for f in fam}
+    path_bound = sum(bound_time(s, steps[s], f) for f in fam for s in fam[f]["steps"])
+    # HBM fraction of every other family (the row kernel: bandwidth steps)
+    others = {}
+    for f, rr in fam.items():
+        if f == dom or rr["ms"] <= 0:
+            continue
+        others[FAMILIES[f]] = {"ms": rr["ms"], "hbm_frac": rr["bytes"] / (rr["ms"] / 1e3) / 1e9 / hbm,
+                               "launches": rr["launches"]}
+    roof["other_families"] = others
+    return roof, path_bound / (total_ms / 1e3), dom
+
+
+def measure_correlated(w, precision, torch, tn, stream, ws, limit, rescale, rows=256, n_open=4, reps=3):
     """Correlated batches (SM Sec. II): `rows` of the workload's bitstrings
     with their last `n_open` qubits left open, so that one contraction
-    yields rows x 2^n_open amplitudes (the same count as the headline
-    batch when rows x 2^n_open = k), then one perfect sample per row
+    yields rows x 2^n_open amplitudes, then one perfect sample per row
     (tn_sample_completions, uniform numbers drawn on the host, seed 5).
     CUDA-event time of the contraction (the plan's rule configuration)
     and of the sampling."""
     n = w.circuit.n_qubits
     oq = list(range(n - n_open, n))
     p = tn.Plan(w.circuit, w.bits[:rows], w.tree.ssa, w.tree.sliced, workspace_limit=min(limit, ws.numel()),
-                open_qubits=oq)
+                open_qubits=oq, rescale=rescale)
     if p.info["workspace_bytes"] > ws.numel():
         return {"skipped": f"needs {p.info['workspace_bytes'] / 2**30:.1f} GiB"}
     p.tn_plan_bind(ws, stream=stream)
@@ -206,7 +411,7 @@ def measure_correlated(w, precision, torch, tn, stream, ws, limit, rows=256, n_o
             "workspace_gib": p.info["workspace_bytes"] / 2 ** 30}
 
 
-def measure_chain(name, precision, torch, tn, stream, fuse_bits, batches=4):
+def measure_chain(name, precision, torch, tn, stream, fuse_bits, peaks, batches=4):
     """Fused chains (tn_options.fuse) against the unfused steps on a workload
     whose heaviest chain is worth fusing: per-step CUDA-event times over the
     first `batches` slice batches, the chain kernel's algorithmic bytes (A_1
@@ -214,7 +419,6 @@ def measure_chain(name, precision, torch, tn, stream, fuse_bits, batches=4):
     HBM roofline."""
     from rqc import make_workload
     w = make_workload(name)
-    peaks, _ = _peaks()
     plans = {f: tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, workspace_limit=200 << 30, fuse=f,
                         fuse_max_bits=fuse_bits) for f in (0, 1)}
     need = max(p.info["workspace_bytes"] for p in plans.values())
@@ -239,11 +443,12 @@ def measure_chain(name, precision, torch, tn, stream, fuse_bits, batches=4):
     for i, s in enumerate(st1):
         if s["chain"] >= 0:
             chains.setdefault(s["chain"], []).append(i)
+    if not chains:
+        return {"workload": name, "chains": 0}
     best = max(chains.values(), key=lambda ids: sum(ms0[i] for i in ids))
     t_unfused = float(sum(ms0[i] for i in best))
     t_fused = float(ms1[best[-1]])
     first, last = st1[best[0]], st1[best[-1]]
-    # algorithmic bytes per pass: A_1 + every B_j + C_L
     a_bytes = 8.0 * first["n_inst_a"] * 2.0 ** first["rank_a"]
     b_bytes = sum(8.0 * st1[i]["n_inst_b"] * 2.0 ** st1[i]["rank_b"] for i in best)
     c_bytes = 8.0 * last["n_inst"] * 2.0 ** (last["mb"] + last["nb"])
@@ -260,30 +465,51 @@ def measure_chain(name, precision, torch, tn, stream, fuse_bits, batches=4):
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle as it stands on this host's cores,
+    each step a bounded sample of the workload (rank 0 only)."""
     if rank != 0:
         return 0
     from rqc import make_workload
     w = make_workload(args.workload)
-    vals = []
     for _ in range(args.warmup):
-        cpu_oracle_sample(w, budget_s=3.0)
+        cpu_oracle_sample(w, budget_s=min(3.0, args.ref_budget), max_rows=1)
+    vals, times = [], []
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         vals.append(cpu_oracle_sample(w, budget_s=args.ref_budget))
+        times.append(time.perf_counter() - t0)
     v = statistics.median(x["value"] for x in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.bits.shape[0] / v,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[-1]["cores"], "kind": "oracle",
-                             "sample": vals[-1]["sample"]},
+                             "sample": "each step: " + vals[-1]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+def sliced_for_world(w, world):
+    """Sliced edges of the plan all ranks share: the workload's own, plus
+    (for world > 1) further edges chosen by the greedy slicer until the
+    slices can be split into at least one batch per rank."""
+    sl = list(w.tree.sliced)
+    need = max(0, math.ceil(math.log2(world))) if world > 1 else 0
+    if len(sl) >= need:
+        return sl
+    from rqc.tree import choose_slices
+    extra = choose_slices(w.struct, w.tree, w.bits.shape[0], n_sliced=need)
+    for e in extra:
+        if e not in sl and len(sl) < need:
+            sl.append(e)
+    return sorted(sl)
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2212_04749_gb300 import builder, tn
+    from paper_2212_04749_gb300.multi import batch_range
     from rqc import make_workload
 
     builder.build()
@@ -297,20 +523,56 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = make_workload(args.workload)
-    bits = _bits_for_rank(w, rank)
+    bits = w.bits if not args.rows else w.bits[:args.rows]
     k = bits.shape[0]
+    sliced = sliced_for_world(w, world)
     stream = torch.cuda.current_stream()
+    dpeaks, dpeak_src = _driver_peaks()
+    peaks = dict(dpeaks)
+    live = measure_peaks(torch, tn, stream) if rank == 0 and args.peaks else {}
+    peaks.update({kk: v for kk, v in live.items() if kk != "how"})
     free, _ = torch.cuda.mem_get_info()
     limit = min(int(args.ws_gib * 2 ** 30), int(free * 0.8))
+    popts = dict(workspace_limit=limit, fuse=args.fuse, fuse_max_bits=args.fuse_bits, rescale=args.rescale)
+    if world > 1:
+        # one slice per batch so the batches split over the ranks
+        popts["slice_batch_log2"] = max(0, len(sliced) - math.ceil(math.log2(world)))
     t0 = time.perf_counter()
-    plan = tn.Plan(w.circuit, bits, w.tree.ssa, w.tree.sliced, workspace_limit=limit, fuse=args.fuse,
-                   fuse_max_bits=args.fuse_bits, rescale=args.rescale)
+    plan = tn.Plan(w.circuit, bits, w.tree.ssa, sliced, **popts)
     t_plan = time.perf_counter() - t0
     info = plan.info
+    lo, hi = batch_range(info["n_batches"], rank, world)
     ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
     plan.tn_plan_bind(ws, stream=stream)
     amps = torch.zeros(2 * k, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    gathered = [torch.empty_like(amps) for _ in range(world)] if world > 1 else None
+    total = torch.empty_like(amps)
+
+    def reduce_in_rank_order():
+        # the one exchange of the path: every rank's k complex128 partial
+        # sums, added in rank order (deterministic)
+        if dist is None:
+            return amps
+        dist.all_gather(gathered, amps)
+        total.copy_(gathered[0])
+        for g in gathered[1:]:
+            total.add_(g)
+        return total
+
+    def one_step(prec, profile=False):
+        amps.zero_()
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        plan.tn_plan_profile(profile)
+        e0.record(stream)
+        if hi > lo:
+            plan.tn_contract(amps, prec, lo, hi, stream=stream)
+        reduce_in_rank_order()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
 
     def select(prec):
         """Configure every step for `prec`; returns the selection record."""
@@ -331,18 +593,17 @@ def run_ours(args, world, rank, local):
         return {"mode": args.select, "rule_ms": rule_ms, "selection_s": sel_s,
                 "configs": np.bincount(cfg, minlength=tn.TN_NCONFIG).tolist()}
 
-    def one_step(prec, profile=False):
-        amps.zero_()
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        plan.tn_plan_profile(profile)
-        e0.record(stream)
-        plan.tn_contract(amps, prec, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1)
+    def profile_steps(prec, runs=2):
+        step_ms = np.zeros(info["n_steps"])
+        kernels = None
+        for _ in range(runs):
+            one_step(prec, profile=True)
+            ms, kernels = plan.tn_plan_step_times()
+            step_ms += ms / runs
+        plan.tn_plan_profile(False)
+        return step_ms, kernels
 
+    ref = reference_values(args.workload, w) if rank == 0 and not args.rows else None
     selection = select(args.precision)
     for _ in range(args.warmup):
         one_step(args.precision)
@@ -367,61 +628,19 @@ def run_ours(args, world, rank, local):
         tt = torch.tensor([mean_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = tt.item()
-    value = k * world / (t_max / 1000.0)
-    # per-step device times: separate runs with CUDA events around every
-    # launch (no graph replay), averaged
-    prof_runs = 2
-    step_ms = np.zeros(info["n_steps"])
-    kernels = None
-    for _ in range(prof_runs):
-        one_step(args.precision, profile=True)
-        ms, kernels = plan.tn_plan_step_times()
-        step_ms += ms / prof_runs
-    plan.tn_plan_profile(False)
+    value = k / (t_max / 1000.0)
+    got = reduce_in_rank_order().cpu().numpy().view(np.complex128).copy()
+    err, n_cmp = rel_l2_against(got, ref)
 
-    # linear XEB of this run's amplitudes (FP64 reduction on the device) and
-    # the maximum-likelihood fidelity under Eq. (fxeb) with error bars (the
-    # stand-in bitstrings are uniform: both near 0)
-    xeb_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
-    tn.tn_xeb(amps, k, w.circuit.n_qubits, xeb_dev, stream=stream)
-    torch.cuda.synchronize()
-    xeb = float(xeb_dev.item())
-    from paper_2212_04749_gb300.xeb import porter_thomas_fit
-    xeb_fit = porter_thomas_fit(amps, k, w.circuit.n_qubits, stream=stream)
-
-    # accuracy of this run against the stored oracle values
-    got = amps.cpu().numpy().view(np.complex128)
-    ref = _golden(args.workload) if rank == 0 else None
-    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref)) if ref is not None and len(ref) == k else None
-
-    selection["tuned_ms"] = t_max
-
-    # the other forms on the same workload (each with its own configuration)
-    others = {}
-    if args.mixed and rank == 0:
-        for prec in ("fp32", "bf16x3", "tf32"):
-            if prec == args.precision:
-                continue
-            sel2 = select(prec)
-            one_step(prec)
-            ts = [one_step(prec) for _ in range(max(2, args.steps // 2))]
-            g2 = amps.cpu().numpy().view(np.complex128)
-            e2 = float(np.linalg.norm(g2 - ref) / np.linalg.norm(ref)) if ref is not None else None
-            others[prec] = {"amplitudes_per_s": k / (statistics.mean(ts) / 1000.0), "ms_per_step": statistics.mean(ts),
-                            "rel_l2_vs_oracle": e2, "selection": sel2}
-        select(args.precision)  # back to the headline form's configuration
-
-    # roofline of the dominant kernel family
-    peaks, peak_src = _peaks()
+    step_ms, kernels = profile_steps(args.precision)
     steps = plan.tn_plan_steps()
-    fam_names = {0: "k_step_row", 1: "k_step_gemm_simt", 2: "k_step_gemm_tc", 3: "k_chain"}
-    fam_ms, fam_bytes, fam_flops, fam_launch = {}, {}, {}, {}
-    for s, st in enumerate(steps):
-        f = int(kernels[s]) if kernels is not None else 0
-        fam_ms[f] = fam_ms.get(f, 0.0) + step_ms[s]
-        fam_bytes[f] = fam_bytes.get(f, 0.0) + st["bytes"] * st["runs"]
-        fam_flops[f] = fam_flops.get(f, 0.0) + st["flops"] * st["runs"]
-        fam_launch[f] = fam_launch.get(f, 0) + int(st["runs"])
+    roof, path_bound_frac, dom = roofline_of(steps, step_ms, kernels, args.precision, peaks)
+    ratio = traffic_record(roof["kernel"])
+    roof["traffic"] = ratio * roof["algorithmic_bytes_per_launch"] if ratio else None
+    roof["traffic_over_algorithmic"] = ratio
+    roof["traffic_source"] = ("ncu dram__bytes_read+write of a small case of the same kernel source, scaled by "
+                              "algorithmic bytes" if ratio else "no capture of the current kernel source")
+    roof["peak_source"] = roof.get("peak_source", dpeak_src)
     if args.dump_steps and rank == 0:
         rows = []
         cfgs = plan.tn_plan_get_configs()
@@ -433,76 +652,50 @@ def run_ours(args, world, rank, local):
             rows.append(r)
         with open(args.dump_steps, "w") as f:
             json.dump({"precision": args.precision, "workload": args.workload, "steps": rows}, f)
-    dom = max(fam_ms, key=fam_ms.get)
-    sec = fam_ms[dom] / 1000.0
-    if dom in (0, 3):
-        ach = fam_bytes[dom] / sec / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-    elif dom == 1:
-        pk = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach = fam_flops[dom] / sec / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
-    else:
-        # tensor-core steps: bound by the tensor pipe or by HBM, whichever
-        # takes longer for the family's algorithmic flops and bytes
-        base = peaks["bf16_tflops_sustained"]
-        pk = base / 3.0 if args.precision == "bf16x3" else base * (1.1 / 2.25)
-        ach = fam_flops[dom] / sec / 1e12
-        t_tensor = fam_flops[dom] / (pk * 1e12)
-        t_hbm = fam_bytes[dom] / (peaks["hbm_gbs"] * 1e9)
-        if t_hbm >= t_tensor:
-            roof = {"bound": "hbm", "achieved": fam_bytes[dom] / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "tensor_tflops": ach, "tensor_frac": ach / pk}
-        else:
-            roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    # per-step bound: each of the family's steps takes at least the longer of
-    # its flops at the compute peak and its bytes at the HBM peak
-    t_bound = 0.0
-    for s, st in enumerate(steps):
-        if (int(kernels[s]) if kernels is not None else 0) != dom:
-            continue
-        tb = st["bytes"] * st["runs"] / (peaks["hbm_gbs"] * 1e9)
-        if dom == 1:
-            tb = max(tb, st["flops"] * st["runs"] / (SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6))
-        elif dom == 2:
-            base = peaks["bf16_tflops_sustained"]
-            pk2 = base / 3.0 if args.precision == "bf16x3" else base * (1.1 / 2.25)
-            tb = max(tb, st["flops"] * st["runs"] / (pk2 * 1e12))
-        t_bound += tb
-    roof["step_bound_frac"] = t_bound / sec
-    # the whole path: every step's bound (its bytes at the HBM peak, or its
-    # flops at its kernel's compute peak when longer) over the step's time
-    t_path = 0.0
-    for s, st in enumerate(steps):
-        fam = int(kernels[s]) if kernels is not None else 0
-        tb = st["bytes"] * st["runs"] / (peaks["hbm_gbs"] * 1e9)
-        if fam == 1:
-            tb = max(tb, st["flops"] * st["runs"] / (SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6))
-        elif fam == 2:
-            base = peaks["bf16_tflops_sustained"]
-            pk2 = base / 3.0 if args.precision == "bf16x3" else base * (1.1 / 2.25)
-            tb = max(tb, st["flops"] * st["runs"] / (pk2 * 1e12))
-        t_path += tb
-    path_bound_frac = t_path / (sum(fam_ms.values()) / 1000.0)
-    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-    # of the tensor-core launches of one timed step of this workload, from
-    # one ncu capture of the current kernel build (815.0 GB over 52
-    # launches: 1.107 x the algorithmic bytes); unknown for other cases
-    measured_traffic = {("grid5x6_m14", "bf16x3", "k_step_gemm_tc"): (815.0e9 / 52, 1.107)}
-    mt = measured_traffic.get((args.workload, args.precision, fam_names[dom]))
-    roof["traffic"] = mt[0] if mt else None
-    if mt:
-        roof["traffic_over_algorithmic"] = mt[1]
-    roof["kernel"] = fam_names[dom]
-    roof["launches_per_step"] = fam_launch[dom]
-    roof["share_of_step_time"] = fam_ms[dom] / max(sum(fam_ms.values()), 1e-12)
-    roof["peak_source"] = peak_src
-    roof["per_kernel_ms"] = {fam_names[f]: fam_ms[f] for f in fam_ms}
+
+    # linear XEB of this run's amplitudes (FP64 reduction on the device) and
+    # the maximum-likelihood fidelity under Eq. (fxeb) with error bars (the
+    # stand-in bitstrings are uniform: both near 0)
+    xeb = xeb_fit = None
+    if rank == 0:
+        dev = torch.from_numpy(got.view(np.float64).copy()).cuda()
+        xeb_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+        tn.tn_xeb(dev, k, w.circuit.n_qubits, xeb_dev, stream=stream)
+        torch.cuda.synchronize()
+        xeb = float(xeb_dev.item())
+        from paper_2212_04749_gb300.xeb import porter_thomas_fit
+        xeb_fit = porter_thomas_fit(dev, k, w.circuit.n_qubits, stream=stream)
+
+    selection["tuned_ms"] = t_max
+
+    # the other forms on the same plan (each with its own configuration)
+    others = {}
+    if args.mixed:
+        for prec in ("fp32", "tf32", "bf16x3"):
+            if prec == args.precision:
+                continue
+            sel2 = select(prec)
+            one_step(prec)
+            ts = [one_step(prec) for _ in range(max(2, args.steps // 2))]
+            tmx = statistics.mean(ts)
+            if dist is not None:
+                tt = torch.tensor([tmx], device="cuda")
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+                tmx = tt.item()
+            g2 = reduce_in_rank_order().cpu().numpy().view(np.complex128).copy()
+            e2, _ = rel_l2_against(g2, ref)
+            sm2, kn2 = profile_steps(prec)
+            roof2, pbf2, _ = roofline_of(steps, sm2, kn2, prec, peaks)
+            others[prec] = {"amplitudes_per_s": k / (tmx / 1000.0), "ms_per_step": tmx,
+                            "tflops_algorithmic": info["flops_ma"] / (tmx / 1000.0) / 1e12,
+                            "rel_l2_vs_oracle": e2, "tolerance": TOL[prec],
+                            "within_tolerance": (e2 <= TOL[prec]) if e2 is not None else None,
+                            "path_bound_frac": pbf2, "roofline": roof2, "selection": sel2}
+        select(args.precision)  # back to the headline form's configuration
 
     # end to end through the public API from host buffers
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and world == 1:
         # successive batches through the public pipeline: each batch is
         # planned on the host (overlapped with the previous batch's device
         # work), its tables uploaded (host to device), contracted, and its
@@ -512,27 +705,28 @@ def run_ours(args, world, rank, local):
         cfg_now = plan.tn_plan_get_configs()
         marks = []
         ws_b = torch.empty_like(ws)  # second workspace: the next batch binds while this one runs
-        for _i, _a in contract_batches(w.circuit, [bits] * (args.e2e_steps + 1), w.tree.ssa, w.tree.sliced,
-                                       args.precision, (ws, ws_b), stream=stream, configs=cfg_now,
-                                       workspace_limit=limit, fuse=args.fuse, fuse_max_bits=args.fuse_bits,
-                                       rescale=args.rescale):
+        for _i, _a in contract_batches(w.circuit, [bits] * (args.e2e_steps + 1), w.tree.ssa, sliced,
+                                       args.precision, (ws, ws_b), stream=stream, configs=cfg_now, **popts):
             marks.append(time.perf_counter())
         del ws_b
         torch.cuda.empty_cache()  # the later measurements size themselves by free device memory
         plan.tn_plan_bind(ws, stream=stream)
         e2e_s = (marks[-1] - marks[0]) / args.e2e_steps
-        e2e = {"value": k * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(info["upload_bytes"]),
+        e2e = {"value": k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(info["upload_bytes"]),
                "d2h_bytes_per_step": int(16 * k), "host_plan_s": t_plan,
                "planning": "overlapped", "table_upload": "overlapped (two workspaces)"}
 
     correlated = None
-    if rank == 0 and args.correlated:
-        correlated = measure_correlated(w, args.precision, torch, tn, stream, ws, limit)
+    if rank == 0 and world == 1 and args.correlated:
+        correlated = measure_correlated(w, args.precision, torch, tn, stream, ws, limit, args.rescale)
         plan.tn_plan_bind(ws, stream=stream)
 
     chain = None
-    if rank == 0 and args.chain_workload:
-        chain = measure_chain(args.chain_workload, args.precision, torch, tn, stream, args.fuse_bits)
+    if rank == 0 and world == 1 and args.chain_workload:
+        plan._ws = None  # the headline plan is done: its workspace goes back to the allocator
+        del ws
+        torch.cuda.empty_cache()
+        chain = measure_chain(args.chain_workload, args.precision, torch, tn, stream, args.fuse_bits, peaks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -541,12 +735,12 @@ def run_ours(args, world, rank, local):
     tflops = info["flops_ma"] / (t_max / 1000.0) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "fp32", "tf32": "tf32", "bf16x3": "bf16x3"}[args.precision],
-        "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": args.workload, "qubits": w.circuit.n_qubits, "cycles": w.spec.cycles,
-                   "bitstrings": k, "sliced_edges": len(w.tree.sliced), "slices": 2 ** len(w.tree.sliced),
-                   "slice_batch": 2 ** info["slice_batch_log2"], "precision": args.precision,
+                   "bitstrings": k, "rows_of_workload": args.rows or None, "sliced_edges": len(sliced), "slices": 2 ** len(sliced),
+                   "slice_batch": 2 ** info["slice_batch_log2"], "batches_per_rank": hi - lo,
+                   "precision": args.precision,
                    "l2": "512 MiB write between steps; intermediates exceed L2",
                    "flops_eq1": info["flops_ma"], "flops_single_amplitude_x_k": info["flops_sa"],
                    "bytes_algorithmic": info["bytes_min"], "max_rank": info["max_rank"],
@@ -554,13 +748,18 @@ def run_ours(args, world, rank, local):
         "tflops_algorithmic": tflops,
         "path_bound_frac": path_bound_frac,
         "rel_l2_vs_oracle": err,
+        "oracle_amplitudes_compared": n_cmp,
+        "tolerance": TOL[args.precision],
         "xeb": xeb,
         "xeb_fit": xeb_fit,
-        "correlated_batches": correlated,
         "other_forms": others or None,
+        "mixed_over_fp32": (value / others["fp32"]["amplitudes_per_s"]) if "fp32" in others else None,
         "config_selection": selection,
         "roofline": roof,
+        "peaks": {"hbm_gbs": peaks["hbm_gbs"], "bf16_tflops_sustained": peaks["bf16_tflops_sustained"],
+                  "bf16_source": dpeak_src, **live},
         "cpu_baseline": cpu,
+        "correlated_batches": correlated,
         "fused_chain": chain,
         "e2e": e2e,
         "gpu_launches": int(info["launches_per_call"]) * args.steps,
@@ -579,24 +778,29 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="grid5x6_m14")
+    ap.add_argument("--workload", default="diamond53_m12")
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16x3"], default="bf16x3",
                     help="headline form (default: the mixed BF16x3 split form); the others run beside it")
     ap.add_argument("--select", choices=["autotune", "model", "rule"], default="autotune",
                     help="per-step kernel configuration: exhaustive autotuner, cost model (--model), or the plan's rule")
     ap.add_argument("--model", default=None, help="cost-model parameters (npy) for --select model")
-    ap.add_argument("--ws-gib", type=float, default=64.0)
+    ap.add_argument("--ws-gib", type=float, default=120.0)
+    ap.add_argument("--rows", type=int, default=0,
+                    help="contract only the first ROWS bitstrings of the workload with its own tree (a smaller "
+                         "case of the same step shapes, e.g. for profiler captures); 0: all")
+    ap.add_argument("--no-peaks", dest="peaks", action="store_false",
+                    help="skip the live FP32/TF32/FP64 peak measurements")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--ref-budget", type=float, default=20.0,
+                    help="seconds of CPU work per oracle sample (cpu_baseline; per step of --impl reference)")
     ap.add_argument("--dump-steps", default=None, help="write per-step features and times (JSON) here")
     ap.add_argument("--fuse", type=int, choices=[0, 1], default=1, help="fused chains of small-operand steps")
     ap.add_argument("--correlated", type=int, choices=[0, 1], default=1,
                     help="also time correlated batches (open qubits) and perfect-sample extraction")
-    ap.add_argument("--rescale", type=int, choices=[0, 1], default=0,
-                    help="per-instance power-of-two rescaling (a safety net of this library, not part of the "
-                         "paper's method; off: the paper's plain arithmetic)")
+    ap.add_argument("--rescale", type=int, choices=[0, 1], default=1,
+                    help="per-instance power-of-two rescaling (on by default; 0: the paper's plain arithmetic)")
     ap.add_argument("--fuse-bits", type=int, default=9, help="d^t: largest fused-chain tile, 2^d^t entries")
     ap.add_argument("--chain-workload", default="grid6x7_m10",
                     help="workload whose heaviest fused chain is timed against the unfused steps ('' to skip)")

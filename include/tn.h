@@ -172,6 +172,16 @@ typedef struct {
 
 int tn_plan_steps(tn_plan_t plan, tn_step_info *steps, int32_t n);
 
+/* The slices of slice batch `batch` (main text: first-level slicing sums
+ * the partial amplitudes of all 2^n_sliced assignments of the sliced bond
+ * indices; SM Sec. IV.B).  tn_contract takes batch ranges: batch b holds
+ * 2^slice_batch_log2 slices, whose ids s (sliced_edges[j] = (s >> j) & 1)
+ * this call writes to slice_ids (host, n >= 2^slice_batch_log2 entries) in
+ * the order the batch's pass computes them.  Over b in [0, n_batches) every
+ * slice id appears exactly once.  Host only.  TN_EINVAL for a batch outside
+ * [0, n_batches) or too small a buffer. */
+int tn_plan_batch_slices(tn_plan_t plan, int64_t batch, int64_t *slice_ids, int64_t n);
+
 /* Bind caller-owned device memory (>= info.workspace_bytes, 256-byte
  * aligned) and upload the plan's tables and gate tensors into it on
  * `stream`.  Must precede tn_contract*. */
@@ -367,6 +377,17 @@ int tn_plan_check(tn_plan_t plan, void *stream);
 int tn_plan_profile(tn_plan_t plan, int enable);
 int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t *kernel, int32_t n);
 
+/* FP32 fused multiply-add throughput probe (no counterpart in the paper: it
+ * measures the denominator of the FP32 form's roofline, the rate of the
+ * CUDA cores' FP32 FMA pipes on this device).  Launches `blocks` blocks of
+ * 256 threads; every thread performs 16 * iters FP32 flops (8 independent
+ * FMA chains), so one launch performs blocks * 256 * 16 * iters flops; the
+ * caller times it with events on `stream`.  out_dev: device, >= blocks
+ * floats, written only in a case the probe's values never reach (it keeps
+ * the work from being optimised away).  TN_EINVAL for blocks outside
+ * (0, 2^31), iters < 0 or a null buffer; asynchronous. */
+int tn_fma_probe(int64_t blocks, int64_t iters, float *out_dev, void *stream);
+
 /* Contraction for callers that cannot allocate device memory.  No
  * counterpart in the paper.  Some callers cannot call cudaMalloc or take
  * device memory from an allocator: code embedded in a host application
@@ -377,8 +398,9 @@ int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t *kernel, int32_t n);
  * (TN_STATIC_SCRATCH_BYTES, 64 MiB, reserved on every device that loads the
  * library until the process exits).  It calls no cudaMalloc, cudaFree or
  * other allocating routine.
- *   amps: caller-owned device complex128 buffer of k entries, accumulated
- *         into as in tn_contract.
+ *   amps: caller-owned device complex128 buffer of k x amps_per_row
+ *         entries (tn_plan_info; amps_per_row = 2^|open qubits|, 1 without
+ *         tn_options.open_mask), accumulated into as in tn_contract.
  *   Plans whose tn_plan_info.workspace_bytes exceed TN_STATIC_SCRATCH_BYTES
  *   are rejected with TN_ENOMEM and a message giving both sizes.
  * The first call on a device looks up the array's device address (once per
@@ -386,8 +408,8 @@ int tn_plan_step_times(tn_plan_t plan, double *ms, int32_t *kernel, int32_t n);
  * capture.  Every call uploads the plan's tables into the array and clears
  * what must start at zero, because the array keeps the last call's
  * contents; calls that overlap on the GPU (other streams, other threads)
- * share the array and race.  A plan's own tn_plan_bind binding is left as it
- * was. */
+ * share the array and race.  A plan's own tn_plan_bind binding, and the CUDA
+ * graphs tn_contract captured for it, are left as they were. */
 #define TN_STATIC_SCRATCH_BYTES (64ll << 20)
 int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream);
 

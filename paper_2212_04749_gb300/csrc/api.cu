@@ -463,6 +463,22 @@ int tn_plan_steps(tn_plan_t plan, tn_step_info *out, int32_t n) {
     return TN_OK;
 }
 
+int tn_plan_batch_slices(tn_plan_t plan, int64_t batch, int64_t *slice_ids, int64_t n) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_batch_slices: null plan");
+    const tnp::Plan &P = reinterpret_cast<PlanObj *>(plan)->P;
+    const int64_t per = int64_t(1) << P.m_low;
+    if (batch < 0 || batch >= P.n_batches) return set_err(TN_EINVAL, "tn_plan_batch_slices: batch outside [0, n_batches)");
+    if (n < per || !slice_ids)
+        return set_err(TN_EINVAL, "tn_plan_batch_slices: need room for " + std::to_string(per) + " slice ids");
+    for (int64_t sigma = 0; sigma < per; ++sigma) {
+        const int64_t v = batch * per + sigma;  // internal slice index
+        int64_t ext = 0;
+        for (size_t t = 0; t < P.perm.size(); ++t) ext |= ((v >> t) & 1) << P.perm[t];
+        slice_ids[sigma] = ext;
+    }
+    return TN_OK;
+}
+
 int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream) {
     if (!plan) return set_err(TN_EINVAL, "tn_plan_bind: null plan");
     PlanObj *o = reinterpret_cast<PlanObj *>(plan);
@@ -632,6 +648,14 @@ int tn_pt_histogram(const double *amps, int64_t k, int32_t n_qubits, double x_ma
     return TN_OK;
 }
 
+int tn_fma_probe(int64_t blocks, int64_t iters, float *out_dev, void *stream) {
+    if (blocks <= 0 || blocks > 0x7fffffffLL || iters < 0 || !out_dev)
+        return set_err(TN_EINVAL, "tn_fma_probe: need 0 < blocks < 2^31, iters >= 0 and an output buffer");
+    CU(tnk::launch_fma_probe(blocks, iters, out_dev, reinterpret_cast<cudaStream_t>(stream)));
+    g_err.clear();
+    return TN_OK;
+}
+
 int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream) {
     if (!plan) return set_err(TN_EINVAL, "tn_contract_static: null plan");
     PlanObj *o = reinterpret_cast<PlanObj *>(plan);
@@ -646,6 +670,10 @@ int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream
     const size_t prev_bytes = o->ws_bytes;
     int32_t *prev_flag = o->err_flag;
     const int32_t prev_graphs = o->P.opt.graphs;
+    // graphs captured for the caller's own binding stay valid once it is
+    // restored: keep them out of the re-bind's reach
+    std::map<PlanObj::GraphKey, cudaGraphExec_t> kept;
+    kept.swap(o->graphs);
     o->P.opt.graphs = 0;  // every call re-uploads the tables: nothing to replay
     int rc = tn_plan_bind(plan, scratch, (size_t)TN_STATIC_SCRATCH_BYTES, stream);
     if (rc == TN_OK) rc = tn_contract(plan, precision, 0, o->P.n_batches, amps, stream);
@@ -660,6 +688,8 @@ int tn_contract_static(tn_plan_t plan, int precision, double *amps, void *stream
         o->desc.clear();
         o->amap.clear();
     }
+    o->drop_graphs();  // none are captured while graphs are off; kept for symmetry
+    o->graphs.swap(kept);
     g_err = msg;
     return rc;
 }

@@ -623,6 +623,24 @@ __global__ void k_sample(const double2 *__restrict__ amps, int64_t k, int r, con
     picks[p] = pick;
 }
 
+// FP32 fused multiply-add throughput probe: each thread runs 8 independent
+// FMA chains for `iters` rounds (16 flops per round); the result is stored
+// only under a condition the values never meet, so the work is kept.
+__global__ void __launch_bounds__(256) k_fma_probe(int64_t iters, float seed, float *out) {
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = seed + float(threadIdx.x + j);
+    const float b = 0.999999f, c = 1e-6f;
+#pragma unroll 4
+    for (int64_t i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fmaf(a[j], b, c);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j];
+    if (s == -1.f) out[blockIdx.x] = s;
+}
+
 }  // namespace
 
 cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *highs, int64_t batch, float2 *ws,
@@ -738,6 +756,12 @@ cudaError_t launch_pt_hist(const double *amps, int64_t k, double n_states, doubl
     const int blocks = int(want < 1024 ? (want > 0 ? want : 1) : 1024);
     k_pt_hist<<<blocks, 256, size_t(nbins + 1) * sizeof(unsigned int), s>>>(reinterpret_cast<const double2 *>(amps),
                                                                          k, n_states, x_max, nbins, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fma_probe(int64_t blocks, int64_t iters, float *out, cudaStream_t s) {
+    if (blocks <= 0 || blocks > 0x7fffffffLL || iters < 0) return cudaErrorInvalidValue;
+    k_fma_probe<<<dim3((unsigned)blocks), 256, 0, s>>>(iters, 1.0f, out);
     return cudaGetLastError();
 }
 

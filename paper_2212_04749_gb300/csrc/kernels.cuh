@@ -75,6 +75,10 @@ cudaError_t launch_pt_moments(const double *amps, int64_t k, double n_states, do
                               cudaStream_t s);
 cudaError_t launch_sample(const double *amps, int64_t k, int r, const double *uniform, int64_t *picks,
                           cudaStream_t s);
+// FP32 FMA throughput probe: `blocks` blocks of 256 threads, each thread
+// 16 * iters flops; out (>= blocks floats) is written only in a case that
+// does not occur.
+cudaError_t launch_fma_probe(int64_t blocks, int64_t iters, float *out, cudaStream_t s);
 cudaError_t launch_pt_hist(const double *amps, int64_t k, double n_states, double x_max, int nbins,
                            unsigned long long *counts, cudaStream_t s);
 

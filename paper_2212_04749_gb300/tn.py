@@ -24,7 +24,7 @@ EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_p
            "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_set_tc_resident_b", "tn_plan_get_configs", "tn_pt_moments", "tn_pt_histogram", "tn_sample_completions",
            "tn_plan_features", "tn_plan_autotune", "tn_plan_select", "tn_mlp_grad_scratch_bytes",
            "tn_mlp_forward", "tn_mlp_grad", "tn_mlp_adam", "tn_mlp_to_half", "tn_mlp_forward_f16",
-           "tn_plan_check", "tn_contract_static", "tn_destroy", "tn_last_error")
+           "tn_plan_check", "tn_contract_static", "tn_fma_probe", "tn_plan_batch_slices", "tn_destroy", "tn_last_error")
 TN_STATIC_SCRATCH_BYTES = 64 << 20
 TN_PT_MAX_BINS = 8192
 TN_MAX_OPEN = 16
@@ -132,6 +132,8 @@ def load(build_if_missing: bool = False):
         "tn_mlp_forward_f16": (ctypes.c_int, [vp, vp, i64, vp, vp]),
         "tn_plan_check": (ctypes.c_int, [vp, vp]),
         "tn_contract_static": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "tn_fma_probe": (ctypes.c_int, [i64, i64, vp, vp]),
+        "tn_plan_batch_slices": (ctypes.c_int, [vp, i64, vp, i64]),
         "tn_plan_step_times": (ctypes.c_int, [vp, vp, vp, i32]),
         "tn_destroy": (None, [vp]),
         "tn_last_error": (ctypes.c_char_p, []),
@@ -260,15 +262,32 @@ class Plan:
             out.append(r)
         return out
 
+    def tn_plan_batch_slices(self, batch):
+        """Slice ids (int64 numpy array) computed by slice batch ``batch``."""
+        n = 1 << self.info["slice_batch_log2"]
+        out = np.zeros(n, np.int64)
+        _check(self._lib.tn_plan_batch_slices(self.h, int(batch), out.ctypes.data, n))
+        return out
+
     def tn_plan_bind(self, workspace, nbytes=None, stream=None):
         if nbytes is None:
             nbytes = workspace.numel() * workspace.element_size()
         self._ws = workspace  # keep it alive while bound
         _check(self._lib.tn_plan_bind(self.h, _ptr(workspace), int(nbytes), _stream(stream)))
 
+    @staticmethod
+    def _check_amps(amps, n_complex, what):
+        """A complex128 device buffer must hold n_complex entries (2 doubles
+        each); raw integer addresses are taken on trust."""
+        if hasattr(amps, "numel") and hasattr(amps, "element_size"):
+            if amps.numel() * amps.element_size() < 16 * n_complex:
+                raise TnError(TN_EINVAL, f"{what}: amplitude buffer holds {amps.numel() * amps.element_size()} "
+                                         f"bytes, needs {16 * n_complex}")
+
     def tn_contract(self, amps, precision=TN_FP32, batch_lo=0, batch_hi=None, stream=None):
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
+        self._check_amps(amps, self.k * self.info["amps_per_row"], "tn_contract")
         if batch_hi is None:
             batch_hi = self.info["n_batches"]
         _check(self._lib.tn_contract(self.h, int(precision), int(batch_lo), int(batch_hi), _ptr(amps),
@@ -287,6 +306,7 @@ class Plan:
         plans above TN_STATIC_SCRATCH_BYTES are rejected)."""
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
+        self._check_amps(amps, self.k * self.info["amps_per_row"], "tn_contract_static")
         _check(self._lib.tn_contract_static(self.h, int(precision), _ptr(amps), _stream(stream)))
 
     def tn_plan_set_kernel(self, step, kernel):
@@ -367,6 +387,11 @@ def tn_pt_moments(amps, k, n_qubits, fidelity, out, stream=None):
 def tn_pt_histogram(amps, k, n_qubits, x_max, nbins, counts, stream=None):
     _check(load().tn_pt_histogram(_ptr(amps), int(k), int(n_qubits), float(x_max), int(nbins), _ptr(counts),
                                   _stream(stream)))
+
+
+def tn_fma_probe(blocks, iters, out, stream=None):
+    """FP32 FMA throughput probe: blocks x 256 threads x 16 x iters flops."""
+    _check(load().tn_fma_probe(int(blocks), int(iters), _ptr(out), _stream(stream)))
 
 
 def tn_mlp_grad_scratch_bytes(n):
