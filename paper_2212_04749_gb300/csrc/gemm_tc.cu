@@ -96,13 +96,14 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return sdesc(saddr, 16, 1024) | (uint64_t(2) << 61);
 }
 
-// instruction descriptor: FP32 accumulate, A/B K-major, M = 128, N = TBNR
-__device__ __forceinline__ uint32_t idesc(uint32_t ab_format) {
+// instruction descriptor: FP32 accumulate, A/B K-major, M = 128, N = nreal
+// (a multiple of 16, at most TBNR)
+__device__ __forceinline__ uint32_t idesc(uint32_t ab_format, uint32_t nreal) {
     uint32_t d = 0;
     d |= 1u << 4;                 // D format: F32
     d |= ab_format << 7;          // A format
     d |= ab_format << 10;         // B format
-    d |= uint32_t(TBNR >> 3) << 17;
+    d |= (nreal >> 3) << 17;
     d |= uint32_t(TBM >> 4) << 24;
     return d;
 }
@@ -255,8 +256,8 @@ constexpr int NTHREADS = 640;
 constexpr int LAUNCH_REGS = 96, PROD_REGS = 88, EPI_REGS = 112, CTL_REGS = 72;
 static_assert(NPROD * PROD_REGS + NEPI * EPI_REGS + 128 * CTL_REGS <= NTHREADS * LAUNCH_REGS,
               "register split above the launch allocation");
-constexpr int MS = 4;         // epilogue metadata ring (tiles ahead of the epilogue)
-constexpr int ACC_COLS = 128;
+constexpr int MS = 8;         // epilogue metadata ring (tiles ahead of the epilogue)
+constexpr int NACC_MAX = 8;   // accumulators in TMEM (narrow tiles: up to 8 in flight)
 constexpr int TMEM_COLS2 = 256;
 
 // Shared-memory layout.  Streaming B (BRES = false): A ring, B MMA stages,
@@ -313,7 +314,8 @@ struct EpiMap {
 };
 
 struct Ctrl {
-    uint64_t full[4], empty[4], rfull[8], rempty[8], afull[8], tfull[2], tempty[2], mfull[MS], mempty[MS];
+    uint64_t full[4], empty[4], rfull[8], rempty[8], afull[8], tfull[NACC_MAX], tempty[NACC_MAX], mfull[MS],
+        mempty[MS];
     uint64_t bfull, bempty;  // resident B: loaded / no longer read by the MMAs
     uint32_t tmem_base;
     int32_t abort_;
@@ -352,6 +354,55 @@ __device__ __forceinline__ int4 tile_decode(const StepDesc &d, int64_t T, int64_
     r.w = int((local - mt * nct) * TBN);
     return r;
 }
+
+// Walks a CTA's contiguous range of tiles in order.  One division at the
+// start (tile_decode's); afterwards each step is a counter update, and the
+// column-tile record of the next unit (schedule 1: the next column tile;
+// schedule 0: the next group) is fetched one unit ahead, so no role waits on
+// a global load per tile.
+struct TileIter {
+    int64_t f;       // unit: schedule 1 its column-tile record, schedule 0 its group's first record
+    int mt;          // row tile
+    int ct, nct;     // column tile within the unit and their count (schedule 1: 0 and 1)
+    int4 rec, nrec;  // the unit's record (schedule 0: its first, column offset 0) and the next unit's
+
+    __device__ __forceinline__ static int unit_tiles(const StepDesc &d, const int4 &r) {
+        return d.sched != 0 ? 1 : int(((int64_t(r.y) << d.nb) + TBN - 1) / TBN);
+    }
+    __device__ __forceinline__ void fetch_next(const StepDesc &d) {
+        const int64_t fn = f + nct;
+        nrec = fn < d.n_ctab ? __ldg(d.trec + fn) : make_int4(0, 0, 0, 0);
+    }
+    __device__ __forceinline__ void init(const StepDesc &d, int64_t T, int64_t mtiles) {
+        int64_t m, g;
+        rec = tile_decode(d, T, mtiles, m, &g);
+        f = g;
+        mt = int(m);
+        ct = 0;
+        if (d.sched == 0) {
+            ct = rec.w / TBN;
+            rec.w = 0;
+        }
+        nct = unit_tiles(d, rec);
+        fetch_next(d);
+    }
+    // the current tile's record (first instance, count, A instance, first column)
+    __device__ __forceinline__ int4 record(const StepDesc &d) const {
+        int4 r = rec;
+        if (d.sched == 0) r.w = ct * TBN;
+        return r;
+    }
+    __device__ __forceinline__ void next(const StepDesc &d, int64_t mtiles) {
+        if (++ct < nct) return;
+        ct = 0;
+        if (++mt < mtiles) return;
+        mt = 0;
+        f += nct;
+        rec = nrec;
+        nct = unit_tiles(d, rec);
+        fetch_next(d);
+    }
+};
 
 // XOR swizzle of a warp staging area (256 16-byte units): eight consecutive
 // units stay within one 128-byte row, and units that differ in higher bits
@@ -547,13 +598,20 @@ __device__ __forceinline__ void fold_max8(const float *v, EpiMeta &em, int c0, i
 
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 warps on a sub-partition)
-    k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA, int nrs) {
+    k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA, int nrs,
+                   int acw, int ow) {
     // MODE 0: B streamed chunk by chunk; 1: B resident (a group's or a
     // column tile's), rescale folded into it; 2: B dictionary, every B
     // instance of the step (at most 64 columns) resident for the whole
     // launch, each tile's columns gathered from the accumulator.
     // nrs: A stages in use (C::RST streaming B; resident B: the pool slots
     // left after the largest resident B)
+    // acw: complex columns of an accumulator (8, 16, 32 or 64; MMA N =
+    // 2 acw): the widest tile (MODE 0, 1) or the dictionary (MODE 2), so
+    // that narrow steps do not multiply zero columns; 128 / acw accumulators
+    // (at most NACC_MAX) rotate through TMEM.  ow: most output columns of a
+    // tile (8 .. 64).  With ow <= 16 the two halves of the epilogue (warps
+    // 8-11, 12-15) drain alternate tiles, each warp 32 rows x ow columns.
     constexpr bool BRES = MODE != 0;
     using C = Cfg<PREC, BRES>;
     extern __shared__ uint8_t smem_raw[];
@@ -565,11 +623,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
     const int N = 1 << d.nb;
     const int K = 1 << d.kb;
     const int nch = (K + TBK - 1) / TBK;
-    // streaming B: tiles blockIdx.x, + gridDim.x, ...; resident B: one
-    // contiguous range of tiles per CTA (a group's tiles run back to back)
-    const int64_t t_begin = BRES ? n_tiles * blockIdx.x / gridDim.x : int64_t(blockIdx.x);
-    const int64_t my_tiles = BRES ? n_tiles * (blockIdx.x + 1) / gridDim.x - t_begin
-                                  : (blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+    // accumulators in rotation: a power of two, so tile l uses accumulator
+    // l & (nacc - 1) in its phase l >> nacc_sh (no 64-bit division)
+    const int nacc_sh = acw >= 64 ? 1 : (acw == 32 ? 2 : 3);
+    const int nacc = 1 << nacc_sh;
+    static_assert(NACC_MAX == 8, "accumulator rotation of at most 8");
+    const uint32_t awr = uint32_t(2 * acw);  // TMEM columns of an accumulator
+    const bool narrow = ow <= 16;
+    const int nepi = narrow ? NEPI / 2 : NEPI;  // epilogue threads that drain one tile
+    // one contiguous range of tiles per CTA (a unit's tiles run back to
+    // back: its B and its records are reused)
+    const int64_t t_begin = n_tiles * blockIdx.x / gridDim.x;
+    const int64_t my_tiles = n_tiles * (blockIdx.x + 1) / gridDim.x - t_begin;
     const int64_t total_chunks = my_tiles * nch;
 
     if (warp == MMA_WARP) {
@@ -590,13 +655,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         }
         mbar_init(&X.bfull, NPROD);
         mbar_init(&X.bempty, 1);
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NACC_MAX; ++a) {
             mbar_init(&X.tfull[a], 1);
-            mbar_init(&X.tempty[a], NEPI);
+            mbar_init(&X.tempty[a], nepi);
         }
         for (int s = 0; s < MS; ++s) {
             mbar_init(&X.mfull[s], 32);
-            mbar_init(&X.mempty[s], NEPI);
+            mbar_init(&X.mempty[s], nepi);
         }
         X.abort_ = *reinterpret_cast<volatile int32_t *>(err);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -649,7 +714,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         atomicExch(err, 1);
         *abort_flag = 1;
     };
-    auto tile_of = [&](int64_t l) { return BRES ? t_begin + l : t_begin + l * gridDim.x; };
 
     if (warp >= MMA_WARP) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(CTL_REGS));
     if (warp == TMA_WARP) {
@@ -658,14 +722,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             int64_t issued = 0;
             bool ok = true;
-            int64_t mt_n = 0;
-            int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_n) : make_int4(0, 0, 0, 0);
+            TileIter it;
+            if (my_tiles > 0) it.init(d, t_begin, mtiles);
             int rs = 0;
             uint32_t rph = 0;
-            for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
-                const int4 r = r_n;  // the next tile's record is fetched one tile ahead
-                const int m0 = int(mt_n * TBM);
-                if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_n);
+            for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles)) {
+                const int4 r = it.record(d);
+                const int m0 = int(it.mt * TBM);
                 for (int c = 0; c < nch; ++c, ++issued) {
                     if (!mbar_wait(&X.rempty[rs], rph ^ 1u)) {
                         ok = false;
@@ -695,12 +758,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         // also splits every A chunk in place
         int rs = 0;
         uint32_t rph = 0, u = 0;
-        int64_t gprev = -1, mt_unused, g_n = 0;
-        int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_unused, &g_n) : make_int4(0, 0, 0, 0);
-        for (int64_t l = 0; l < my_tiles && !*abort_flag; ++l) {
-            const int4 r = r_n;
-            const int64_t g = MODE == 2 ? 0 : g_n;  // the dictionary is loaded once
-            if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_unused, &g_n);
+        int64_t gprev = -1;
+        TileIter it;
+        if (my_tiles > 0) it.init(d, t_begin, mtiles);
+        for (int64_t l = 0; l < my_tiles && !*abort_flag; ++l, it.next(d, mtiles)) {
+            const int4 r = it.record(d);
+            const int64_t g = MODE == 2 ? 0 : it.f;  // the dictionary is loaded once
             if (g != gprev) {
                 if (u > 0 && !mbar_wait(&X.bempty, (u - 1) & 1u)) {
                     give_up();
@@ -734,43 +797,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             }
         }
       } else {
-        int64_t bbase[2] = {-1, -1};
         int64_t issued = 0;
-        // metadata pipeline: records two tiles ahead, B instance one tile ahead
-        int4 rec_pf[2] = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
-        int ib_pf = 0;
-        auto col_inst = [&](const int4 &r) -> int64_t {  // instance of this thread's B column, or -1
-            const int64_t gc = int64_t(r.w) + bcol;
-            return gc < (int64_t(r.y) << d.nb) ? int64_t(r.x) + (gc >> d.nb) : -1;
-        };
-        int64_t mt_unused;
-        if (my_tiles > 0) {
-            rec_pf[0] = tile_decode(d, tile_of(0), mtiles, mt_unused);
-            if (my_tiles > 1) rec_pf[1] = tile_decode(d, tile_of(1), mtiles, mt_unused);
-            const int64_t ci = col_inst(rec_pf[0]);
-            ib_pf = ci >= 0 ? __ldg(d.instab + ci).y : 0;
-        }
+        // the B column of this thread, per unit and column tile: its
+        // element offset in B (-1: past the tile's columns), looked up when
+        // the tile's record or column offset changes
+        int64_t bb = -1, fprev = -1;
+        int ctprev = -1;
+        int c_iss = 0;  // chunk of the tile being issued
+        TileIter it;
+        if (my_tiles > 0) it.init(d, t_begin, mtiles);
         for (int64_t gch = 0; gch < total_chunks && !*abort_flag; ++gch) {
             // B pieces run LOOK chunks ahead.  Each thread reads back only
             // the 32 bytes it copied, and its raw slot was last used by a
             // chunk it has already expanded, so the ring needs no barrier.
             while (issued < total_chunks && issued <= gch + C::LOOK) {
-                const int64_t l = issued / nch;
-                const int c = int(issued - l * nch);
+                const int c = c_iss;
                 const int bslot = int(issued % C::BRST);
                 if (c == 0) {
-                    const int4 r = rec_pf[l & 1];
-                    const int64_t ci = col_inst(r);
-                    // column-affine B: column n of instance ib starts at ib*sB + n*K
-                    bbase[l & 1] = ci >= 0 ? int64_t(ib_pf) * d.sB + (((int64_t(r.w) + bcol) & (N - 1)) << d.kb) : -1;
-                    if (l + 1 < my_tiles) {
-                        const int64_t cn = col_inst(rec_pf[(l + 1) & 1]);
-                        ib_pf = cn >= 0 ? __ldg(d.instab + cn).y : 0;
+                    if (issued > 0) it.next(d, mtiles);
+                    if (it.f != fprev || it.ct != ctprev) {
+                        const int4 r = it.record(d);
+                        const int64_t gc = int64_t(r.w) + bcol;
+                        // column-affine B: column n of instance ib starts at ib*sB + n*K
+                        bb = -1;
+                        if (gc < (int64_t(r.y) << d.nb)) {
+                            const int ib = __ldg(d.instab + (int64_t(r.x) + (gc >> d.nb))).y;
+                            bb = int64_t(ib) * d.sB + ((gc & (N - 1)) << d.kb);
+                        }
+                        fprev = it.f;
+                        ctprev = it.ct;
                     }
-                    if (l + 2 < my_tiles) rec_pf[l & 1] = tile_decode(d, tile_of(l + 2), mtiles, mt_unused);
                 }
+                if (++c_iss == nch) c_iss = 0;
                 {  // B: this thread's column, k quad kqb
-                    const int64_t bb = bbase[l & 1];
                     const uint32_t dst = smem_u32(sm + C::OFF_BRAW + bslot * C::SLOT_BRAW) + uint32_t(tid) * 32;
                     const int k = c * TBK + 4 * kqb;
                     const bool v = bb >= 0 && k + 3 < K;
@@ -814,7 +873,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             // the MMAs of one K chunk: A slot a0 (swizzled rows), B slot b0
             auto issue_chunk = [&](uint32_t dtm, uint32_t a0, uint32_t b0, bool first) {
                 if (PREC == 1) {
-                    const uint32_t id = idesc(2u);
+                    const uint32_t id = idesc(2u, awr);
 #pragma unroll
                     for (int j = 0; j < TBKR / 8; ++j) {  // K step: 8 tf32 = 32 bytes of an A row
                         const uint32_t off = uint32_t(2 * j) * LBO;
@@ -823,7 +882,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 } else {
                     // A: hi and lo K steps alternate in the slot (32 bytes
                     // each, swizzled rows); B: hi plane, lo plane 8 KB on
-                    const uint32_t id = idesc(1u);
+                    const uint32_t id = idesc(1u, awr);
                     const uint32_t bl = b0 + TBNR * TBKR * 2;
 #pragma unroll
                     for (int j = 0; j < TBKR / 16; ++j) {
@@ -839,14 +898,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             if constexpr (BRES) {
                 int rs = 0;
                 uint32_t rph = 0, u = 0;
-                int64_t gprev = -1, mt_unused, g_n = 0;
-                int4 r_n = my_tiles > 0 ? tile_decode(d, tile_of(0), mtiles, mt_unused, &g_n) : make_int4(0, 0, 0, 0);
-                for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
-                    const int4 r = r_n;
-                    const int64_t g = MODE == 2 ? 0 : g_n;
-                    if (l + 1 < my_tiles) r_n = tile_decode(d, tile_of(l + 1), mtiles, mt_unused, &g_n);
-                    const int acc = int(l & 1);
-                    if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> 1) & 1u) ^ 1u)) {
+                int64_t gprev = -1;
+                TileIter it;
+                if (my_tiles > 0) it.init(d, t_begin, mtiles);
+                for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles)) {
+                    const int4 r = it.record(d);
+                    const int64_t g = MODE == 2 ? 0 : it.f;
+                    const int acc = int(l & (nacc - 1));
+                    if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> nacc_sh) & 1u) ^ 1u)) {
                         ok = false;
                         break;
                     }
@@ -860,7 +919,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                         gprev = g;
                     }
                     tc_fence_after();
-                    const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
+                    const uint32_t dtm = tmem + uint32_t(acc) * awr;
                     const int ctl = (MODE == 2 || d.sched != 0) ? 0 : r.w / TBN;  // the tile's column tile within the resident B
                     const uint32_t bset = smem_u32(sm + C::OFF_RAW + (nrs + ctl * nch) * C::SLOT_RAW);
                     for (int c = 0; c < nch; ++c) {
@@ -881,13 +940,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             } else {
                 int64_t gch = 0;
                 for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l) {
-                    const int acc = int(l & 1);
-                    if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> 1) & 1u) ^ 1u)) {
+                    const int acc = int(l & (nacc - 1));
+                    if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> nacc_sh) & 1u) ^ 1u)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t dtm = tmem + uint32_t(acc * ACC_COLS);
+                    const uint32_t dtm = tmem + uint32_t(acc) * awr;
                     for (int c = 0; c < nch; ++c, ++gch) {
                         const int slot = int(gch % C::ST);
                         const int rs = int(gch % C::RST);
@@ -913,12 +972,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         __syncwarp();
     } else if (warp == META_WARP) {
         // ------------------------------------------------------------ epilogue metadata
-        // Software pipeline over this CTA's tiles: round j loads the column
-        // records of tile j+2, the B instances of tile j+1 and the operand
-        // exponents of tile j together (one memory latency per round), then
-        // fills tile j's slot (instance and rescale per column, C base
-        // offset, valid columns).  The instance exponents E_C are written
-        // here as well, once per instance: at its n = 0 column in row tile 0.
+        // Per tile: the instance, rescale and exponent of each column, the
+        // C base offset and the valid columns, into the slot ahead of the
+        // epilogue.  The column data depend only on the tile's unit and
+        // column tile, so they are loaded once per change (a unit spans
+        // many row tiles) and kept in registers; the instance exponents E_C
+        // are written here as well, once per instance: at its n = 0 column
+        // in row tile 0.
         auto flush_max = [&](const EpiMeta &em) {
             if (!d.mxC) return;
 #pragma unroll
@@ -928,43 +988,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 if (v && em.inst[c] >= 0) record_max(d.mxC + em.inst[c], v);
             }
         };
-        int64_t mt0 = 0, mt1 = 0, mt2 = 0;
-        int4 r0 = make_int4(0, 0, 0, 0), r1 = r0, r2 = r0;
-        int ib0[2] = {-1, -1};
         auto col_inst = [&](const int4 &r, int c) -> int {  // instance of tile column c, or -1
             const int64_t gc = int64_t(r.w) + c;
             return gc < (int64_t(r.y) << d.nb) ? r.x + int(gc >> d.nb) : -1;
         };
-        if (my_tiles > 0) {
-            r0 = tile_decode(d, tile_of(0), mtiles, mt0);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int i = col_inst(r0, lane + 32 * q);
-                ib0[q] = i >= 0 ? __ldg(d.instab + i).y : -1;
-            }
-        }
-        if (my_tiles > 1) r1 = tile_decode(d, tile_of(1), mtiles, mt1);
+        TileIter it;
+        if (my_tiles > 0) it.init(d, t_begin, mtiles);
+        int64_t fprev = -1;
+        int ctprev = -1;
+        int inst_c[2] = {-1, -1}, ib_c[2] = {-1, -1}, eb_c[2] = {0, 0}, EB_c[2] = {0, 0};
+        int ea_c = 0, EA_c = 0, ncv_c = 0, w_c = 0;
+        int64_t base_c = 0;  // C offset of the tile's (row 0, column 0) with the row tile's bits left out
         bool ok = true;
-        for (int64_t j = 0; j < my_tiles; ++j) {
-            uint32_t mxb[2] = {0u, 0u};
-            int32_t EBv[2] = {0, 0};
-            int ib1[2] = {-1, -1};
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (ib0[q] >= 0) {
-                    mxb[q] = d.mxB ? __ldg(d.mxB + ib0[q]) : 0u;
-                    EBv[q] = __ldg(d.EB + ib0[q]);
-                }
-            const uint32_t mxa = d.mxA ? __ldg(d.mxA + r0.z) : 0u;
-            const int32_t EAv = __ldg(d.EA + r0.z);
-            if (j + 1 < my_tiles) {
+        for (int64_t j = 0; j < my_tiles; ++j, it.next(d, mtiles)) {
+            if (it.f != fprev || it.ct != ctprev) {
+                const int4 r = it.record(d);
+                const uint32_t mxa = d.mxA ? __ldg(d.mxA + r.z) : 0u;
+                EA_c = __ldg(d.EA + r.z);
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    const int i = col_inst(r1, lane + 32 * q);
-                    ib1[q] = i >= 0 ? __ldg(d.instab + i).y : -1;
+                    inst_c[q] = col_inst(r, lane + 32 * q);
+                    ib_c[q] = inst_c[q] >= 0 ? __ldg(d.instab + inst_c[q]).y : -1;
                 }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    uint32_t mxb = 0u;
+                    EB_c[q] = 0;
+                    if (ib_c[q] >= 0) {
+                        mxb = d.mxB ? __ldg(d.mxB + ib_c[q]) : 0u;
+                        EB_c[q] = __ldg(d.EB + ib_c[q]);
+                    }
+                    eb_c[q] = d.mxB ? exp_of(mxb) : 0;
+                }
+                ea_c = d.mxA ? exp_of(mxa) : 0;
+                const int64_t ncols = int64_t(r.y) << d.nb;
+                ncv_c = int(ncols - r.w < TBN ? ncols - r.w : TBN);
+                base_c = (int64_t(r.x) + (r.w >> d.nb)) * d.sC + dep(int64_t(r.w) & (N - 1), d.pCn, d.nb);
+                w_c = r.w;
+                fprev = it.f;
+                ctprev = it.ct;
             }
-            if (j + 2 < my_tiles) r2 = tile_decode(d, tile_of(j + 2), mtiles, mt2);
             const int slot = int(j % MS);
             const bool w = mbar_wait(&X.mempty[slot], (uint32_t(j / MS) & 1u) ^ 1u);
             if (!__all_sync(0xffffffffu, w) || __any_sync(0xffffffffu, *abort_flag != 0)) {
@@ -975,31 +1038,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             // the slot's previous tile (j - MS) is done: its maxima go to
             // global memory from here, off the epilogue's path
             if (j >= MS) flush_max(em);
-            const int ea = d.mxA ? exp_of(mxa) : 0;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int c = lane + 32 * q;
-                const int inst = col_inst(r0, c);
-                const int eb = d.mxB ? exp_of(mxb[q]) : 0;
+                const int inst = inst_c[q];
                 em.inst[c] = inst;
                 em.mx[c] = 0u;
-                em.sc[c] = pow2f(-(ea + (MODE == 2 ? 0 : eb)));  // the dictionary carries 2^-eb
-                if (MODE == 2) em.acol[c] = int16_t(inst >= 0 ? (ib0[q] << d.nb) + ((r0.w + c) & (N - 1)) : 0);
-                if (inst >= 0 && mt0 == 0 && ((int64_t(r0.w) + c) & (N - 1)) == 0) d.EC[inst] = EAv + ea + EBv[q] + eb;
+                em.sc[c] = pow2f(-(ea_c + (MODE == 2 ? 0 : eb_c[q])));  // the dictionary carries 2^-eb
+                if (MODE == 2) em.acol[c] = int16_t(inst >= 0 ? (ib_c[q] << d.nb) + ((w_c + c) & (N - 1)) : 0);
+                if (inst >= 0 && it.mt == 0 && ((int64_t(w_c) + c) & (N - 1)) == 0)
+                    d.EC[inst] = EA_c + ea_c + EB_c[q] + eb_c[q];
             }
             if (lane == 0) {
-                const int64_t ncols = int64_t(r0.y) << d.nb;
-                em.base = (int64_t(r0.x) + (r0.w >> d.nb)) * d.sC + dep(int64_t(r0.w) & (N - 1), d.pCn, d.nb) +
-                          dep(mt0 * TBM, d.pCm, d.mb);
-                em.ncv = int(ncols - r0.w < TBN ? ncols - r0.w : TBN);
+                em.base = base_c + dep(it.mt * TBM, d.pCm, d.mb);
+                em.ncv = ncv_c;
             }
             mbar_arrive(&X.mfull[slot]);  // every lane (count 32): its writes are released
-            r0 = r1;
-            mt0 = mt1;
-            ib0[0] = ib1[0];
-            ib0[1] = ib1[1];
-            r1 = r2;
-            mt1 = mt2;
         }
         // flush the last MS tiles once the epilogue has released them
         for (int64_t j = my_tiles > MS ? my_tiles - MS : 0; ok && j < my_tiles; ++j) {
@@ -1055,10 +1109,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         const bool pair = mp.pair != 0;
         const bool rows_ok = lanegrp * 32 < mp.nrows;  // M = 64: quadrants 2 and 3 hold no rows
         const int64_t qoff = mp.qoff[lanegrp];
-        for (int64_t l = 0; l < my_tiles; ++l) {
-            const int acc = int(l & 1), slot = int(l % MS);
+        for (int64_t l = narrow ? sub : 0; l < my_tiles; l += narrow ? 2 : 1) {
+            const int acc = int(l & (nacc - 1)), slot = int(l % MS);
             bool w = mbar_wait(&X.mfull[slot], uint32_t(l / MS) & 1u);
-            w = w && mbar_wait(&X.tfull[acc], uint32_t(l >> 1) & 1u);
+            w = w && mbar_wait(&X.tfull[acc], uint32_t(l >> nacc_sh) & 1u);
             if (!__all_sync(0xffffffffu, w) || __any_sync(0xffffffffu, *abort_flag != 0)) {
                 give_up();
                 break;
@@ -1067,16 +1121,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             EpiMeta &em = X.epi[slot];
             const int ncv = em.ncv;
             const int nh = ncv > TBN / 2 ? 2 : 1;
+            // passes of 8 columns this warp reads from the accumulator
+            // (non-dictionary narrow tiles of 8 columns: one)
+            const int npass = (MODE != 2 && acw < 16) ? 1 : 2;
             for (int h = 0; h < nh; ++h) {
-                const int c0 = h * 32 + sub * 16;      // first column of this warp's block
+                const int c0 = narrow ? 0 : h * 32 + sub * 16;  // first column of this warp's block
                 const bool act = rows_ok && c0 < ncv;  // warp-uniform
                 // two passes of 8 complex columns (16 accumulator columns)
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
                     float v[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = 0.f;
                     if (act && MODE == 2) {
                         // dictionary: each run of the pass from its own accumulator columns
-                        const uint32_t tb = tmem + uint32_t(acc * ACC_COLS) + (uint32_t(lanegrp * 32) << 16);
+                        const uint32_t tb = tmem + uint32_t(acc) * awr + (uint32_t(lanegrp * 32) << 16);
                         const int cp = c0 + 8 * p;
                         switch (N < 8 ? N : 8) {
                             case 1: tmem_gather<1>(v, tb, em, cp, ncv); break;
@@ -1084,8 +1143,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                             case 4: tmem_gather<4>(v, tb, em, cp, ncv); break;
                             default: tmem_gather<8>(v, tb, em, cp, ncv); break;
                         }
-                    } else if (act) {
-                        const uint32_t ta = tmem + uint32_t(acc * ACC_COLS + (c0 + 8 * p) * 2) +
+                    } else if (act && p < npass) {
+                        const uint32_t ta = tmem + uint32_t(acc) * awr + uint32_t((c0 + 8 * p) * 2) +
                                             (uint32_t(lanegrp * 32) << 16);
                         uint32_t r[16];
                         asm volatile(
@@ -1098,7 +1157,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
 #pragma unroll
                         for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
                     }
-                    if (h == nh - 1 && p == 1) {  // the accumulator is free for the tile after next
+                    if (h == nh - 1 && p == 1) {  // the accumulator is free for a later tile
                         tc_fence_before();
                         mbar_arrive(&X.tempty[acc]);
                     }
@@ -1134,7 +1193,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 if (!act) continue;
                 const int ncw = ncv - c0;  // valid columns of this block
                 __syncwarp();
-                const int64_t wb = em.base + qoff + mp.hoff[h * 2 + sub] + offL;
+                const int64_t wb = em.base + qoff + mp.hoff[narrow ? 0 : h * 2 + sub] + offL;
                 if (pair && ncw >= 16) {  // whole block valid, 16-byte runs: straight-line stores
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -1262,20 +1321,31 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
     const int ndict = tc_dictionary_chunks(d);
     const int nbset = ndict > 0 ? ndict : tc_resident_b_chunks(d);
     const int nrs = std::min(Cfg<2, true>::RST, Cfg<2, true>::NSLOT - nbset);
+    // accumulator and output widths (complex columns, powers of two in
+    // [8, 64]): the most columns a tile has, or the dictionary's width
+    auto width = [](int64_t cols) {
+        int w = 8;
+        while (w < cols && w < TBN) w <<= 1;
+        return w;
+    };
+    const int ow = width(int64_t(d.max_group) << d.nb);
+    const int acw = ndict > 0 ? width(d.nInstB << d.nb) : ow;
     if (ndict > 0) {
         if (precision == 1)
-            k_step_gemm_tc<1, 2><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+            k_step_gemm_tc<1, 2><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);
         else
-            k_step_gemm_tc<2, 2><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+            k_step_gemm_tc<2, 2><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);
     } else if (nbset > 0) {
         if (precision == 1)
-            k_step_gemm_tc<1, 1><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+            k_step_gemm_tc<1, 1><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);
         else
-            k_step_gemm_tc<2, 1><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs);
+            k_step_gemm_tc<2, 1><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);
     } else if (precision == 1) {
-        k_step_gemm_tc<1, 0><<<g, NTHREADS, smem_bytes<1, false>(), s>>>(d, mtiles, err, *a_map, Cfg<1, false>::RST);
+        k_step_gemm_tc<1, 0><<<g, NTHREADS, smem_bytes<1, false>(), s>>>(d, mtiles, err, *a_map, Cfg<1, false>::RST,
+                                                                         acw, ow);
     } else {
-        k_step_gemm_tc<2, 0><<<g, NTHREADS, smem_bytes<2, false>(), s>>>(d, mtiles, err, *a_map, Cfg<2, false>::RST);
+        k_step_gemm_tc<2, 0><<<g, NTHREADS, smem_bytes<2, false>(), s>>>(d, mtiles, err, *a_map, Cfg<2, false>::RST,
+                                                                         acw, ow);
     }
     return cudaGetLastError();
 }
