@@ -122,6 +122,8 @@ void build_descs(PlanObj *o) {
         d.n_ctab = (int64_t)st.col_tiles.size();
         d.trec = at<const int4>(o, st.off_tile_rec);
         d.instab = at<const int2>(o, st.off_inst_ab);
+        d.bpack = P.bpack_bytes > 0 ? at<uint8_t>(o, P.off_bpack) : nullptr;
+        d.bpack_bytes = P.bpack_bytes;
 
         int64_t mg = 0;
         for (int64_t g = 0; g < st.n_groups; ++g) mg = std::max(mg, st.group_first[g + 1] - st.group_first[g]);

@@ -220,6 +220,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// contiguous bulk copy global -> this CTA's shared memory (16-byte aligned,
+// size a multiple of 16), completion counted on `bar`
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
@@ -284,6 +293,8 @@ struct Cfg {
     static_assert(LOOK < BRST, "B pieces in flight fit the raw ring");
 };
 constexpr int BRES_MAX_B = 8;  // resident B: at most 8 chunks (nct x nch), so at least 3 A stages
+constexpr int PACK_ST = 5;     // packed B: 5 stages of (A chunk, B chunk) in the pool
+static_assert(2 * PACK_ST <= Cfg<2, true>::NSLOT && PACK_ST <= Cfg<2, true>::RST, "packed-B stages fit the pool");
 
 // Per-tile epilogue metadata, written by the metadata warp into a ring of
 // MS slots ahead of the epilogue.
@@ -612,8 +623,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
     // (at most NACC_MAX) rotate through TMEM.  ow: most output columns of a
     // tile (8 .. 64).  With ow <= 16 the two halves of the epilogue (warps
     // 8-11, 12-15) drain alternate tiles, each warp 32 rows x ow columns.
-    constexpr bool BRES = MODE != 0;
-    using C = Cfg<PREC, BRES>;
+    // MODE 3: B packed in MMA form in global memory (tc_pack_b, once per
+    // launch) and bulk-copied chunk by chunk beside A from L2, B carrying
+    // 2^-eb
+    constexpr bool BRES = MODE == 1 || MODE == 2;
+    constexpr bool BPACK = MODE == 3;
+    using C = Cfg<PREC, BRES || BPACK>;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment: the swizzled A slots are whole 8-row atoms
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -726,16 +741,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             if (my_tiles > 0) it.init(d, t_begin, mtiles);
             int rs = 0;
             uint32_t rph = 0;
+            const uint8_t *bsrc = nullptr;  // packed B: the tile's first chunk
+            int64_t fprev = -1;
+            int ctprev = -1;
             for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles)) {
                 const int4 r = it.record(d);
                 const int m0 = int(it.mt * TBM);
+                if (BPACK && (it.f != fprev || it.ct != ctprev)) {
+                    // the tile's 64 columns lie in one B instance (N >= 64):
+                    // its chunks for this column tile are consecutive
+                    const int ib = __ldg(d.instab + (int64_t(r.x) + (r.w >> d.nb))).y;
+                    const int64_t blk = (int64_t(ib) << (d.nb - 6)) + ((r.w & (N - 1)) >> 6);
+                    bsrc = d.bpack + blk * nch * int64_t(C::SLOT_B);
+                    fprev = it.f;
+                    ctprev = it.ct;
+                }
                 for (int c = 0; c < nch; ++c, ++issued) {
                     if (!mbar_wait(&X.rempty[rs], rph ^ 1u)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&X.rfull[rs], C::SLOT_RAW);
+                    mbar_expect_tx(&X.rfull[rs], BPACK ? C::SLOT_RAW + C::SLOT_B : C::SLOT_RAW);
                     tma_load_3d(smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), &tmA, TBKR * c, m0, r.z, &X.rfull[rs]);
+                    if (BPACK)
+                        bulk_load(smem_u32(sm + C::OFF_RAW + (PACK_ST + rs) * C::SLOT_RAW), bsrc + c * C::SLOT_B,
+                                  C::SLOT_B, &X.rfull[rs]);
                     if (++rs == nrs) {
                         rs = 0;
                         rph ^= 1u;
@@ -752,7 +782,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         // ------------------------------------------------------------ B loads, A split
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(PROD_REGS));
         const int bcol = tid & 63, kqb = tid >> 6;
-      if constexpr (BRES) {
+      if constexpr (BRES || BPACK) {
         // resident B: at each group switch (once the MMAs stopped reading
         // the previous group's B) load the group's B into the pool; BF16x3
         // also splits every A chunk in place
@@ -764,12 +794,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         for (int64_t l = 0; l < my_tiles && !*abort_flag; ++l, it.next(d, mtiles)) {
             const int4 r = it.record(d);
             const int64_t g = MODE == 2 ? 0 : it.f;  // the dictionary is loaded once
-            if (g != gprev) {
+            if (BRES && g != gprev) {
                 if (u > 0 && !mbar_wait(&X.bempty, (u - 1) & 1u)) {
                     give_up();
                     break;
                 }
-                load_bset<PREC, MODE == 2>(d, r, nch, K, sm + C::OFF_RAW + nrs * C::SLOT_RAW, bcol, kqb);
+                if constexpr (BRES) load_bset<PREC, MODE == 2>(d, r, nch, K, sm + C::OFF_RAW + nrs * C::SLOT_RAW, bcol, kqb);
                 proxy_fence();
                 mbar_arrive(&X.bfull);
                 ++u;
@@ -895,7 +925,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 }
             };
             bool ok = true;
-            if constexpr (BRES) {
+            if constexpr (BRES || BPACK) {
                 int rs = 0;
                 uint32_t rph = 0, u = 0;
                 int64_t gprev = -1;
@@ -909,7 +939,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                         ok = false;
                         break;
                     }
-                    if (g != gprev) {  // new group: release the old B once its MMAs are done, wait for the new
+                    if (BRES && g != gprev) {  // new group: release the old B once its MMAs are done, wait for the new
                         if (u > 0) mma_commit(&X.bempty);
                         if (!mbar_wait(&X.bfull, u & 1u)) {
                             ok = false;
@@ -928,7 +958,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                             break;
                         }
                         tc_fence_after();
-                        issue_chunk(dtm, smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), bset + c * C::SLOT_RAW, c == 0);
+                        const uint32_t bch = BPACK ? smem_u32(sm + C::OFF_RAW + (PACK_ST + rs) * C::SLOT_RAW)
+                                                   : bset + c * C::SLOT_RAW;
+                        issue_chunk(dtm, smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), bch, c == 0);
                         mma_commit(&X.rempty[rs]);
                         if (++rs == nrs) {
                             rs = 0;
@@ -1044,7 +1076,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 const int inst = inst_c[q];
                 em.inst[c] = inst;
                 em.mx[c] = 0u;
-                em.sc[c] = pow2f(-(ea_c + (MODE == 2 ? 0 : eb_c[q])));  // the dictionary carries 2^-eb
+                em.sc[c] = pow2f(-(ea_c + (MODE >= 2 ? 0 : eb_c[q])));  // dictionary and packed B carry 2^-eb
                 if (MODE == 2) em.acol[c] = int16_t(inst >= 0 ? (ib_c[q] << d.nb) + ((w_c + c) & (N - 1)) : 0);
                 if (inst >= 0 && it.mt == 0 && ((int64_t(w_c) + c) & (N - 1)) == 0)
                     d.EC[inst] = EA_c + ea_c + EB_c[q] + eb_c[q];
@@ -1229,7 +1261,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
     }
 }
 
+// Packed B (MODE 3): every B instance of the step, 64 columns x 16 complex
+// k per 16 KB block (block (ib * N/64 + column tile) * nch + chunk) in the
+// layout of a B stage (real 2x2 form, K-major, TF32 or BF16 hi and lo
+// planes), each column multiplied by its instance's 2^-eb (exact).  One
+// block per CTA; thread (column, k quad) as in the producers' expansion.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_pack_b(const StepDesc d, int nch) {
+    const int tid = threadIdx.x, bcol = tid & 63, kqb = tid >> 6;
+    const int64_t blk = blockIdx.x;
+    const int c = int(blk % nch);
+    const int64_t ct_all = blk / nch;  // ib * (N / 64) + column tile
+    const int64_t ib = ct_all >> (d.nb - 6);
+    const int64_t n = ((ct_all & ((int64_t(1) << (d.nb - 6)) - 1)) << 6) + bcol;
+    const int K = 1 << d.kb;
+    const int k = c * TBK + 4 * kqb;
+    const float s = d.mxB ? pow2f(-exp_of(__ldg(d.mxB + ib))) : 1.f;
+    float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
+    if (k + 3 < K) {
+        const float4 *src = reinterpret_cast<const float4 *>(d.B + ib * d.sB + (n << d.kb) + k);
+        p0 = __ldg(src);
+        p1 = __ldg(src + 1);
+    }
+    expand_b<PREC>(d.bpack + blk * (TBNR * TBKR * 4), bcol, kqb,
+                   make_float4(p0.x * s, p0.y * s, p0.z * s, p0.w * s),
+                   make_float4(p1.x * s, p1.y * s, p1.z * s, p1.w * s));
+}
+
 }  // namespace
+
+int64_t tc_packed_b_bytes(const StepDesc &d) {
+    if (d.nb < 6 || !gemm_tc_supports(d)) return 0;
+    const int64_t nch = ((int64_t(1) << d.kb) + TBK - 1) / TBK;
+    return d.nInstB * (int64_t(1) << (d.nb - 6)) * nch * int64_t(TBNR * TBKR * 4);
+}
 
 bool gemm_tc_supports(const StepDesc &d) {
     // K >= 8 complex (at least half a chunk), 64 <= M < 2^31 rows
@@ -1273,15 +1338,18 @@ cudaError_t init_kernels() {
         if (e != cudaSuccess) return e;
         if (q != cudaDriverEntryPointSuccess || !g_encode) return cudaErrorNotSupported;
     }
-    const void *fns[6] = {reinterpret_cast<const void *>(k_step_gemm_tc<1, 0>),
+    const void *fns[8] = {reinterpret_cast<const void *>(k_step_gemm_tc<1, 0>),
                           reinterpret_cast<const void *>(k_step_gemm_tc<2, 0>),
                           reinterpret_cast<const void *>(k_step_gemm_tc<1, 1>),
                           reinterpret_cast<const void *>(k_step_gemm_tc<2, 1>),
                           reinterpret_cast<const void *>(k_step_gemm_tc<1, 2>),
-                          reinterpret_cast<const void *>(k_step_gemm_tc<2, 2>)};
-    const int bytes[6] = {(int)smem_bytes<1, false>(), (int)smem_bytes<2, false>(), (int)smem_bytes<1, true>(),
-                          (int)smem_bytes<2, true>(),  (int)smem_bytes<1, true>(),  (int)smem_bytes<2, true>()};
-    for (int i = 0; i < 6; ++i) {
+                          reinterpret_cast<const void *>(k_step_gemm_tc<2, 2>),
+                          reinterpret_cast<const void *>(k_step_gemm_tc<1, 3>),
+                          reinterpret_cast<const void *>(k_step_gemm_tc<2, 3>)};
+    const int bytes[8] = {(int)smem_bytes<1, false>(), (int)smem_bytes<2, false>(), (int)smem_bytes<1, true>(),
+                          (int)smem_bytes<2, true>(),  (int)smem_bytes<1, true>(),  (int)smem_bytes<2, true>(),
+                          (int)smem_bytes<1, true>(),  (int)smem_bytes<2, true>()};
+    for (int i = 0; i < 8; ++i) {
         e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[i]);
         if (e != cudaSuccess) return e;
     }
@@ -1330,6 +1398,23 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
     };
     const int ow = width(int64_t(d.max_group) << d.nb);
     const int acw = ndict > 0 ? width(d.nInstB << d.nb) : ow;
+    // B packed once per launch in MMA form and streamed from L2 where it is
+    // neither a dictionary nor resident and N >= 64 (a tile's columns lie
+    // in one B instance), if the plan reserved room for it
+    const int64_t pack = tc_packed_b_bytes(d);
+    if (ndict == 0 && nbset == 0 && d.tc_resident_b && pack > 0 && d.bpack && pack <= d.bpack_bytes) {
+        const int nch = int(((int64_t(1) << d.kb) + TBK - 1) / TBK);
+        const int64_t blocks = pack / (TBNR * TBKR * 4);
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        if (precision == 1) {
+            k_pack_b<1><<<dim3((unsigned)blocks), 256, 0, s>>>(d, nch);
+            k_step_gemm_tc<1, 3><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, PACK_ST, acw, ow);
+        } else {
+            k_pack_b<2><<<dim3((unsigned)blocks), 256, 0, s>>>(d, nch);
+            k_step_gemm_tc<2, 3><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, PACK_ST, acw, ow);
+        }
+        return cudaGetLastError();
+    }
     if (ndict > 0) {
         if (precision == 1)
             k_step_gemm_tc<1, 2><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);

@@ -41,6 +41,8 @@ struct StepDesc {
     int64_t n_ctab;
     const int4 *trec;             // per column tile: {first instance, count, A instance, first column}
     const int2 *instab;           // per output instance: {A instance, B instance}
+    uint8_t *bpack;               // tensor cores: scratch for B packed in MMA form (null: none)
+    int64_t bpack_bytes;
     int8_t pAm[40];
     int8_t pBn[24];
     int8_t pCm[40];
@@ -93,6 +95,9 @@ int tc_resident_b_chunks(const StepDesc &d);
 // tile keeps them resident for the whole launch (a dictionary): the chunk
 // count, else 0.
 int tc_dictionary_chunks(const StepDesc &d);
+// Bytes of the packed-B form of a step (every B instance in the MMA layout,
+// 16 KB per 64 columns x 16 complex k), 0 if the step cannot take it.
+int64_t tc_packed_b_bytes(const StepDesc &d);
 // One-time per-device setup (function attributes, SM count); call outside
 // any stream capture.
 cudaError_t init_kernels();

@@ -787,6 +787,18 @@ struct Builder {
                 push_upload(p, st.off_tile_rec, rec);
             }
         }
+        // room for the packed B operand of the largest step that can take it
+        // (N >= 64, K >= 8, 64 <= M < 2^31: every B instance, 16 bytes per
+        // complex entry, K padded to chunks of 16); steps run one at a time,
+        // so one region serves all; steps above 256 MiB stream B instead
+        p.bpack_bytes = 0;
+        for (const Step &st : p.steps) {
+            if (st.nb < 6 || st.kb < 3 || st.kb > 24 || st.mb < 6 || st.mb > 30) continue;
+            const int64_t nch = ((int64_t(1) << st.kb) + 15) / 16;
+            const int64_t bytes = p.nodes[st.b].n_inst * (int64_t(1) << (st.nb - 6)) * nch * 16384;
+            if (bytes <= (int64_t(256) << 20)) p.bpack_bytes = std::max(p.bpack_bytes, bytes);
+        }
+        p.off_bpack = p.bpack_bytes > 0 ? take(p.bpack_bytes) : -1;
         for (Chain &c : p.chains) {
             const Step &last = p.steps[c.steps.back()];
             const int64_t ni = p.nodes[last.node].n_inst;

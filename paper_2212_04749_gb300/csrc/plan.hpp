@@ -169,6 +169,7 @@ struct Plan {
     int64_t off_emax = -1, emax_bytes = 0;  // max words of every node, by level
     std::vector<int64_t> emax_prefix;       // [lv]: bytes covering the nodes of level <= lv
     int64_t off_scratch = -1;               // 256 bytes of device scratch (error word)
+    int64_t off_bpack = -1, bpack_bytes = 0; // tensor cores: room for one step's B packed in MMA form
     // host images uploaded at bind time: (offset, bytes)
     std::vector<std::pair<int64_t, std::vector<uint8_t>>> uploads;
 };
