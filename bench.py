@@ -578,6 +578,8 @@ def run_ours(args, world, rank, local):
         """Configure every step for `prec`; returns the selection record."""
         for s_ in range(info["n_steps"]):
             plan.tn_plan_set_config(s_, -1)
+        for c_ in range(info["n_chains"]):
+            plan.tn_plan_set_chain(c_, 1)
         if args.select == "rule":
             return {"mode": "rule"}
         rule_ms = statistics.median(one_step(prec) for _ in range(2))
@@ -590,8 +592,10 @@ def run_ours(args, world, rank, local):
             costmodel.select(costmodel.Bound(None, plan, ws, amps, stream), prec, tr)
         sel_s = time.perf_counter() - t0
         cfg = plan.tn_plan_get_configs()
+        ch = plan.tn_plan_get_chains()
         return {"mode": args.select, "rule_ms": rule_ms, "selection_s": sel_s,
-                "configs": np.bincount(cfg, minlength=tn.TN_NCONFIG).tolist()}
+                "configs": np.bincount(cfg, minlength=tn.TN_NCONFIG).tolist(),
+                "chains_fused": int(np.sum(ch)), "chains": int(len(ch))}
 
     def profile_steps(prec, runs=2):
         step_ms = np.zeros(info["n_steps"])
@@ -703,10 +707,12 @@ def run_ours(args, world, rank, local):
         # batch between the first and the last result
         from paper_2212_04749_gb300.pipeline import contract_batches
         cfg_now = plan.tn_plan_get_configs()
+        chains_now = plan.tn_plan_get_chains()
         marks = []
         ws_b = torch.empty_like(ws)  # second workspace: the next batch binds while this one runs
         for _i, _a in contract_batches(w.circuit, [bits] * (args.e2e_steps + 1), w.tree.ssa, sliced,
-                                       args.precision, (ws, ws_b), stream=stream, configs=cfg_now, **popts):
+                                       args.precision, (ws, ws_b), stream=stream, configs=cfg_now,
+                                       chains=chains_now, **popts):
             marks.append(time.perf_counter())
         del ws_b
         torch.cuda.empty_cache()  # the later measurements size themselves by free device memory

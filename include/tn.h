@@ -119,7 +119,7 @@ typedef struct {
     int64_t upload_bytes;         /* host-to-device bytes tn_plan_bind copies */
     int64_t launches_per_call;    /* kernels one full tn_contract launches */
     int32_t n_open;               /* open output qubits (tn_options.open_mask) */
-    int32_t pad0;
+    int32_t n_chains;             /* fused chains (tn_options.fuse) */
     int64_t amps_per_row;         /* 2^n_open complex amplitudes per input row */
 } tn_plan_info;
 
@@ -294,6 +294,17 @@ int tn_plan_set_config(tn_plan_t plan, int32_t step, int32_t config);
  * to measure and test the streaming form.  TN_EINVAL for a null plan. */
 int tn_plan_set_tc_resident_b(tn_plan_t plan, int32_t enable);
 
+/* Fused chains (tn_options.fuse; SM Sec. V.C fuses a run of steps so that
+ * only its last output leaves fast memory).  A chain runs fused (enable = 1,
+ * the default: one kernel, intermediates never stored) or as its separate
+ * steps (0: each step with its own configuration, its intermediate written
+ * to the slot the plan keeps for it); both give the same values up to
+ * rounding.  tn_plan_autotune decides per chain by timing both.  TN_EINVAL
+ * for a chain outside [0, n_chains). */
+int tn_plan_set_chain(tn_plan_t plan, int32_t chain, int32_t enable);
+/* Whether each chain runs fused (n entries, 1 or 0). */
+int tn_plan_get_chains(tn_plan_t plan, int32_t *enabled, int32_t n);
+
 /* Configuration each step will run with (the plan's choice where none was
  * set); n entries. */
 int tn_plan_get_configs(tn_plan_t plan, int32_t *config, int32_t n);
@@ -318,7 +329,10 @@ int tn_plan_features(tn_plan_t plan, int precision, int32_t config, float *feat,
  * NaN where not measured.  Afterwards every selected step is set to its
  * fastest configuration.  amps_scratch: device complex128 buffer of k
  * entries the runs accumulate into (its contents are meaningless
- * afterwards).  Needs a bound workspace; synchronises `stream`. */
+ * afterwards).  Fused chains: the configurations are timed with every
+ * chain run as separate steps; then each chain is timed fused and kept
+ * fused only where that beats the sum of its steps' best times
+ * (tn_plan_set_chain).  Needs a bound workspace; synchronises `stream`. */
 int tn_plan_autotune(tn_plan_t plan, int precision, int32_t reps, const uint8_t *step_mask, double *amps_scratch,
                      double *times, void *stream);
 

@@ -50,6 +50,8 @@ struct PlanObj {
     size_t ev_used = 0;
     std::vector<int32_t> step_kernel;     // kernel family each step ran last (0 row, 1 SIMT GEMM, 2 TC GEMM)
     std::vector<int32_t> config_override; // per step: -1 plan choice, else a configuration (tn.h)
+    std::vector<uint8_t> chain_on;        // per fused chain: run as one kernel (1) or as its steps (0)
+    bool chain_fused(int c) const { return c >= 0 && (c >= (int)chain_on.size() || chain_on[c] != 0); }
     struct GraphKey {
         int precision;
         int64_t lo, hi;
@@ -198,7 +200,7 @@ int effective_config(const PlanObj *o, int s) {
 
 int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
     const tnp::Step &S = o->P.steps[s];
-    if (S.chain >= 0) {  // fused chain: runs whole at its last step
+    if (o->chain_fused(S.chain)) {  // fused chain: runs whole at its last step
         if ((int)o->step_kernel.size() <= s) o->step_kernel.resize(o->P.steps.size(), -1);
         o->step_kernel[s] = 3;
         if (!S.chain_last) return TN_OK;
@@ -406,10 +408,12 @@ int tn_plan_query(tn_plan_t plan, tn_plan_info *info) {
     int64_t up = 0;
     for (const auto &u : P.uploads) up += (int64_t)u.second.size();
     info->upload_bytes = up;
+    const PlanObj *po = reinterpret_cast<const PlanObj *>(plan);
     double steps_run = 0;
-    for (const tnp::Step &st : P.steps) steps_run += (st.chain < 0 || st.chain_last) ? st.runs : 0.0;
+    for (const tnp::Step &st : P.steps) steps_run += (!po->chain_fused(st.chain) || st.chain_last) ? st.runs : 0.0;
     info->launches_per_call = (int64_t)steps_run + 2 * P.n_batches;  // + leaf fill and accumulate per batch
     info->n_open = (int32_t)P.open_qubits.size();
+    info->n_chains = (int32_t)P.chains.size();
     info->amps_per_row = int64_t(1) << P.open_qubits.size();
     return TN_OK;
 }
@@ -716,6 +720,23 @@ int tn_plan_set_config(tn_plan_t plan, int32_t step, int32_t config) {
     return TN_OK;
 }
 
+int tn_plan_set_chain(tn_plan_t plan, int32_t chain, int32_t enable) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_set_chain: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    if (chain < 0 || chain >= (int32_t)o->P.chains.size()) return set_err(TN_EINVAL, "tn_plan_set_chain: bad chain");
+    o->chain_on.resize(o->P.chains.size(), 1);
+    o->chain_on[chain] = enable ? 1 : 0;
+    o->drop_graphs();
+    return TN_OK;
+}
+
+int tn_plan_get_chains(tn_plan_t plan, int32_t *enabled, int32_t n) {
+    if (!plan || (n > 0 && !enabled)) return set_err(TN_EINVAL, "tn_plan_get_chains: null argument");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    for (int32_t c = 0; c < n && c < (int32_t)o->P.chains.size(); ++c) enabled[c] = o->chain_fused(c) ? 1 : 0;
+    return TN_OK;
+}
+
 int tn_plan_set_tc_resident_b(tn_plan_t plan, int32_t enable) {
     if (!plan) return set_err(TN_EINVAL, "tn_plan_set_tc_resident_b: null plan");
     PlanObj *o = reinterpret_cast<PlanObj *>(plan);
@@ -759,6 +780,9 @@ int tn_plan_autotune(tn_plan_t plan, int precision, int32_t reps, const uint8_t 
     const bool prof = o->profile;
     o->profile = true;  // CUDA events around every step launch
     o->config_override.assign(ns, -1);
+    const int nchains = (int)P.chains.size();
+    const std::vector<uint8_t> prev_chain = o->chain_on;
+    o->chain_on.assign(nchains, 0);  // configurations are timed on the separate steps
     int rc = TN_OK;
     for (int c = 0; c < TN_NCONFIG && rc == TN_OK; ++c) {
         bool any = false;
@@ -783,7 +807,7 @@ int tn_plan_autotune(tn_plan_t plan, int precision, int32_t reps, const uint8_t 
     }
     if (rc == TN_OK) rc = tn_plan_check(plan, stream);
     o->profile = prof;
-    const std::string msg = g_err;
+    std::string msg = g_err;
     for (int s = 0; s < ns; ++s) {
         int pick = cur[s];
         if (rc == TN_OK && (!step_mask || step_mask[s])) {
@@ -797,6 +821,41 @@ int tn_plan_autotune(tn_plan_t plan, int precision, int32_t reps, const uint8_t 
             }
         }
         o->config_override[s] = pick;
+    }
+    // fused chains: each kept fused only where its kernel beats the sum of
+    // its steps' best times (the chain's time is booked on its last step)
+    // (with a step mask only some steps were timed: the chains keep their
+    // previous setting)
+    if (rc != TN_OK || step_mask) o->chain_on = prev_chain;
+    if (rc == TN_OK && nchains > 0 && !step_mask) {
+        std::vector<double> unfused(nchains, 0.0), fused(nchains, NAN);
+        for (int s = 0; s < ns; ++s) {
+            const int c = P.steps[s].chain;
+            if (c < 0) continue;
+            double bt = NAN;
+            for (int k = 0; k < TN_NCONFIG; ++k) {
+                const double t = best[size_t(s) * TN_NCONFIG + k];
+                if (!std::isnan(t) && (std::isnan(bt) || t < bt)) bt = t;
+            }
+            unfused[c] += std::isnan(bt) ? 0.0 : bt;
+        }
+        o->chain_on.assign(nchains, 1);
+        o->profile = true;
+        for (int r = 0; r <= reps && rc == TN_OK; ++r) {
+            rc = tn_contract(plan, precision, 0, P.n_batches > 0 ? 1 : 0, amps_scratch, stream);
+            if (rc == TN_OK) rc = tn_plan_step_times(plan, ms.data(), nullptr, ns);
+            if (rc != TN_OK || r == 0) continue;
+            for (int s = 0; s < ns; ++s) {
+                const tnp::Step &S = P.steps[s];
+                if (S.chain < 0 || !S.chain_last) continue;
+                if (std::isnan(fused[S.chain]) || ms[s] < fused[S.chain]) fused[S.chain] = ms[s];
+            }
+        }
+        if (rc == TN_OK) rc = tn_plan_check(plan, stream);
+        if (rc != TN_OK) msg = g_err;
+        o->profile = prof;
+        for (int c = 0; c < nchains; ++c) o->chain_on[c] = (!std::isnan(fused[c]) && fused[c] < unfused[c]) ? 1 : 0;
+        if (rc != TN_OK) o->chain_on = prev_chain;
     }
     o->drop_graphs();
     if (times) std::copy(best.begin(), best.end(), times);

@@ -20,7 +20,8 @@ import numpy as np
 from . import tn
 
 
-def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stream=None, configs=None, **opts):
+def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stream=None, configs=None, chains=None,
+                     **opts):
     """Yield (batch index, amplitudes) for each bitstring batch in order.
 
     circ, tree_ssa, sliced, **opts: as for tn.Plan; every batch is planned
@@ -30,7 +31,8 @@ def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stre
     tables then upload while the current batch runs).  stream: the torch CUDA stream the
     contractions run on (default: the current stream).  configs: optional
     per-step configurations applied to every plan (all batches must then
-    yield plans with the same step count).  The amplitudes are complex128
+    yield plans with the same step count); chains: optional per-chain fused
+    flags (tn_plan_set_chain) applied likewise.  The amplitudes are complex128
     numpy arrays in input order (rows x 2^|open qubits| with
     opts open_qubits / open_mask), read from pinned host memory after the
     batch's contraction finished.
@@ -67,6 +69,9 @@ def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stre
             if configs is not None:
                 for s, c in enumerate(configs):
                     p.tn_plan_set_config(s, int(c))
+            if chains is not None:
+                for c, on in enumerate(chains):
+                    p.tn_plan_set_chain(c, int(on))
             m = len(batches[i]) * p.info["amps_per_row"]
             if amps is None or amps.numel() < 2 * m:
                 amps = torch.zeros(2 * max(m, 1), dtype=torch.float64, device="cuda")

@@ -24,7 +24,8 @@ EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_p
            "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_set_tc_resident_b", "tn_plan_get_configs", "tn_pt_moments", "tn_pt_histogram", "tn_sample_completions",
            "tn_plan_features", "tn_plan_autotune", "tn_plan_select", "tn_mlp_grad_scratch_bytes",
            "tn_mlp_forward", "tn_mlp_grad", "tn_mlp_adam", "tn_mlp_to_half", "tn_mlp_forward_f16",
-           "tn_plan_check", "tn_contract_static", "tn_fma_probe", "tn_plan_batch_slices", "tn_destroy", "tn_last_error")
+           "tn_plan_check", "tn_contract_static", "tn_fma_probe", "tn_plan_batch_slices", "tn_plan_set_chain",
+           "tn_plan_get_chains", "tn_destroy", "tn_last_error")
 TN_STATIC_SCRATCH_BYTES = 64 << 20
 TN_PT_MAX_BINS = 8192
 TN_MAX_OPEN = 16
@@ -65,7 +66,7 @@ class tn_plan_info(ctypes.Structure):
                 ("flops_ma", ctypes.c_double), ("flops_sa", ctypes.c_double), ("flops_exec", ctypes.c_double),
                 ("bytes_min", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
                 ("peak_tensor_bytes", ctypes.c_int64), ("upload_bytes", ctypes.c_int64),
-                ("launches_per_call", ctypes.c_int64), ("n_open", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("launches_per_call", ctypes.c_int64), ("n_open", ctypes.c_int32), ("n_chains", ctypes.c_int32),
                 ("amps_per_row", ctypes.c_int64)]
 
 
@@ -134,6 +135,8 @@ def load(build_if_missing: bool = False):
         "tn_contract_static": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "tn_fma_probe": (ctypes.c_int, [i64, i64, vp, vp]),
         "tn_plan_batch_slices": (ctypes.c_int, [vp, i64, vp, i64]),
+        "tn_plan_set_chain": (ctypes.c_int, [vp, i32, i32]),
+        "tn_plan_get_chains": (ctypes.c_int, [vp, vp, i32]),
         "tn_plan_step_times": (ctypes.c_int, [vp, vp, vp, i32]),
         "tn_destroy": (None, [vp]),
         "tn_last_error": (ctypes.c_char_p, []),
@@ -314,6 +317,15 @@ class Plan:
 
     def tn_plan_set_config(self, step, config):
         _check(self._lib.tn_plan_set_config(self.h, int(step), int(config)))
+
+    def tn_plan_set_chain(self, chain, enable):
+        _check(self._lib.tn_plan_set_chain(self.h, int(chain), int(bool(enable))))
+
+    def tn_plan_get_chains(self):
+        n = self.info["n_chains"]
+        c = np.zeros(max(n, 1), np.int32)
+        _check(self._lib.tn_plan_get_chains(self.h, c.ctypes.data, n))
+        return c[:n]
 
     def tn_plan_set_tc_resident_b(self, enable):
         _check(self._lib.tn_plan_set_tc_resident_b(self.h, int(bool(enable))))

@@ -99,3 +99,45 @@ def test_grid6x7_fused_sampled_slices():
     err = rel_l2(got, rec["partials"])
     print(f"grid6x7_m10 fused fp32: rel-L2 over {got.size} partials {err:.3e}")
     assert err <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_chains_fused_or_unfused_per_chain_and_autotuned(prec):
+    # every chain can run fused or as its separate steps (tn_plan_set_chain);
+    # both match the state vector, mixed settings too, and the autotuner
+    # keeps a chain fused only where its kernel beat the sum of its steps
+    torch, tn = require_cuda()
+    c = random_circuit(grid_layout(4, 5), 12, seed=21)
+    s = network_structure(c)
+    bits = uniform_bitstrings(20, 1500, seed=5)
+    ssa = candidate_trees(s, 1500, seed=2, trials=2)[0]
+    sl = choose_slices(s, ContractionTree(ssa=ssa), 1500, n_sliced=2)
+    ref = sv.amplitudes(c, bits)
+    stream = torch.cuda.current_stream()
+    p = tn.Plan(c, bits, ssa, sl, fuse=1, fuse_max_bits=9, rescale=1)
+    nch = p.info["n_chains"]
+    assert nch >= 2 and nch == _n_chains(p)
+    ws = torch.empty(p.info["workspace_bytes"], dtype=torch.uint8, device="cuda")
+    p.tn_plan_bind(ws, stream=stream)
+    amps = torch.zeros(2 * len(bits), dtype=torch.float64, device="cuda")
+    launches_fused = p.info["launches_per_call"]
+    for pattern in ("all_off", "alternate", "all_on"):
+        for ch in range(nch):
+            p.tn_plan_set_chain(ch, {"all_off": 0, "alternate": ch & 1, "all_on": 1}[pattern])
+        amps.zero_()
+        p.tn_contract(amps, prec, stream=stream)
+        p.tn_plan_check(stream=stream)
+        torch.cuda.synchronize()
+        err = rel_l2(amps.cpu().numpy().view(np.complex128), ref)
+        print(f"20q {prec} chains {pattern}: rel-L2 {err:.2e}, launches {p.info['launches_per_call']}")
+        assert err <= TOL[prec], (pattern, err)
+        if pattern == "all_off":
+            assert p.info["launches_per_call"] > launches_fused
+    times = p.tn_plan_autotune(prec, amps, reps=1, stream=stream)
+    on = p.tn_plan_get_chains()
+    print(f"20q {prec}: autotuner keeps {int(on.sum())} of {nch} chains fused")
+    amps.zero_()
+    p.tn_contract(amps, prec, stream=stream)
+    p.tn_plan_check(stream=stream)
+    torch.cuda.synchronize()
+    assert rel_l2(amps.cpu().numpy().view(np.complex128), ref) <= TOL[prec]
