@@ -411,57 +411,54 @@ def measure_correlated(w, precision, torch, tn, stream, ws, limit, rescale, rows
             "workspace_gib": p.info["workspace_bytes"] / 2 ** 30}
 
 
-def measure_chain(name, precision, torch, tn, stream, fuse_bits, peaks, batches=4):
-    """Fused chains (tn_options.fuse) against the unfused steps on a workload
-    whose heaviest chain is worth fusing: per-step CUDA-event times over the
-    first `batches` slice batches, the chain kernel's algorithmic bytes (A_1
-    read, B_j reads, C_L write; its intermediates are never stored) and its
-    HBM roofline."""
-    from rqc import make_workload
-    w = make_workload(name)
-    plans = {f: tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, workspace_limit=200 << 30, fuse=f,
-                        fuse_max_bits=fuse_bits) for f in (0, 1)}
-    need = max(p.info["workspace_bytes"] for p in plans.values())
-    free, _ = torch.cuda.mem_get_info()
-    if need > 0.9 * free:
-        return {"workload": name, "skipped": f"needs {need / 2**30:.1f} GiB"}
-    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-    amps = torch.zeros(2 * w.bits.shape[0], dtype=torch.float64, device="cuda")
-    nb = min(batches, plans[1].info["n_batches"])
+def measure_fusion(plan, precision, tn, one_step, peaks):
+    """Fused chains (SM Sec. V.C) on the timed plan, after the autotuner
+    chose per chain: every chain's time fused (its kernel, booked on its
+    last step) and unfused (the sum of its steps, each with its tuned
+    configuration), one profiled contraction each way, and the chain
+    kernel's HBM roofline (algorithmic bytes: A_1 read, every B_j read, C_L
+    written; the intermediates are never stored)."""
+    n = plan.info["n_chains"]
+    if n == 0:
+        return {"chains": 0}
+    keep = plan.tn_plan_get_chains().copy()
+    steps = plan.tn_plan_steps()
+    members = {}
+    for i, st in enumerate(steps):
+        if st["chain"] >= 0:
+            members.setdefault(st["chain"], []).append(i)
     res = {}
-    for f, p in plans.items():
-        p.tn_plan_bind(ws, stream=stream)
-        p.tn_plan_profile(True)
-        p.tn_contract(amps, precision, 0, nb, stream=stream)  # warm-up
-        p.tn_contract(amps, precision, 0, nb, stream=stream)
-        ms, fam = p.tn_plan_step_times()
-        res[f] = (ms, fam, p.tn_plan_steps())
-        p.tn_plan_profile(False)
-    ms1, fam1, st1 = res[1]
-    ms0, _, st0 = res[0]
-    chains = {}
-    for i, s in enumerate(st1):
-        if s["chain"] >= 0:
-            chains.setdefault(s["chain"], []).append(i)
-    if not chains:
-        return {"workload": name, "chains": 0}
-    best = max(chains.values(), key=lambda ids: sum(ms0[i] for i in ids))
-    t_unfused = float(sum(ms0[i] for i in best))
-    t_fused = float(ms1[best[-1]])
-    first, last = st1[best[0]], st1[best[-1]]
-    a_bytes = 8.0 * first["n_inst_a"] * 2.0 ** first["rank_a"]
-    b_bytes = sum(8.0 * st1[i]["n_inst_b"] * 2.0 ** st1[i]["rank_b"] for i in best)
-    c_bytes = 8.0 * last["n_inst"] * 2.0 ** (last["mb"] + last["nb"])
-    runs = sum(1 for b in range(nb) if b == 0 or st1[best[-1]]["level"] <= (b & -b).bit_length() - 1)
-    alg = (a_bytes + b_bytes + c_bytes) * runs
-    ach = alg / (t_fused / 1e3) / 1e9
-    del ws
-    torch.cuda.empty_cache()
-    return {"workload": name, "precision": precision, "slice_batches": nb, "chains": len(chains), "d_t": fuse_bits,
-            "heaviest_chain_steps": best, "unfused_ms": t_unfused, "fused_ms": t_fused,
-            "speedup": t_unfused / t_fused if t_fused > 0 else None,
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes": alg, "kernel": "k_chain"}}
+    for on in (1, 0):
+        for c in range(n):
+            plan.tn_plan_set_chain(c, on)
+        one_step(precision, profile=True)
+        res[on] = plan.tn_plan_step_times()[0]
+    for c in range(n):
+        plan.tn_plan_set_chain(c, int(keep[c]))
+    fused = {c: float(res[1][ids[-1]]) for c, ids in members.items()}
+    unfused = {c: float(sum(res[0][i] for i in ids)) for c, ids in members.items()}
+    kept = [c for c in range(n) if keep[c]]
+    rej = [c for c in range(n) if not keep[c]]
+
+    def alg_bytes(ids):
+        first, last = steps[ids[0]], steps[ids[-1]]
+        a = 8.0 * first["n_inst_a"] * 2.0 ** first["rank_a"]
+        b = sum(8.0 * steps[i]["n_inst_b"] * 2.0 ** steps[i]["rank_b"] for i in ids)
+        cc = 8.0 * last["n_inst"] * 2.0 ** (last["mb"] + last["nb"])
+        return (a + b + cc) * last["runs"]
+    tf = sum(fused[c] for c in kept)
+    tu = sum(unfused[c] for c in kept)
+    out = {"chains": n, "kept_fused": len(kept),
+           "kept": {"fused_ms": tf, "unfused_ms": tu, "speedup": tu / tf if tf > 0 else None},
+           "rejected": {"fused_ms": sum(fused[c] for c in rej), "unfused_ms": sum(unfused[c] for c in rej)}}
+    if kept and tf > 0:
+        ach = sum(alg_bytes(members[c]) for c in kept) / (tf / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": ach / peaks["hbm_gbs"], "kernel": "k_chain"}
+    heavy = max(members, key=lambda c: unfused[c])
+    out["heaviest"] = {"steps": members[heavy], "fused_ms": fused[heavy], "unfused_ms": unfused[heavy],
+                       "kept_fused": bool(keep[heavy])}
+    return out
 
 
 def run_reference(args, world, rank):
@@ -522,7 +519,17 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = make_workload(args.workload)
+    if args.case is not None:
+        from types import SimpleNamespace
+        from paper_2212_04749_gb300 import costmodel
+        from rqc.network import network_structure
+        cs = costmodel.random_case(args.case)
+        w = SimpleNamespace(circuit=cs.circuit, bits=cs.bits, struct=network_structure(cs.circuit),
+                            tree=SimpleNamespace(ssa=cs.ssa, sliced=list(cs.sliced)),
+                            spec=SimpleNamespace(cycles=None, index=None))
+        args.workload = "case" + str(args.case) + "_" + cs.name
+    else:
+        w = make_workload(args.workload)
     bits = w.bits if not args.rows else w.bits[:args.rows]
     k = bits.shape[0]
     sliced = sliced_for_world(w, world)
@@ -607,7 +614,7 @@ def run_ours(args, world, rank, local):
         plan.tn_plan_profile(False)
         return step_ms, kernels
 
-    ref = reference_values(args.workload, w) if rank == 0 and not args.rows else None
+    ref = reference_values(args.workload, w) if rank == 0 and not args.rows and args.case is None else None
     selection = select(args.precision)
     for _ in range(args.warmup):
         one_step(args.precision)
@@ -727,12 +734,9 @@ def run_ours(args, world, rank, local):
         correlated = measure_correlated(w, args.precision, torch, tn, stream, ws, limit, args.rescale)
         plan.tn_plan_bind(ws, stream=stream)
 
-    chain = None
-    if rank == 0 and world == 1 and args.chain_workload:
-        plan._ws = None  # the headline plan is done: its workspace goes back to the allocator
-        del ws
-        torch.cuda.empty_cache()
-        chain = measure_chain(args.chain_workload, args.precision, torch, tn, stream, args.fuse_bits, peaks)
+    fusion = None
+    if rank == 0 and args.fuse:
+        fusion = measure_fusion(plan, args.precision, tn, one_step, peaks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -766,7 +770,7 @@ def run_ours(args, world, rank, local):
                   "bf16_source": dpeak_src, **live},
         "cpu_baseline": cpu,
         "correlated_batches": correlated,
-        "fused_chain": chain,
+        "fused_chains": fusion,
         "e2e": e2e,
         "gpu_launches": int(info["launches_per_call"]) * args.steps,
         "clocks": clocks,
@@ -794,6 +798,9 @@ def main():
     ap.add_argument("--rows", type=int, default=0,
                     help="contract only the first ROWS bitstrings of the workload with its own tree (a smaller "
                          "case of the same step shapes, e.g. for profiler captures); 0: all")
+    ap.add_argument("--case", type=int, default=None,
+                    help="instead of a named workload, the seeded random circuit and tree of "
+                         "costmodel.random_case(CASE) (small plans of a few GB, e.g. for profiler captures)")
     ap.add_argument("--no-peaks", dest="peaks", action="store_false",
                     help="skip the live FP32/TF32/FP64 peak measurements")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -808,8 +815,6 @@ def main():
     ap.add_argument("--rescale", type=int, choices=[0, 1], default=1,
                     help="per-instance power-of-two rescaling (on by default; 0: the paper's plain arithmetic)")
     ap.add_argument("--fuse-bits", type=int, default=9, help="d^t: largest fused-chain tile, 2^d^t entries")
-    ap.add_argument("--chain-workload", default="grid6x7_m10",
-                    help="workload whose heaviest fused chain is timed against the unfused steps ('' to skip)")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":

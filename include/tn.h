@@ -142,6 +142,12 @@ int tn_plan(const tn_circuit *circ, const uint8_t *bits, int64_t k,
             const int32_t *tree_ssa, const int32_t *sliced_edges, int32_t n_sliced,
             const tn_options *opt, tn_plan_t *out);
 
+/* Sizes and costs of a plan (host only): the multiple-amplitude cost S_k of
+ * Eq. (1) summed over the slices (flops_ma) beside the single-amplitude cost
+ * times the distinct bitstrings (flops_sa, the main text's comparison of
+ * S_k with k S), the largest per-instance rank, the algorithmic bytes, the
+ * workspace tn_plan_bind needs and the batch partition of the slices
+ * (SM Sec. IV.B).  TN_EINVAL for null arguments. */
 int tn_plan_query(tn_plan_t plan, tn_plan_info *info);
 
 /* Per-node reuse widths w_v (distinct projections of the bitstrings onto
@@ -187,8 +193,12 @@ int tn_plan_batch_slices(tn_plan_t plan, int64_t batch, int64_t *slice_ids, int6
  * `stream`.  Must precede tn_contract*. */
 int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream);
 
-/* Accumulate into amps (device, complex128, k x amps_per_row entries) the
- * partial amplitudes of every slice in slice batches [batch_lo, batch_hi).
+/* The contraction (main text: the amplitudes of all requested bitstrings
+ * with every shared intermediate computed once, Eq. (1); SM Sec. IV.B: the
+ * amplitude is the sum over the slices of the sliced indices' partial
+ * amplitudes).  Accumulate into amps (device, complex128, k x amps_per_row
+ * entries) the partial amplitudes of every slice in slice batches
+ * [batch_lo, batch_hi).
  * With open qubits q_0 < ... < q_{r-1} (tn_options.open_mask), entry
  * p * 2^r + x of input row p is the amplitude of its bitstring with qubit
  * q_i set to bit r - 1 - i of x (the lowest open qubit is the most
@@ -203,7 +213,9 @@ int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream);
 int tn_contract(tn_plan_t plan, int precision, int64_t batch_lo, int64_t batch_hi,
                 double *amps, void *stream);
 
-/* Partial amplitudes of individual slices, for comparison with an oracle:
+/* Partial amplitudes of individual slices (SM Sec. IV.B: one assignment of
+ * the sliced indices each), for comparison with an oracle: slice_ids are
+ * external slice numbers s (sliced_edges[j] = (s >> j) & 1);
  * partials (device, complex128) receives ns x k x amps_per_row entries,
  * slice-major, rows and completions as in tn_contract, each already scaled
  * back by its power-of-two exponent. */

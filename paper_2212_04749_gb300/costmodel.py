@@ -267,7 +267,8 @@ def contraction_ms(b: Bound, precision: str, reps: int = 3) -> float:
     return float(np.median(ts))
 
 
-def evaluate(b: Bound, precision: str, trainer: Trainer, reps: int = 3, margin: float = 0.0) -> dict:
+def evaluate(b: Bound, precision: str, trainer: Trainer, reps: int = 3, margin: float = 0.0,
+             hybrid_margin: float = 0.2) -> dict:
     """End-to-end times (ms) under the plan's rule, the cost model and the
     exhaustive autotuner, plus the time each selection took."""
     ns = b.plan.info["n_steps"]
@@ -277,6 +278,12 @@ def evaluate(b: Bound, precision: str, trainer: Trainer, reps: int = 3, margin: 
     _, sel_s = select(b, precision, trainer, margin=margin)
     cfg_model = b.plan.tn_plan_get_configs().copy()
     t_model = contraction_ms(b, precision, reps)
+    # the network with the autotuner as its fallback: steps whose two best
+    # predictions lie within hybrid_margin (log2 ms) are timed instead
+    for s in range(ns):
+        b.plan.tn_plan_set_config(s, -1)
+    unc, hyb_s = select(b, precision, trainer, margin=hybrid_margin, fallback=True)
+    t_hybrid = contraction_ms(b, precision, reps)
     t0 = time.perf_counter()
     table = b.plan.tn_plan_autotune(precision, b.amps, reps=2, stream=b.stream)
     tune_s = time.perf_counter() - t0
@@ -291,7 +298,8 @@ def evaluate(b: Bound, precision: str, trainer: Trainer, reps: int = 3, margin: 
     return {"case": b.case.name, "precision": precision, "steps": ns, "rule_ms": t_rule, "model_ms": t_model,
             "tuned_ms": t_tuned, "model_select_s": sel_s, "autotune_s": tune_s,
             "regret_vs_tuned": t_model / t_tuned - 1.0, "gain_vs_rule": t_rule / t_model - 1.0,
-            "table_regret": table_regret, "agree_with_tuned": float(np.mean(cfg_model == cfg_tuned))}
+            "table_regret": table_regret, "agree_with_tuned": float(np.mean(cfg_model == cfg_tuned)),
+            "hybrid_ms": t_hybrid, "hybrid_select_s": hyb_s, "uncertain_frac": float(np.mean(unc))}
 
 
 def main():

@@ -182,26 +182,38 @@ def test_cost_model_gain_over_the_rule_and_regret():
     rows = []
     for s in (10002, 10006, 10015):  # held-out plans of 1.5e11-2e11 flops
         b = cm.bind(cm.random_case(s))
-        if b is None:
-            continue
+        assert b is not None, f"held-out case {s} did not bind"
         for prec in ("fp32", "bf16x3"):
             r = cm.evaluate(b, prec, tr, reps=3)
             rows.append(r)
             print(f"{r['case']} {prec}: rule {r['rule_ms']:.3f} ms, model {r['model_ms']:.3f} ms "
-                  f"(selection {r['model_select_s'] * 1e3:.1f} ms), autotuner {r['tuned_ms']:.3f} ms "
-                  f"(tuning {r['autotune_s']:.2f} s), table regret {r['table_regret']:+.3f}")
+                  f"(selection {r['model_select_s'] * 1e3:.1f} ms), model + fallback {r['hybrid_ms']:.3f} ms "
+                  f"({r['uncertain_frac']:.0%} of steps timed, {r['hybrid_select_s']:.2f} s), autotuner "
+                  f"{r['tuned_ms']:.3f} ms (tuning {r['autotune_s']:.2f} s), table regret {r['table_regret']:+.3f}")
         del b
-    assert rows
+    assert len(rows) == 6
     rule = sum(r["rule_ms"] for r in rows)
     model = sum(r["model_ms"] for r in rows)
+    hybrid = sum(r["hybrid_ms"] for r in rows)
     tuned = sum(r["tuned_ms"] for r in rows)
     sel = sum(r["model_select_s"] for r in rows)
+    hsel = sum(r["hybrid_select_s"] for r in rows)
     tune = sum(r["autotune_s"] for r in rows)
     print(f"cost model: corpus {len(corpus.y)} rows, fit mse {fit_mse:.3f} (log2 ms)^2; "
-          f"total rule {rule:.2f} ms, model {model:.2f} ms, autotuner {tuned:.2f} ms; "
-          f"selection {sel:.3f} s vs autotuning {tune:.2f} s")
-    # the network's choice is no slower than the rule (beyond timing noise),
-    # within 25 % of the autotuner, and costs a small fraction of tuning
-    assert model <= 1.10 * rule
-    assert model <= 1.25 * tuned
-    assert sel < 0.2 * tune
+          f"total rule {rule:.2f} ms, model {model:.2f} ms, model + fallback {hybrid:.2f} ms, "
+          f"autotuner {tuned:.2f} ms; selection {sel:.3f} s / {hsel:.2f} s vs autotuning {tune:.2f} s")
+    # Gain of the learned part, per plan and precision (geometric mean of
+    # rule time / chosen time; some plans leave nothing to gain, the
+    # autotuner itself is 1-11 % faster than the rule on these): the network
+    # with its autotuner fallback beats the rule by more than the run-to-run
+    # noise of these timings (about 1 %), stays within 3 % of the exhaustive
+    # autotuner and takes less than half its time; the network alone (no
+    # measurement at all) stays within 5 % of the autotuner.
+    gain = float(np.exp(np.mean([np.log(r["rule_ms"] / r["hybrid_ms"]) for r in rows])))
+    gain_tuned = float(np.exp(np.mean([np.log(r["rule_ms"] / r["tuned_ms"]) for r in rows])))
+    print(f"geometric-mean gain over the rule: model + fallback {gain:.3f}, autotuner {gain_tuned:.3f}")
+    assert gain >= 1.02
+    assert hybrid <= 1.03 * tuned
+    assert hsel < 0.5 * tune
+    assert model <= 1.05 * tuned
+    assert sel < 0.05 * tune
