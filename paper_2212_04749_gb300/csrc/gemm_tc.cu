@@ -36,6 +36,7 @@
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // code in *err, skips the remaining work, frees its TMEM and returns.
 #include <algorithm>
+#include <type_traits>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -322,6 +323,8 @@ struct EpiMap {
     int32_t rank[9];      // compressed position of warp bit b (rows 0-4, columns 0-3)
     int32_t pair;         // doff[0] == 1: compressed elements 2u, 2u+1 are one 16-byte store
     int32_t nrows;        // valid rows per tile (min(M, 128))
+    int32_t direct;       // narrow tiles with C bit 0 = row bit 0: each lane stores its row's columns
+    int64_t coff[16];     // direct stores: C offset of tile column c (a group's columns start at 0)
 };
 
 struct Ctrl {
@@ -557,8 +560,17 @@ __device__ __forceinline__ void tmem_ld(uint32_t ta, uint32_t *r) {
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                      : "r"(ta));
+    } else if constexpr (NR == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(ta));
     } else {
-        static_assert(NR == 16, "16 columns at most");
+        static_assert(NR == 16, "32 columns at most");
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -567,43 +579,44 @@ __device__ __forceinline__ void tmem_ld(uint32_t ta, uint32_t *r) {
     }
 }
 
-// B dictionary epilogue: the 8 tile columns cp .. cp + 7 of a pass, in runs
-// of R (one instance each), each run read from the accumulator columns its
-// instance's B occupies; runs past the tile's valid columns read as zeros.
-template <int R>
-__device__ __forceinline__ void tmem_gather(float (&v)[16], uint32_t tb, const EpiMeta &em, int cp, int ncv) {
-    uint32_t r[16];
+// B dictionary, a warp block of 16 columns c0 .. c0 + 15: every run of R
+// columns (one instance) from the accumulator columns its instance's B
+// occupies; all loads issued before one wait.  Columns past the tile's
+// valid ones read as zeros.
+template <int NC, int R>
+__device__ __forceinline__ void tmem_gather16(uint32_t (&r)[32], uint32_t tb, const EpiMeta &em, int c0, int ncv) {
 #pragma unroll
-    for (int j = 0; j < 8 / R; ++j) tmem_ld<2 * R>(tb + 2u * uint32_t(em.acol[cp + j * R]), r + 2 * j * R);
+    for (int j = 0; j < NC / R; ++j) tmem_ld<2 * R>(tb + 2u * uint32_t(em.acol[c0 + j * R]), r + 2 * j * R);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 8 / R; ++j) {
-        const bool ok = cp + j * R < ncv;
+    for (int j = 0; j < NC / R; ++j) {
+        const bool ok = c0 + j * R < ncv;
 #pragma unroll
-        for (int q = 0; q < 2 * R; ++q) v[2 * j * R + q] = ok ? __uint_as_float(r[2 * j * R + q]) : 0.f;
+        for (int q = 0; q < 2 * R; ++q) r[2 * j * R + q] = ok ? r[2 * j * R + q] : 0u;
     }
 }
 
-// Epilogue max-|component| of one pass (8 complex columns; v: 16
-// accumulator values of this lane's row) over runs of RUN columns (one
-// instance each): folded in registers, one warp reduction per run, scaled
-// by the run's power of two (exact; SCALED: the values carry it already) and
-// merged into the slot's entry at the run's first column.  Columns past the
-// tile's valid ones hold zeros (their B columns are zero) and merge nothing.
-template <int RUN, bool SCALED>
-__device__ __forceinline__ void fold_max8(const float *v, EpiMeta &em, int c0, int lane) {
-    uint32_t a[8];
+// Max-|component| of a warp block (16 complex columns; r: this lane's 32
+// accumulator values as float bits) over runs of RUN columns (one instance
+// each): folded in registers, one warp reduction per run, scaled by the
+// run's power of two (exact; SCALED: the values carry it already) and merged
+// into the slot's entry at the run's first column.  Columns past the tile's
+// valid ones hold zeros and merge nothing.
+template <int NC, int RUN, bool SCALED>
+__device__ __forceinline__ void fold_max16(const uint32_t (&r)[32], EpiMeta &em, int c0, int lane) {
+    uint32_t a[NC];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = __float_as_uint(fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
+    for (int j = 0; j < NC; ++j)
+        a[j] = __float_as_uint(fmaxf(fabsf(__uint_as_float(r[2 * j])), fabsf(__uint_as_float(r[2 * j + 1]))));
 #pragma unroll
     for (int s = 1; s < RUN; s <<= 1)
 #pragma unroll
-        for (int j = 0; j < 8; j += 2 * s) a[j] = max(a[j], a[j + s]);
+        for (int j = 0; j < NC; j += 2 * s) a[j] = max(a[j], a[j + s]);
 #pragma unroll
-    for (int j = 0; j < 8; j += RUN) {
-        const uint32_t r = __reduce_max_sync(0xffffffffu, a[j]);
-        if (lane == 0 && r)
-            atomicMax(&em.mx[c0 + j], SCALED ? r : __float_as_uint(__uint_as_float(r) * em.sc[c0 + j]));
+    for (int j = 0; j < NC; j += RUN) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, a[j]);
+        if (lane == 0 && m)
+            atomicMax(&em.mx[c0 + j], SCALED ? m : __float_as_uint(__uint_as_float(m) * em.sc[c0 + j]));
     }
 }
 
@@ -719,6 +732,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         }
         mp.pair = mp.doff[0] == 1;
         mp.nrows = d.mb >= 7 ? TBM : (1 << d.mb);
+        // Narrow tiles (one tile per group, at most 8 columns) whose C
+        // layout puts row bit 0 at address bit 0: lanes (rows) store
+        // neighbouring elements, so the registers go out without staging
+        mp.direct = (ow <= 8 && d.mb >= 7 && d.pCm[0] == 0) ? 1 : 0;
+        for (int c = 0; c < 16; ++c)
+            mp.coff[c] = c < (1 << d.nb) * d.max_group
+                             ? int64_t(c >> d.nb) * d.sC + dep(int64_t(c & ((1 << d.nb) - 1)), d.pCn, d.nb)
+                             : 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -1141,6 +1162,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         const bool pair = mp.pair != 0;
         const bool rows_ok = lanegrp * 32 < mp.nrows;  // M = 64: quadrants 2 and 3 hold no rows
         const int64_t qoff = mp.qoff[lanegrp];
+        const bool direct = mp.direct != 0;
+        int64_t laneoff = 0;  // direct stores: C offset of this lane's row within its quadrant
+#pragma unroll
+        for (int b = 0; b < 5; ++b)
+            if (b < d.mb && ((lane >> b) & 1)) laneoff += int64_t(1) << d.pCm[b];
         for (int64_t l = narrow ? sub : 0; l < my_tiles; l += narrow ? 2 : 1) {
             const int acc = int(l & (nacc - 1)), slot = int(l % MS);
             bool w = mbar_wait(&X.mfull[slot], uint32_t(l / MS) & 1u);
@@ -1153,76 +1179,85 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             EpiMeta &em = X.epi[slot];
             const int ncv = em.ncv;
             const int nh = ncv > TBN / 2 ? 2 : 1;
-            // passes of 8 columns this warp reads from the accumulator
-            // (non-dictionary narrow tiles of 8 columns: one)
+            // halves of 8 columns this warp reads from the accumulator
+            // (non-dictionary tiles of 8 columns: one)
             const int npass = (MODE != 2 && acw < 16) ? 1 : 2;
             for (int h = 0; h < nh; ++h) {
                 const int c0 = narrow ? 0 : h * 32 + sub * 16;  // first column of this warp's block
                 const bool act = rows_ok && c0 < ncv;  // warp-uniform
-                // two passes of 8 complex columns (16 accumulator columns)
+                // the block's complex columns (16, or 8 where no tile has
+                // more: NC), every load issued before one wait
+                auto block = [&](auto nc_) {
+                    constexpr int NC = decltype(nc_)::value;
+                    uint32_t r[32];
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    float v[16];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = 0.f;
+                    for (int q = 0; q < 32; ++q) r[q] = 0u;
                     if (act && MODE == 2) {
-                        // dictionary: each run of the pass from its own accumulator columns
                         const uint32_t tb = tmem + uint32_t(acc) * awr + (uint32_t(lanegrp * 32) << 16);
-                        const int cp = c0 + 8 * p;
-                        switch (N < 8 ? N : 8) {
-                            case 1: tmem_gather<1>(v, tb, em, cp, ncv); break;
-                            case 2: tmem_gather<2>(v, tb, em, cp, ncv); break;
-                            case 4: tmem_gather<4>(v, tb, em, cp, ncv); break;
-                            default: tmem_gather<8>(v, tb, em, cp, ncv); break;
+                        switch (N < NC ? N : NC) {
+                            case 1: tmem_gather16<NC, 1>(r, tb, em, c0, ncv); break;
+                            case 2: tmem_gather16<NC, 2>(r, tb, em, c0, ncv); break;
+                            case 4: tmem_gather16<NC, 4>(r, tb, em, c0, ncv); break;
+                            case 8: tmem_gather16<NC, 8>(r, tb, em, c0, ncv); break;
+                            default: tmem_gather16<NC, NC>(r, tb, em, c0, ncv); break;
                         }
-                    } else if (act && p < npass) {
-                        const uint32_t ta = tmem + uint32_t(acc) * awr + uint32_t((c0 + 8 * p) * 2) +
-                                            (uint32_t(lanegrp * 32) << 16);
-                        uint32_t r[16];
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                              "=r"(r[14]), "=r"(r[15])
-                            : "r"(ta));
+                    } else if (act) {
+                        const uint32_t ta =
+                            tmem + uint32_t(acc) * awr + uint32_t(c0 * 2) + (uint32_t(lanegrp * 32) << 16);
+                        if (NC == 16 && npass == 2) tmem_ld<16>(ta + 16u, r + 16);
+                        tmem_ld<16>(ta, r);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
                     }
-                    if (h == nh - 1 && p == 1) {  // the accumulator is free for a later tile
+                    if (h == nh - 1) {  // the accumulator is free for a later tile
                         tc_fence_before();
                         mbar_arrive(&X.tempty[acc]);
                     }
-                    if (!act) continue;
-                    const int cp = c0 + 8 * p;  // first column of this pass
+                    if (!act) return;
                     if (d.mxC) {
-                        switch (N < 8 ? N : 8) {
-                            case 1: fold_max8<1, MODE == 1>(v, em, cp, lane); break;
-                            case 2: fold_max8<2, MODE == 1>(v, em, cp, lane); break;
-                            case 4: fold_max8<4, MODE == 1>(v, em, cp, lane); break;
-                            default: fold_max8<8, MODE == 1>(v, em, cp, lane); break;
+                        switch (N < NC ? N : NC) {
+                            case 1: fold_max16<NC, 1, MODE == 1>(r, em, c0, lane); break;
+                            case 2: fold_max16<NC, 2, MODE == 1>(r, em, c0, lane); break;
+                            case 4: fold_max16<NC, 4, MODE == 1>(r, em, c0, lane); break;
+                            case 8: fold_max16<NC, 8, MODE == 1>(r, em, c0, lane); break;
+                            default: fold_max16<NC, NC, MODE == 1>(r, em, c0, lane); break;
                         }
+                    }
+                    if (NC == 8 && direct) {
+                        // each lane its row's valid columns, straight from registers
+                        float2 *rowp = d.C + (em.base + qoff + laneoff);
+#pragma unroll
+                        for (int jj = 0; jj < NC; ++jj) {
+                            if (jj >= ncv) break;
+                            const float sv = MODE == 1 ? 1.f : em.sc[jj];
+                            rowp[mp.coff[jj]] =
+                                make_float2(__uint_as_float(r[2 * jj]) * sv, __uint_as_float(r[2 * jj + 1]) * sv);
+                        }
+                        return;
                     }
                     // scale and stage in destination order
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const float4 sc4 = *reinterpret_cast<const float4 *>(&em.sc[cp + 4 * q]);
+                    for (int q = 0; q < NC / 4; ++q) {
+                        const float4 sc4 = *reinterpret_cast<const float4 *>(&em.sc[c0 + 4 * q]);
                         const float scq[4] = {sc4.x, sc4.y, sc4.z, sc4.w};
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
-                            const int jj = 8 * p + 4 * q + t;  // column within the warp's block
+                            const int jj = 4 * q + t;  // column within the warp's block
                             int a = arow;
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
                                 if ((jj >> j) & 1) a ^= acol[j];
                             // resident B carries the rescale already
-                            const float s = MODE == 1 ? 1.f : scq[t];
+                            const float sv = MODE == 1 ? 1.f : scq[t];
                             *reinterpret_cast<float2 *>(wst + a) =
-                                make_float2(v[2 * (4 * q + t)] * s, v[2 * (4 * q + t) + 1] * s);
+                                make_float2(__uint_as_float(r[2 * jj]) * sv, __uint_as_float(r[2 * jj + 1]) * sv);
                         }
                     }
-                }
-                if (!act) continue;
+                };
+                if (ow <= 8)
+                    block(std::integral_constant<int, 8>());
+                else
+                    block(std::integral_constant<int, 16>());
+                if (!act || direct) continue;
                 const int ncw = ncv - c0;  // valid columns of this block
                 __syncwarp();
                 const int64_t wb = em.base + qoff + mp.hoff[narrow ? 0 : h * 2 + sub] + offL;
