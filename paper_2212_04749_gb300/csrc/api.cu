@@ -496,6 +496,7 @@ int tn_plan_bind(tn_plan_t plan, void *workspace, size_t bytes, void *stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     CU(tnk::init_kernels());
     CU(tnk::init_chain_kernel());
+    CU(tnk::init_simt_kernels());
     o->drop_graphs();
     o->ws = static_cast<uint8_t *>(workspace);
     o->ws_bytes = bytes;

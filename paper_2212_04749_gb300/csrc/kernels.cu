@@ -478,6 +478,173 @@ __global__ void __launch_bounds__(256) k_step_gemm_simt(const StepDesc d, int ct
     }
 }
 
+// Grouped SIMT complex GEMM, FP32 FMA, K >= 2: the same 128 x 64 tiles
+// and block order as k_step_gemm_simt, 128 threads of 8 x 8 complex
+// outputs each (rows tm + 16 x, columns 8 tn + y), K in chunks of up to 16
+// staged in shared memory by cp.async in two stages, so that a chunk's
+// loads run while the previous chunk is multiplied.  Shared memory holds A
+// and B K-contiguous per row / column (the operands' own order), rows
+// padded to 18 complex (144 bytes) so that the 16-byte reads of eight lanes
+// on consecutive rows touch every bank once.
+constexpr int SBM = 128, SBN = 64, SBK = 16, SLD = 18;
+constexpr size_t SIMT2_SMEM = size_t(2) * (SBM + SBN) * SLD * sizeof(float2);
+
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+
+__global__ void __launch_bounds__(128) k_step_gemm_simt2(const StepDesc d, int ctiles, int mtiles) {
+    extern __shared__ __align__(16) float2 s2[];
+    __shared__ int64_t s_offC[SBM];
+    __shared__ int64_t s_bbase[SBN], s_cbase[SBN];
+    __shared__ int32_t s_eb[SBN];
+    __shared__ uint32_t s_mx[SBN];
+    __shared__ int64_t s_ia;
+    __shared__ int s_ea;
+    const int tid = threadIdx.x;
+    const int64_t bid = blockIdx.x;
+    int mt, ct;
+    int64_t g;
+    if (d.sched == 0) {
+        mt = int(bid % mtiles);
+        const int64_t rest = bid / mtiles;
+        ct = int(rest % ctiles);
+        g = rest / ctiles;
+    } else {
+        ct = int(bid % ctiles);
+        const int64_t rest = bid / ctiles;
+        mt = int(rest % mtiles);
+        g = rest / mtiles;
+    }
+    const int64_t i0 = d.gfirst[g];
+    const int64_t icount = d.gfirst[g + 1] - i0;
+    const int N = 1 << d.nb;
+    const int64_t M = int64_t(1) << d.mb;
+    const int K = 1 << d.kb;
+    const int64_t cols = icount * N;
+    const int64_t c0 = int64_t(ct) * SBN;
+    if (c0 >= cols) return;  // uniform across the block
+    const int64_t m0 = int64_t(mt) * SBM;
+    if (tid == 0) {
+        const int64_t sig = i0 / d.nOut, beta = i0 - sig * d.nOut;
+        s_ia = int64_t(d.sigA[sig]) * d.nOutA + d.outA[beta];
+        s_ea = d.mxA ? exp_of(d.mxA[s_ia]) : 0;
+    }
+    __syncthreads();
+    {
+        const int64_t m = m0 + tid;
+        s_offC[tid] = m < M ? dep(m, d.pCm, d.mb) : 0;
+    }
+    if (tid < SBN) {
+        const int c = tid;
+        const int64_t gc = c0 + c;
+        s_mx[c] = 0;
+        if (gc < cols) {
+            const int64_t inst = i0 + gc / N;
+            const int n = int(gc % N);
+            const int64_t sig = inst / d.nOut, beta = inst - sig * d.nOut;
+            const int64_t ib = int64_t(d.sigB[sig]) * d.nOutB + d.outB[beta];
+            s_bbase[c] = ib * d.sB + (int64_t(n) << d.kb);  // B is K-major and affine
+            s_cbase[c] = inst * d.sC + dep(n, d.pCn, d.nb);
+            const int eb = d.mxB ? exp_of(d.mxB[ib]) : 0;
+            s_eb[c] = eb;
+            if (n == 0 && mt == 0) d.EC[inst] = d.EA[s_ia] + s_ea + d.EB[ib] + eb;
+        } else {
+            s_bbase[c] = -1;
+            s_cbase[c] = -1;
+            s_eb[c] = 0;
+        }
+    }
+    __syncthreads();
+    const float2 *A = d.A + s_ia * d.sA;  // row m at m * K: K-major and affine
+    const int bk = K < SBK ? K : SBK;      // complex k per chunk (even: K >= 2)
+    const int pieces = bk >> 1;            // 16-byte pieces per row / column and chunk
+    const int nchunk = K / bk;
+    // stage st: A at s2 + st * SBM * SLD, B at s2 + 2 * SBM * SLD + st * SBN * SLD
+    // one chunk's cp.async: piece q of row r at (r, 2q); consecutive threads
+    // take consecutive pieces of a row (coalesced)
+    auto issue = [&](int ch, int st) {
+        const int k0 = ch * bk;
+        for (int e = tid; e < SBM * pieces; e += 128) {
+            const int r = e / pieces, q = e - r * pieces;
+            const bool v = m0 + r < M;
+            const float2 *src = v ? A + ((m0 + r) << d.kb) + k0 + 2 * q : A;
+            cp_async16_zfill(static_cast<uint32_t>(__cvta_generic_to_shared(s2 + st * SBM * SLD + r * SLD + 2 * q)), src,
+                             v);
+        }
+        for (int e = tid; e < SBN * pieces; e += 128) {
+            const int c = e / pieces, q = e - c * pieces;
+            const int64_t bb = s_bbase[c];
+            const bool v = bb >= 0;
+            const float2 *src = v ? d.B + bb + k0 + 2 * q : d.B;
+            cp_async16_zfill(
+                static_cast<uint32_t>(__cvta_generic_to_shared(s2 + 2 * SBM * SLD + st * SBN * SLD + c * SLD + 2 * q)),
+                src, v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int tm = tid & 15, tn = tid >> 4;
+    float2 acc[8][8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = make_float2(0.f, 0.f);
+    issue(0, 0);
+    for (int ch = 0; ch < nchunk; ++ch) {
+        if (ch + 1 < nchunk) {
+            issue(ch + 1, (ch + 1) & 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const float2 *a_s = s2 + (ch & 1) * SBM * SLD + tm * SLD;
+        const float2 *b_s = s2 + 2 * SBM * SLD + (ch & 1) * SBN * SLD + (8 * tn) * SLD;
+        for (int kk = 0; kk < bk; kk += 2) {
+            float4 a[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) a[x] = *reinterpret_cast<const float4 *>(a_s + 16 * x * SLD + kk);
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+                const float4 b = *reinterpret_cast<const float4 *>(b_s + y * SLD + kk);
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    cfma(acc[x][y], make_float2(a[x].x, a[x].y), make_float2(b.x, b.y));
+                    cfma(acc[x][y], make_float2(a[x].z, a[x].w), make_float2(b.z, b.w));
+                }
+            }
+        }
+        __syncthreads();  // the stage is refilled two chunks later
+    }
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+        const int c = 8 * tn + y;
+        if (s_cbase[c] < 0) continue;
+        const float sc = pow2f(-(s_ea + s_eb[c]));
+        uint32_t mx = 0;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int r = tm + 16 * x;
+            if (m0 + r >= M) continue;
+            const float2 v = make_float2(acc[x][y].x * sc, acc[x][y].y * sc);
+            d.C[s_cbase[c] + s_offC[r]] = v;
+            mx = max(mx, absmax_bits(v));
+        }
+        if (d.mxC) {  // lanes tn*16 .. tn*16+15 share column c: reduce each half-warp first
+            const unsigned half = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
+            const uint32_t r = __reduce_max_sync(half, mx);
+            if (tm == 0 && r) atomicMax(&s_mx[c], r);
+        }
+    }
+    if (d.mxC) {
+        __syncthreads();
+        if (tid < SBN && s_cbase[tid] >= 0) {
+            const int64_t inst = i0 + (c0 + tid) / N;
+            record_max(d.mxC + inst, s_mx[tid]);
+        }
+    }
+}
+
 // root entry of completion x: its r bits reversed (root bit t = the t-th
 // lowest open qubit; x's most significant bit = the lowest open qubit)
 __device__ __forceinline__ int64_t root_entry(int64_t x, int r) {
@@ -705,8 +872,17 @@ cudaError_t launch_step_gemm_simt(const StepDesc &d, cudaStream_t s) {
     const int64_t blocks = d.n_groups * ctiles * mtiles;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL || ctiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_step_gemm_simt<<<dim3((unsigned)blocks), 256, 0, s>>>(d, (int)ctiles, (int)mtiles);
+    static_assert(SBM == GBM && SBN == GBN, "both SIMT GEMMs tile alike");
+    if (d.kb >= 1) {  // K >= 2: 16-byte pieces of A rows and B columns
+        k_step_gemm_simt2<<<dim3((unsigned)blocks), 128, SIMT2_SMEM, s>>>(d, (int)ctiles, (int)mtiles);
+    } else {
+        k_step_gemm_simt<<<dim3((unsigned)blocks), 256, 0, s>>>(d, (int)ctiles, (int)mtiles);
+    }
     return cudaGetLastError();
+}
+
+cudaError_t init_simt_kernels() {
+    return cudaFuncSetAttribute(k_step_gemm_simt2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SIMT2_SMEM));
 }
 
 cudaError_t launch_accumulate(const float2 *root, const int32_t *E, const int32_t *uniq, int64_t k,
