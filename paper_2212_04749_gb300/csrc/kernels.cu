@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int 
     __shared__ int64_t s_ib[ROW_CH];
     __shared__ int32_t s_e[ROW_CH], s_EC[ROW_CH];
     __shared__ uint32_t s_mx[ROW_CH];
+    __shared__ int64_t s_pass_off[16];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = 1 << d.kb;
     const int KN = K * N;
@@ -217,36 +218,59 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int 
                 s_EC[tid] = EAa + d.EB[ib] + eb;
                 s_mx[tid] = 0u;
             }
+            if (tid < passes) s_pass_off[tid] = dep(int64_t(tid) * 8 * R, s_pCm, mb);
             __syncthreads();
+            // B staged with each instance's power-of-two rescale folded in (exact)
             for (int e = tid; e < ch * KN; e += ROW_THREADS) {
                 const int j = e / KN;
-                s_B[e] = __ldg(d.B + s_ib[j] * d.sB + (e - j * KN));
+                const float sc = pow2f(-s_e[j]);
+                const float2 b = __ldg(d.B + s_ib[j] * d.sB + (e - j * KN));
+                s_B[e] = make_float2(b.x * sc, b.y * sc);
             }
             __syncthreads();
+            // row m = m0 + it 8R + (warp R + sub): three disjoint bit ranges,
+            // so its C offset is this lane's part plus the pass's part
+            const int64_t lane_off = dep(m0 + int64_t(warp) * R + sub, s_pCm, mb);
+            // max-|x| per instance: in registers across the passes when the
+            // chunk has at most 4 instances, reduced over the warp once
+            const bool few = ch <= 4;
+            uint32_t mxr[4] = {0u, 0u, 0u, 0u};
             for (int it = 0; it < passes; ++it) {
                 const int64_t m = m0 + (int64_t(it) * 8 + warp) * R + sub;
                 float2 a[KL];
                 load_row(a, ia, m, true);
-                const int64_t offC = (mb > 8 ? dep(m >> 8, s_pCm + 8, mb - 8) : 0) + s_mloC[m & 255];
+                const int64_t offC = lane_off + s_pass_off[it];
                 for (int j = 0; j < ch; ++j) {
                     float2 acc[N];
                     row_times_b(acc, a, s_B + j * KN);
-                    const float sc = pow2f(-s_e[j]);
                     float2 *C = d.C + (i0 + c0 + j) * d.sC + offC;
                     uint32_t mx = 0;
                     if (store_lane) {
 #pragma unroll
                         for (int h = 0; h < N; ++h) {
                             if (h >= n_held) break;
-                            const float2 v = make_float2(acc[h].x * sc, acc[h].y * sc);
-                            C[s_offCn[n0 + h]] = v;
-                            mx = max(mx, absmax_bits(v));
+                            C[s_offCn[n0 + h]] = acc[h];
+                            mx = max(mx, absmax_bits(acc[h]));
                         }
                     }
                     if (d.mxC) {
-                        const uint32_t r = __reduce_max_sync(0xffffffffu, mx);
-                        if (lane == 0 && r) atomicMax(&s_mx[j], r);
+                        if (few) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (q == j) mxr[q] = max(mxr[q], mx);
+                        } else {
+                            const uint32_t r = __reduce_max_sync(0xffffffffu, mx);
+                            if (lane == 0 && r) atomicMax(&s_mx[j], r);
+                        }
                     }
+                }
+            }
+            if (d.mxC && few) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q >= ch) break;
+                    const uint32_t r = __reduce_max_sync(0xffffffffu, mxr[q]);
+                    if (lane == 0 && r) atomicMax(&s_mx[q], r);
                 }
             }
             __syncthreads();
