@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int 
     const int KN = K * N;
     const int mb = d.mb;
     const int64_t M = int64_t(1) << mb;
-    const int L = K >= 16 ? 8 : (K >= 2 ? K / 2 : 1);
+    const int L = K / KL;  // lanes per row (row_lanes on the host)
     const int R = 32 / L;
     const int sub = lane / L, kl = lane % L;
     const int passes = rows_per_block / (8 * R);
@@ -235,10 +235,14 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int 
             // chunk has at most 4 instances, reduced over the warp once
             const bool few = ch <= 4;
             uint32_t mxr[4] = {0u, 0u, 0u, 0u};
+            // the next pass's A row is loaded while this pass computes
+            float2 a_nx[KL];
+            load_row(a_nx, ia, m0 + int64_t(warp) * R + sub, true);
             for (int it = 0; it < passes; ++it) {
-                const int64_t m = m0 + (int64_t(it) * 8 + warp) * R + sub;
                 float2 a[KL];
-                load_row(a, ia, m, true);
+#pragma unroll
+                for (int q = 0; q < KL; ++q) a[q] = a_nx[q];
+                if (it + 1 < passes) load_row(a_nx, ia, m0 + (int64_t(it + 1) * 8 + warp) * R + sub, true);
                 const int64_t offC = lane_off + s_pass_off[it];
                 for (int j = 0; j < ch; ++j) {
                     float2 acc[N];
@@ -843,12 +847,27 @@ cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *hi
     return cudaGetLastError();
 }
 
+// Lanes per row of the row kernel: as few as keep a lane's share of the
+// row's K * N products within 64 (fewer cross-lane sums per output), at
+// least K / 32 (a lane holds at most 32 complex A values) and at most 8
+// (and K / 2: a lane loads 16 bytes at a time).
+static int row_lanes(int kb, int nb) {
+    const int K = 1 << kb;
+    int L = (K << nb) >> 6;
+    L = L < 1 ? 1 : (L > 8 ? 8 : L);
+    if (L < K / 32) L = K / 32;
+    if (K >= 2 && L > K / 2) L = K / 2;
+    return L;
+}
+
 cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
     if (d.kb + d.nb > 8 || d.nb > 4 || d.mb > 40) return cudaErrorInvalidValue;
     const int K = 1 << d.kb;
-    const int L = K >= 16 ? 8 : (K >= 2 ? K / 2 : 1);
+    const int L = row_lanes(d.kb, d.nb);
     const int R = 32 / L;
     const int KL = K / L;
+    if ((d.nb == 4 && KL > 4) || (d.nb == 3 && KL > 8) || (d.nb == 2 && KL > 16) || KL > 32)
+        return cudaErrorInvalidValue;  // no instance of the kernel for this split
     const int64_t M = int64_t(1) << d.mb;
     int64_t blocks, mblocks = 1;
     int rows_per_block;
@@ -867,14 +886,16 @@ cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const dim3 g((unsigned)blocks);
 #define TN_ROW(NB_, KL_) k_step_row<NB_, KL_><<<g, ROW_THREADS, 0, s>>>(d, rows_per_block, mblocks)
-#define TN_ROW_KL(NB_)                         \
-    switch (KL) {                              \
-        case 1: TN_ROW(NB_, 1); break;         \
-        case 2: TN_ROW(NB_, 2); break;         \
-        case 4: TN_ROW(NB_, (NB_ <= 3 ? 4 : 2)); break;   \
-        case 8: TN_ROW(NB_, (NB_ <= 2 ? 8 : 2)); break;   \
-        case 16: TN_ROW(NB_, (NB_ <= 1 ? 16 : 2)); break; \
-        default: TN_ROW(NB_, (NB_ == 0 ? 32 : 2)); break; \
+    // KL = K / L for K * N <= 256: NB 0-1 up to 32, NB 2 up to 16, NB 3 up
+    // to 8, NB 4 up to 4 (row_lanes keeps 2 KL + 2 N <= 72 registers)
+#define TN_ROW_KL(NB_)                                         \
+    switch (KL) {                                              \
+        case 1: TN_ROW(NB_, 1); break;                         \
+        case 2: TN_ROW(NB_, 2); break;                         \
+        case 4: TN_ROW(NB_, 4); break;                         \
+        case 8: TN_ROW(NB_, (NB_ <= 3 ? 8 : 4)); break;        \
+        case 16: TN_ROW(NB_, (NB_ <= 2 ? 16 : 4)); break;      \
+        default: TN_ROW(NB_, (NB_ <= 1 ? 32 : 4)); break;      \
     }
     switch (d.nb) {
         case 0: TN_ROW_KL(0); break;
