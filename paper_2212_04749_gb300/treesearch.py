@@ -1,0 +1,286 @@
+"""Contraction-tree search ranked by predicted contraction time.
+
+The paper searches contraction orders with the multiple-amplitude cost S_k
+of main text Eq. (1) as the loss and refines the sliced set by lifetime
+(SM Sec. IV.A-B).  On GB300 the steps are bound by their bytes and shapes
+more than by their flops (a tree with 3x fewer Eq. (1) flops ran 2x slower),
+so this search ranks candidate trees by the time the learned cost model
+predicts for their steps:
+
+1. candidates: the seeded random-greedy trees of ``rqc.tree.candidate_trees``
+   and the neighbours of a start tree under *rotations* -- a node v = (x, y)
+   with y = (y1, y2) becomes ((x, y1), y2) or ((x, y2), y1), the two other
+   ways of pairing its three subtrees;
+2. a cheap filter: the candidate is sliced under the rank cap
+   (``rqc.tree.choose_slices``) and kept if its Eq. (1) flops stay within a
+   factor of the best seen;
+3. the ranking: the candidate is planned on the host (``tn.Plan``: instance
+   DAG, step shapes, runs), every (step, configuration) pair is scored by the
+   cost model (``Trainer.predict``: log2 ms per pass), each step takes its
+   fastest allowed configuration, and the predicted time is the sum over
+   steps of that time x the step's passes;
+4. a hill climb over rotations accepts a neighbour whose predicted time is
+   lower, from the best-ranked start;
+5. the best few are measured (plan, bind, autotune, contract) against the
+   start tree, so the choice rests on measured time.
+
+``python -m paper_2212_04749_gb300.treesearch --workload diamond53_m12``
+prints the ranking and the measurements as JSON.
+"""
+
+import json
+import time
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import costmodel, tn
+
+
+def _children(ssa: np.ndarray, T: int) -> Dict[int, Tuple[int, int]]:
+    return {T + i: (int(a), int(b)) for i, (a, b) in enumerate(np.asarray(ssa).reshape(-1, 2))}
+
+
+def _to_ssa(ch: Dict[int, Tuple[int, int]], root: int, T: int) -> np.ndarray:
+    """SSA pair list of a tree given as children per internal node: post
+    order from the root, internal nodes renumbered T, T+1, ... as they close."""
+    out: List[Tuple[int, int]] = []
+    ids: Dict[int, int] = {}
+    stack = [(root, False)]
+    while stack:
+        v, done = stack.pop()
+        if v < T:
+            continue
+        if done:
+            a, b = ch[v]
+            out.append((ids.get(a, a), ids.get(b, b)))
+            ids[v] = T + len(out) - 1
+        else:
+            stack.append((v, True))
+            a, b = ch[v]
+            stack.append((b, False))
+            stack.append((a, False))
+    return np.asarray(out, np.int64)
+
+
+def rotations(ssa: np.ndarray, T: int) -> List[np.ndarray]:
+    """Every tree one rotation away: for each internal v = (x, y) with y
+    internal, the two re-pairings ((x, y1), y2) and ((x, y2), y1), with x and
+    y taken in both orders."""
+    ch = _children(ssa, T)
+    root = 2 * T - 2
+    out = []
+    for v, (p, q) in ch.items():
+        for x, y in ((p, q), (q, p)):
+            if y < T:
+                continue
+            y1, y2 = ch[y]
+            for keep, move in ((y2, y1), (y1, y2)):
+                nch = dict(ch)
+                nch[y] = (x, move)   # y now pairs x with one of its children
+                nch[v] = (y, keep)   # v pairs that with the other
+                out.append(_to_ssa(nch, root, T))
+    return out
+
+
+class Ranker:
+    """Predicted contraction time of a tree for one workload."""
+
+    def __init__(self, circuit, bits, struct, trainer: costmodel.Trainer, precision: str,
+                 max_rank: Optional[int], workspace_limit: int):
+        self.circuit, self.bits, self.struct = circuit, bits, struct
+        self.k = bits.shape[0]
+        self.trainer, self.precision = trainer, precision
+        self.max_rank, self.limit = max_rank, workspace_limit
+
+    def slice(self, ssa):
+        from rqc.tree import ContractionTree, choose_slices, estimate_cost
+        c = estimate_cost(self.struct, ssa, self.k)
+        sl = []
+        if self.max_rank is not None and c.max_rank > self.max_rank:
+            sl = choose_slices(self.struct, ContractionTree(ssa=ssa), self.k, None, self.max_rank)
+            c = estimate_cost(self.struct, ssa, self.k, sl)
+        return sl, c
+
+    def predict(self, ssa, sl) -> Optional[dict]:
+        try:
+            p = tn.Plan(self.circuit, self.bits, ssa, sl, workspace_limit=self.limit, fuse=0)
+        except tn.TnError:
+            return None  # does not fit the workspace limit
+        n = p.info["n_steps"]
+        runs = np.array([s["runs"] for s in p.tn_plan_steps()], np.float64)
+        feats, ok = [], []
+        for c in range(tn.TN_NCONFIG):
+            f, e = p.tn_plan_features(self.precision, c)
+            feats.append(f)
+            ok.append(e)
+        y = self.trainer.predict(np.concatenate(feats)).reshape(tn.TN_NCONFIG, n)
+        ms = np.where(np.stack(ok), 2.0 ** y, np.inf).min(axis=0)
+        info = p.info
+        return {"predicted_ms": float(np.sum(ms * runs)), "flops_eq1": info["flops_ma"],
+                "bytes": info["bytes_min"], "workspace_gib": info["workspace_bytes"] / 2 ** 30,
+                "max_rank": info["max_rank"], "n_sliced": len(sl)}
+
+
+def measure(circuit, bits, ssa, sl, precision, workspace_limit, reps=3) -> Optional[float]:
+    """Contraction time (ms, CUDA events, median of reps) after the
+    exhaustive autotuner configured the plan."""
+    import torch
+    try:
+        p = tn.Plan(circuit, bits, ssa, sl, workspace_limit=workspace_limit, fuse=0)
+    except tn.TnError:
+        return None
+    ws = torch.empty(p.info["workspace_bytes"], dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    p.tn_plan_bind(ws, stream=st)
+    amps = torch.zeros(2 * bits.shape[0], dtype=torch.float64, device="cuda")
+    p.tn_plan_autotune(precision, amps, reps=1, stream=st)
+    ts = []
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        p.tn_contract(amps, precision, stream=st)
+        e1.record(st)
+        e1.synchronize()
+        if r:
+            ts.append(e0.elapsed_time(e1))
+    p.tn_plan_check(stream=st)
+    p._ws = None
+    del ws, amps, p
+    torch.cuda.empty_cache()
+    return float(np.median(ts))
+
+
+def search(ranker: Ranker, start: np.ndarray, seeds=(), trials=16, steps=40, flops_slack=1.5, per_step=150,
+           log=None):
+    """Rank the start tree and the random-greedy candidates, then hill-climb
+    over rotations from the best (per step at most per_step seeded random
+    neighbours, first improvement taken); returns every ranked tree, best
+    first."""
+    from rqc.tree import candidate_trees
+    T = ranker.struct.n_tensors
+    seen = {}
+
+    def rank(ssa):
+        key = np.asarray(ssa).tobytes()
+        if key in seen:
+            return seen[key]
+        sl, c = ranker.slice(ssa)
+        r = None
+        if ranker.max_rank is None or c.max_rank <= ranker.max_rank:
+            r = ranker.predict(ssa, sl)
+            if r is not None:
+                r.update({"ssa": np.asarray(ssa).tolist(), "sliced": [int(e) for e in sl]})
+        seen[key] = r
+        return r
+
+    ranked = [rank(start)]
+    for sd in seeds:
+        for ssa in candidate_trees(ranker.struct, ranker.k, sd, trials):
+            ranked.append(rank(ssa))
+    ranked = [r for r in ranked if r is not None]
+    best = min(ranked, key=lambda r: r["predicted_ms"])
+    if log:
+        log(f"start {ranked[0]['predicted_ms']:.1f} ms predicted; best of {len(ranked)} candidates "
+            f"{best['predicted_ms']:.1f} ms")
+    for it in range(steps):
+        cur = np.asarray(best["ssa"])
+        from rqc.tree import estimate_cost
+        base_flops = estimate_cost(ranker.struct, cur, ranker.k).flops
+        improved = False
+        nbrs = rotations(cur, T)
+        order = np.random.default_rng(it).permutation(len(nbrs))[:per_step]
+        for j in order:
+            ssa = nbrs[j]
+            if estimate_cost(ranker.struct, ssa, ranker.k).flops > flops_slack * base_flops:
+                continue
+            r = rank(ssa)
+            if r is not None and r["predicted_ms"] < best["predicted_ms"] * (1 - 1e-3):
+                best = r
+                improved = True
+                break
+        if log:
+            log(f"climb {it}: {best['predicted_ms']:.1f} ms predicted, {len(seen)} trees ranked")
+        if not improved:
+            break
+    out = [r for r in seen.values() if r is not None]
+    out.sort(key=lambda r: r["predicted_ms"])
+    return out
+
+
+def main():
+    import argparse
+    import torch
+    from rqc import make_workload
+    ap = argparse.ArgumentParser(description="contraction-tree search ranked by the cost model's predicted time")
+    ap.add_argument("--workload", default="diamond53_m12")
+    ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--cases", type=int, default=40, help="random plans for the cost model's corpus")
+    ap.add_argument("--budget-s", type=float, default=90.0)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--seeds", default="3004,3104,3204")
+    ap.add_argument("--climb", type=int, default=40)
+    ap.add_argument("--measure", type=int, default=3, help="measure the best N predicted trees")
+    ap.add_argument("--ws-gib", type=float, default=120.0)
+    ap.add_argument("--per-step", type=int, default=150, help="rotations tried per climb step")
+    ap.add_argument("--start", default=None, help="JSON with a start tree (its 'ssa' and 'sliced', e.g. "
+                                                    "an earlier --out's 'best')")
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    torch.cuda.init()
+    log = lambda m: print(m, flush=True)  # noqa: E731
+    w = make_workload(args.workload)
+    limit = int(args.ws_gib * 2 ** 30)
+    # corpus: the workload's own steps under its start tree, then random plans
+    corpus = costmodel.Corpus()
+    b = costmodel.bind(costmodel.workload_case(args.workload), ws_limit=limit)
+    if b is not None:
+        X, y, _ = costmodel.autotune_rows(b, args.precision)
+        corpus.add(X, y, -1)
+        del b
+        torch.cuda.empty_cache()
+    costmodel.collect([costmodel.random_case(s) for s in range(args.cases)], corpus, precisions=(args.precision,),
+                      reps=1, log=None, budget_s=args.budget_s, flops_range=(1e8, 1e15))
+    tr = costmodel.Trainer(seed=0)
+    tr.fit(corpus.X, corpus.y, epochs=args.epochs)
+    log(f"cost model: {len(corpus.y)} timings")
+    ranker = Ranker(w.circuit, w.bits, w.struct, tr, args.precision, w.spec.max_rank, limit)
+    t0 = time.time()
+    start = np.asarray(w.tree.ssa)
+    if args.start:
+        with open(args.start) as f:
+            st = json.load(f)
+        start = np.asarray(st.get("best", st)["ssa"])
+    ranked = search(ranker, start, seeds=[int(s) for s in args.seeds.split(",") if s],
+                    steps=args.climb, per_step=args.per_step, log=log)
+    search_s = time.time() - t0
+    start_key = np.asarray(w.tree.ssa).tolist()  # the workload's own tree is always measured
+    res = {"workload": args.workload, "precision": args.precision, "ranked": len(ranked), "search_s": search_s,
+           "corpus_rows": int(len(corpus.y)), "measured": []}
+    todo = ranked[:args.measure]
+    if not any(r["ssa"] == start_key for r in todo):
+        own = [r for r in ranked if r["ssa"] == start_key][:1]
+        if not own:
+            sl, _ = ranker.slice(np.asarray(w.tree.ssa))
+            r = ranker.predict(np.asarray(w.tree.ssa), sl)
+            if r is not None:
+                r.update({"ssa": start_key, "sliced": [int(e) for e in sl]})
+                own = [r]
+        todo = todo + own
+    for r in todo:
+        ms = measure(w.circuit, w.bits, np.asarray(r["ssa"]), r["sliced"], args.precision, limit)
+        rec = {k: v for k, v in r.items() if k != "ssa"}
+        rec["measured_ms"] = ms
+        rec["is_start_tree"] = r["ssa"] == start_key
+        res["measured"].append(rec)
+        log(json.dumps(rec))
+    if args.out:
+        best = min((m for m in zip(todo, res["measured"]) if m[1]["measured_ms"]), key=lambda m: m[1]["measured_ms"])
+        res["best"] = {"ssa": best[0]["ssa"], "sliced": best[0]["sliced"], **best[1]}
+        with open(args.out, "w") as f:
+            json.dump(res, f)
+    print(json.dumps({k: v for k, v in res.items() if k != "best"}))
+
+
+if __name__ == "__main__":
+    main()
