@@ -15,10 +15,19 @@ Seeds: circuit 1000+i, bitstrings 2000+i, tree search 3000+i for workload i.
 * ``diamond53_m12``: 53 qubits, 54-site diamond with one dead site,
                      12 cycles, 258 fSim gates, 8192 bitstrings, sliced until
                      the largest per-instance intermediate has <= 2^32 entries.
+                     Its tree is the one stored in ``rqc/trees/``: the best
+                     measured tree of the time-ranked tree search
+                     (``paper_2212_04749_gb300.treesearch``), which needs no
+                     slicing (largest intermediate 2^24); ``seeded_tree=True``
+                     gives the seeded random-greedy tree instead.
 """
 
 from dataclasses import dataclass
 from typing import Optional
+
+import hashlib
+import json
+import os
 
 import numpy as np
 
@@ -39,13 +48,15 @@ class WorkloadSpec:
     n_sliced: Optional[int]
     max_rank: Optional[int]
     trials: int = 16
+    tree_file: Optional[str] = None  # stored tree (rqc/trees/), else the seeded search
 
 
 WORKLOADS = {
     "grid3x4_m8": WorkloadSpec("grid3x4_m8", 1, "grid3x4", 8, 64, None, None),
     "grid5x6_m14": WorkloadSpec("grid5x6_m14", 2, "grid5x6", 14, 4096, 10, 28),
     "grid6x7_m10": WorkloadSpec("grid6x7_m10", 3, "grid6x7", 10, 1024, 14, None, trials=8),
-    "diamond53_m12": WorkloadSpec("diamond53_m12", 4, "diamond53", 12, 8192, None, 32),
+    "diamond53_m12": WorkloadSpec("diamond53_m12", 4, "diamond53", 12, 8192, None, 32,
+                                  tree_file="diamond53_m12.json"),
 }
 
 
@@ -72,22 +83,53 @@ def _layout(name):
 
 
 _CACHE = {}
+TREES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "trees")
 
 
-def make_workload(name: str, k: Optional[int] = None, trials: Optional[int] = None) -> Workload:
+def circuit_digest(circ: Circuit) -> str:
+    """Digest of a circuit's gate positions and names (what a tree of its
+    network depends on)."""
+    q0, q1, layer, _ = circ.to_arrays()
+    h = hashlib.sha256()
+    for a in (q0, q1, layer):
+        h.update(np.ascontiguousarray(a).tobytes())
+    h.update(",".join(g.kind for g in circ.gates).encode())
+    return h.hexdigest()
+
+
+def stored_tree(spec: WorkloadSpec, circ: Circuit) -> Optional[ContractionTree]:
+    """The workload's stored tree, if it has one for exactly this circuit."""
+    if not spec.tree_file:
+        return None
+    with open(os.path.join(TREES, spec.tree_file)) as f:
+        rec = json.load(f)
+    if rec["circuit_sha256"] != circuit_digest(circ):
+        raise ValueError(f"{spec.tree_file} belongs to another circuit (the generators changed)")
+    t = ContractionTree(ssa=np.asarray(rec["ssa"], np.int64))
+    t.sliced = [int(e) for e in rec["sliced"]]
+    return t
+
+
+def make_workload(name: str, k: Optional[int] = None, trials: Optional[int] = None,
+                  seeded_tree: bool = False) -> Workload:
     """Build (and memoise) a workload.  ``k`` and ``trials`` override the
-    bitstring count and the number of greedy trials (smaller test cases)."""
+    bitstring count and the number of greedy trials (smaller test cases; the
+    seeded search then runs); ``seeded_tree`` ignores a stored tree."""
     spec = WORKLOADS[name]
-    key = (name, k, trials)
+    key = (name, k, trials, seeded_tree)
     if key in _CACHE:
         return _CACHE[key]
     kk = spec.k if k is None else k
     circ = random_circuit(_layout(spec.layout), spec.cycles, seed=1000 + spec.index)
     bits = uniform_bitstrings(circ.n_qubits, kk, seed=2000 + spec.index)
     struct = network_structure(circ)
-    tree = greedy_tree(struct, kk, seed=3000 + spec.index,
-                       trials=spec.trials if trials is None else trials,
-                       n_sliced=spec.n_sliced, max_rank=spec.max_rank)
+    tree = None
+    if not seeded_tree and k is None and trials is None:
+        tree = stored_tree(spec, circ)
+    if tree is None:
+        tree = greedy_tree(struct, kk, seed=3000 + spec.index,
+                           trials=spec.trials if trials is None else trials,
+                           n_sliced=spec.n_sliced, max_rank=spec.max_rank)
     w = Workload(spec, circ, bits, struct, tree)
     _CACHE[key] = w
     return w

@@ -44,3 +44,16 @@ def test_contracting_along_a_rotated_tree_gives_the_same_amplitudes():
     for r in rotations(np.asarray(w.tree.ssa), T)[::9]:
         got = otn.partial_amplitudes(w.circuit, r, w.bits[:8])[0]
         assert np.max(np.abs(got - ref)) < 1e-13
+
+
+def test_stored_diamond53_tree_is_a_valid_tree_of_its_circuit():
+    # the benchmark's tree comes from the time-ranked search; it must be a
+    # tree of exactly this circuit's network and keep every intermediate
+    # within the 2^32-entry cap of the workload
+    w = make_workload("diamond53_m12")
+    T = w.struct.n_tensors
+    _valid(np.asarray(w.tree.ssa), T)
+    c = estimate_cost(w.struct, w.tree.ssa, w.bits.shape[0], w.tree.sliced)
+    assert c.max_rank <= 32
+    seeded = make_workload("diamond53_m12", seeded_tree=True)
+    assert c.flops < estimate_cost(seeded.struct, seeded.tree.ssa, w.bits.shape[0]).flops
