@@ -218,6 +218,10 @@ int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
     if (cfg < 2) {
         fam = 0;
         e = tnk::launch_step_row(d, st);
+    } else if (d.mb + d.nb <= 2 && d.kb >= 6) {
+        // a few long dot products per instance (e.g. the root): one block each
+        fam = 1;
+        e = tnk::launch_step_dot(d, st);
     } else if (precision != TN_FP32 && tnk::gemm_tc_supports(d)) {
         fam = 2;
         e = o->amap[s].ok ? tnk::launch_step_gemm_tc(d, &o->amap[s].map, precision, o->err_flag, st)

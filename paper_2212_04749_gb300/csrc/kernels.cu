@@ -673,6 +673,54 @@ __global__ void __launch_bounds__(128) k_step_gemm_simt2(const StepDesc d, int c
     }
 }
 
+// Steps with at most four outputs per instance (M N <= 4) and a long K:
+// each output C[i](m, n) = sum_k A[a(i)](m, k) B[b(i)](k, n) is one dot
+// product of two K-contiguous complex runs, computed by one block (16-byte
+// loads, FP32 FMA, a fixed-order block reduction), scaled by the operands'
+// power-of-two factors and stored with its instance's exponent and max.
+__global__ void __launch_bounds__(256) k_step_dot(const StepDesc d) {
+    __shared__ float2 s_part[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mn_log = d.mb + d.nb;
+    const int64_t i = int64_t(blockIdx.x) >> mn_log;
+    const int mn = int(blockIdx.x & ((1u << mn_log) - 1));
+    const int m = mn >> d.nb, n = mn & ((1 << d.nb) - 1);
+    const int2 ab = d.instab[i];
+    const int K = 1 << d.kb;
+    const float4 *a4 = reinterpret_cast<const float4 *>(d.A + int64_t(ab.x) * d.sA + (int64_t(m) << d.kb));
+    const float4 *b4 = reinterpret_cast<const float4 *>(d.B + int64_t(ab.y) * d.sB + (int64_t(n) << d.kb));
+    float2 acc = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
+    for (int q = tid; q < K / 2; q += 256) {
+        const float4 x = __ldg(a4 + q), y = __ldg(b4 + q);
+        cfma(acc, make_float2(x.x, x.y), make_float2(y.x, y.y));
+        cfma(acc2, make_float2(x.z, x.w), make_float2(y.z, y.w));
+    }
+    acc.x += acc2.x;
+    acc.y += acc2.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) s_part[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        float2 t = s_part[0];
+        for (int w = 1; w < 8; ++w) {
+            t.x += s_part[w].x;
+            t.y += s_part[w].y;
+        }
+        const int ea = d.mxA ? exp_of(d.mxA[ab.x]) : 0;
+        const int eb = d.mxB ? exp_of(d.mxB[ab.y]) : 0;
+        const float sc = pow2f(-(ea + eb));
+        const float2 v = make_float2(t.x * sc, t.y * sc);
+        d.C[i * d.sC + dep(m, d.pCm, d.mb) + dep(n, d.pCn, d.nb)] = v;
+        if (mn == 0) d.EC[i] = d.EA[ab.x] + ea + d.EB[ab.y] + eb;
+        const uint32_t mx = absmax_bits(v);
+        if (d.mxC && mx) record_max(d.mxC + i, mx);
+    }
+}
+
 // root entry of completion x: its r bits reversed (root bit t = the t-th
 // lowest open qubit; x's most significant bit = the lowest open qubit)
 __device__ __forceinline__ int64_t root_entry(int64_t x, int r) {
@@ -923,6 +971,15 @@ cudaError_t launch_step_gemm_simt(const StepDesc &d, cudaStream_t s) {
     } else {
         k_step_gemm_simt<<<dim3((unsigned)blocks), 256, 0, s>>>(d, (int)ctiles, (int)mtiles);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_dot(const StepDesc &d, cudaStream_t s) {
+    if (d.mb + d.nb > 2 || d.kb < 6) return cudaErrorInvalidValue;
+    const int64_t blocks = d.nInst << (d.mb + d.nb);
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_step_dot<<<dim3((unsigned)blocks), 256, 0, s>>>(d);
     return cudaGetLastError();
 }
 

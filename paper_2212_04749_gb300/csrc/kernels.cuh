@@ -65,6 +65,9 @@ cudaError_t launch_fill(const FillJobD *jobs, int64_t njobs, const LeafHighD *hi
                         float2 *ws, cudaStream_t s);
 cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s);
 cudaError_t launch_step_gemm_simt(const StepDesc &d, cudaStream_t s);
+// Steps with M N <= 4 outputs per instance and K >= 64: one block per
+// output, a dot product of two K-contiguous runs (FP32).
+cudaError_t launch_step_dot(const StepDesc &d, cudaStream_t s);
 // One-time per-device setup of the SIMT GEMM (its dynamic shared memory).
 cudaError_t init_simt_kernels();
 // The root holds 2^r entries per instance (r open output qubits, its bit t

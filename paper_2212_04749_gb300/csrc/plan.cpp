@@ -238,7 +238,7 @@ struct Builder {
         for (int v = T; v < NN; ++v) {
             Node &nd = P.nodes[v];
             // major key: the operand the step reads as A (the larger one)
-            const bool left_big = P.nodes[nd.left].rank >= P.nodes[nd.right].rank;
+            const bool left_big = a_is_left(P.nodes[nd.left], P.nodes[nd.right]);
             const int a = left_big ? nd.left : nd.right, b = left_big ? nd.right : nd.left;
             const int64_t nb = P.nodes[b].n_out;
             std::vector<int64_t> key(ku);
@@ -259,6 +259,20 @@ struct Builder {
             for (int64_t u = 0; u < ku; ++u)
                 oi[v][u] = int32_t(std::lower_bound(vals.begin(), vals.end(), key[u]) - vals.begin());
         }
+    }
+
+    // The operand a step streams as A: the one likely to hold more entries
+    // over its bitstring instances, so that B -- read by every group -- is
+    // the smaller.  The estimate, rank + min(output qubits below, 16), does
+    // not depend on the bitstrings, so a bitstring alone and the same
+    // bitstring in a batch run their steps with the same operand roles (the
+    // reuse-invariance of an instance's arithmetic); ties by rank, then the
+    // left child.
+    static bool a_is_left(const Node &l, const Node &r) {
+        const int sl = l.rank + std::min<int>((int)l.outs.size(), 16);
+        const int sr = r.rank + std::min<int>((int)r.outs.size(), 16);
+        if (sl != sr) return sl > sr;
+        return l.rank >= r.rank;
     }
 
     static std::vector<int32_t> compress_map(const std::vector<int> &parent_low,
@@ -317,7 +331,7 @@ struct Builder {
             Step st;
             st.node = v;
             const Node &l = P.nodes[nd.left], &r = P.nodes[nd.right];
-            const bool left_big = l.rank >= r.rank;
+            const bool left_big = a_is_left(l, r);
             st.a = left_big ? nd.left : nd.right;
             st.b = left_big ? nd.right : nd.left;
             st.level = nd.level;
