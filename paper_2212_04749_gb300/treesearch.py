@@ -92,6 +92,11 @@ class Ranker:
         self.k = bits.shape[0]
         self.trainer, self.precision = trainer, precision
         self.max_rank, self.limit = max_rank, workspace_limit
+        # roofline rates (GB/s, algorithmic TFLOP/s): the measured copy rate,
+        # BF16x3 = the measured BF16 rate / 3 products (TF32 about twice
+        # that), the measured FP32 FMA rate
+        self.hbm_gbs, self.fp32_tflops = 6780.0, 65.0
+        self.tensor_tflops = 1700.0 / 3 if precision == "bf16x3" else 1050.0
 
     def slice(self, ssa):
         from rqc.tree import ContractionTree, choose_slices, estimate_cost
@@ -108,14 +113,25 @@ class Ranker:
         except tn.TnError:
             return None  # does not fit the workspace limit
         n = p.info["n_steps"]
-        runs = np.array([s["runs"] for s in p.tn_plan_steps()], np.float64)
+        steps = p.tn_plan_steps()
+        runs = np.array([s["runs"] for s in steps], np.float64)
         feats, ok = [], []
         for c in range(tn.TN_NCONFIG):
             f, e = p.tn_plan_features(self.precision, c)
             feats.append(f)
             ok.append(e)
         y = self.trainer.predict(np.concatenate(feats)).reshape(tn.TN_NCONFIG, n)
-        ms = np.where(np.stack(ok), 2.0 ** y, np.inf).min(axis=0)
+        # no configuration beats its roofline: the prediction is floored at
+        # the step's bytes at the HBM rate and its flops at the rate of the
+        # configuration's unit (tensor cores for a GEMM step they can take)
+        by = np.array([s["bytes"] for s in steps], np.float64) / (self.hbm_gbs * 1e6)
+        fl = np.array([s["flops"] for s in steps], np.float64)
+        tc_ok = np.array([s["kb"] >= 3 and 6 <= s["mb"] <= 30 for s in steps])
+        floor = np.empty((tn.TN_NCONFIG, n))
+        for c in range(tn.TN_NCONFIG):
+            rate = np.where((c >= 2) & tc_ok & (self.precision != "fp32"), self.tensor_tflops, self.fp32_tflops)
+            floor[c] = np.maximum(by, fl / (rate * 1e9))
+        ms = np.where(np.stack(ok), np.maximum(2.0 ** y, floor), np.inf).min(axis=0)
         info = p.info
         return {"predicted_ms": float(np.sum(ms * runs)), "flops_eq1": info["flops_ma"],
                 "bytes": info["bytes_min"], "workspace_gib": info["workspace_bytes"] / 2 ** 30,
