@@ -19,7 +19,9 @@
 // Tile: 128 rows x 64 complex columns (MMA M = 128, N = 128), K in chunks
 // of 16 complex (32 real).  A arrives by TMA as 128 rows of 128 bytes in
 // the 128-byte swizzled K-major layout (TF32 uses it as is; BF16x3 splits
-// it in place, hi and lo K steps alternating within each row).  B columns
+// it into hi and lo and keeps them in tensor memory, one row per lane, so
+// that its MMAs read only B from shared memory: shared-memory bandwidth is
+// what bounds the long-K steps).  B columns
 // are gathered per instance, expanded into the real 2x2 form and stored in
 // the K-major no-swizzle layout (core matrix 8 rows x 16 bytes; LBO =
 // distance between K-adjacent core matrices = 128 rows x 16 B, SBO =
@@ -163,11 +165,12 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
         : "memory");
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+// A from tensor memory (a_tm: lane 0, first column of the K step)
+__device__ __forceinline__ void mma_f16_ts(uint32_t d, uint32_t a_tm, uint64_t b, uint32_t id, uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(id), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a_tm), "l"(b), "r"(id), "r"(acc)
         : "memory");
 }
 
@@ -240,7 +243,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 //   warps 0-7  : B: streaming, per-thread cp.async pieces LOOK chunks ahead,
 //                expanded chunk by chunk; resident / dictionary, the whole
 //                B loaded and expanded at each group (column tile) switch.
-//                BF16x3: A split into hi/lo in place in the TMA ring; TF32
+//                BF16x3: A split into hi/lo from the TMA ring into TMEM; TF32
 //                reads A straight from the ring.
 //   warps 8-15 : epilogue, two warps per TMEM lane quadrant (warp % 4), each
 //                draining 16 complex columns of each half tile; two
@@ -254,6 +257,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 //                a ring of MS tiles ahead of the epilogue.
 // The epilogue warpgroups take registers from the others (setmaxnreg).
 constexpr int NPROD = 256;   // warps 0-7
+// BF16x3: warps 0-3 alone write the split A into TMEM, each thread one row
+// (its warp's lane quadrant), both K steps.  With the two K steps written by
+// warps w and w + 4 at once (same lanes, other columns) the products came
+// out different from run to run; one writer per lane quadrant gives the
+// exact results of the shared-memory form.
+constexpr int NAW = 128;
 constexpr int EPI_WARP0 = 8; // warps 8-15: two per TMEM lane quadrant
 constexpr int NEPI = 256;
 constexpr int MMA_WARP = 16;
@@ -268,7 +277,12 @@ static_assert(NPROD * PROD_REGS + NEPI * EPI_REGS + 128 * CTL_REGS <= NTHREADS *
               "register split above the launch allocation");
 constexpr int MS = 8;         // epilogue metadata ring (tiles ahead of the epilogue)
 constexpr int NACC_MAX = 8;   // accumulators in TMEM (narrow tiles: up to 8 in flight)
-constexpr int TMEM_COLS2 = 256;
+constexpr int TMEM_COLS2 = 256;  // accumulators
+// BF16x3 also keeps the split A chunks in TMEM, 32 columns a stage after
+// the accumulators (at most 8 stages), so it allocates all 512 columns
+constexpr int TM_A = TMEM_COLS2, TM_ASTAGE = 32;
+template <int PREC>
+__host__ __device__ constexpr uint32_t tmem_alloc_cols() { return PREC == 2 ? 512u : uint32_t(TMEM_COLS2); }
 
 // Shared-memory layout.  Streaming B (BRES = false): A ring, B MMA stages,
 // raw B pieces, epilogue staging.  Resident B (BRES = true): a pool of
@@ -328,8 +342,8 @@ struct EpiMap {
 };
 
 struct Ctrl {
-    uint64_t full[4], empty[4], rfull[8], rempty[8], afull[8], tfull[NACC_MAX], tempty[NACC_MAX], mfull[MS],
-        mempty[MS];
+    uint64_t full[4], empty[4], rfull[8], rempty[8], afull[8], taempty[8], tfull[NACC_MAX], tempty[NACC_MAX],
+        mfull[MS], mempty[MS];
     uint64_t bfull, bempty;  // resident B: loaded / no longer read by the MMAs
     uint32_t tmem_base;
     int32_t abort_;
@@ -379,6 +393,11 @@ struct TileIter {
     int mt;          // row tile
     int ct, nct;     // column tile within the unit and their count (schedule 1: 0 and 1)
     int4 rec, nrec;  // the unit's record (schedule 0: its first, column offset 0) and the next unit's
+    // blocks of tblk tiles dealt round-robin to the CTAs (tblk = 0: one
+    // contiguous range per CTA): the next block's first tile, the tiles
+    // left in the current block
+    int64_t bnext;
+    int bleft;
 
     __device__ __forceinline__ static int unit_tiles(const StepDesc &d, const int4 &r) {
         return d.sched != 0 ? 1 : int(((int64_t(r.y) << d.nb) + TBN - 1) / TBN);
@@ -406,7 +425,27 @@ struct TileIter {
         if (d.sched == 0) r.w = ct * TBN;
         return r;
     }
-    __device__ __forceinline__ void next(const StepDesc &d, int64_t mtiles) {
+    // the CTA's first tile (blocks: its first block's)
+    __device__ __forceinline__ void start(const StepDesc &d, int64_t mtiles, int64_t n_tiles, int tblk) {
+        if (tblk <= 0) {
+            bleft = 0x7fffffff;
+            init(d, n_tiles * blockIdx.x / gridDim.x, mtiles);
+            return;
+        }
+        const int64_t t0 = int64_t(blockIdx.x) * tblk;
+        bleft = int(min(int64_t(tblk), n_tiles - t0));
+        bnext = t0 + int64_t(gridDim.x) * tblk;
+        init(d, t0, mtiles);
+    }
+    __device__ __forceinline__ void next(const StepDesc &d, int64_t mtiles, int64_t n_tiles, int tblk) {
+        if (tblk > 0 && --bleft == 0) {  // the CTA's next block
+            if (bnext < n_tiles) {
+                bleft = int(min(int64_t(tblk), n_tiles - bnext));
+                init(d, bnext, mtiles);
+                bnext += int64_t(gridDim.x) * tblk;
+            }
+            return;
+        }
         if (++ct < nct) return;
         ct = 0;
         if (++mt < mtiles) return;
@@ -433,11 +472,18 @@ __device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const
                           make_float2(p1.z, p1.w)};
     const float r0[8] = {t4[0].x, -t4[0].y, t4[1].x, -t4[1].y, t4[2].x, -t4[2].y, t4[3].x, -t4[3].y};
     const float r1[8] = {t4[0].y, t4[0].x, t4[1].y, t4[1].x, t4[2].y, t4[2].x, t4[3].y, t4[3].x};
+    // A 16-byte unit's bank group is its row mod 8, so the threads of a
+    // warp (32 consecutive columns) write the odd row first where bit 2 of
+    // the column is set: each store instruction then covers all 32 banks
+    const int sw = (bcol >> 2) & 1;
+    const int ra = 2 * bcol + sw, rb = 2 * bcol + 1 - sw;
     if (PREC == 1) {
-        *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol, 8 * kqb, 4)) = make_float4(r0[0], r0[1], r0[2], r0[3]);
-        *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol, 8 * kqb + 4, 4)) = make_float4(r0[4], r0[5], r0[6], r0[7]);
-        *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb, 4)) = make_float4(r1[0], r1[1], r1[2], r1[3]);
-        *reinterpret_cast<float4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb + 4, 4)) = make_float4(r1[4], r1[5], r1[6], r1[7]);
+        const float4 a0 = make_float4(r0[0], r0[1], r0[2], r0[3]), a1 = make_float4(r0[4], r0[5], r0[6], r0[7]);
+        const float4 b0 = make_float4(r1[0], r1[1], r1[2], r1[3]), b1 = make_float4(r1[4], r1[5], r1[6], r1[7]);
+        *reinterpret_cast<float4 *>(base + kmaj_off(ra, 8 * kqb, 4)) = sw ? b0 : a0;
+        *reinterpret_cast<float4 *>(base + kmaj_off(ra, 8 * kqb + 4, 4)) = sw ? b1 : a1;
+        *reinterpret_cast<float4 *>(base + kmaj_off(rb, 8 * kqb, 4)) = sw ? a0 : b0;
+        *reinterpret_cast<float4 *>(base + kmaj_off(rb, 8 * kqb + 4, 4)) = sw ? a1 : b1;
     } else {
         __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
 #pragma unroll
@@ -448,46 +494,53 @@ __device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const
             l1[q] = __float2bfloat16_rn(r1[q] - __bfloat162float(h1[q]));
         }
         uint8_t *blo = base + TBNR * TBKR * 2;
-        *reinterpret_cast<uint4 *>(base + kmaj_off(2 * bcol, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(h0);
-        *reinterpret_cast<uint4 *>(blo + kmaj_off(2 * bcol, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(l0);
-        *reinterpret_cast<uint4 *>(base + kmaj_off(2 * bcol + 1, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(h1);
-        *reinterpret_cast<uint4 *>(blo + kmaj_off(2 * bcol + 1, 8 * kqb, 2)) = *reinterpret_cast<uint4 *>(l1);
+        const uint4 H0 = *reinterpret_cast<uint4 *>(h0), L0 = *reinterpret_cast<uint4 *>(l0);
+        const uint4 H1 = *reinterpret_cast<uint4 *>(h1), L1 = *reinterpret_cast<uint4 *>(l1);
+        const uint32_t oa = kmaj_off(ra, 8 * kqb, 2), ob = kmaj_off(rb, 8 * kqb, 2);
+        *reinterpret_cast<uint4 *>(base + oa) = sw ? H1 : H0;
+        *reinterpret_cast<uint4 *>(blo + oa) = sw ? L1 : L0;
+        *reinterpret_cast<uint4 *>(base + ob) = sw ? H0 : H1;
+        *reinterpret_cast<uint4 *>(blo + ob) = sw ? L0 : L1;
     }
 }
 
-// BF16x3: split an FP32 A chunk into hi/lo in place.  The slot holds 128
-// rows of 32 real k (128 bytes, 128-byte swizzle); thread (row, half) reads
-// the 16 values of its half row (logical 16-byte units 4 half .. 4 half + 3)
-// and writes, over the same four units, hi of its first and second 8
-// values, then lo of them.  As a BF16 K-major operand of 64 elements per
-// row, the slot then holds the K steps hi(k 0-15), lo(k 0-15), hi(k 16-31),
-// lo(k 16-31).  Every thread rewrites only the bytes it read.
-__device__ __forceinline__ void split_a_inplace(uint8_t *slot, int tid) {
-    const int row = tid >> 1, half = tid & 1, sw = row & 7;
-    uint8_t *rowp = slot + row * 128;
-    float x[16];
+// BF16x3: the A operand goes to tensor memory.  A chunk arrives by TMA as
+// 128 rows of 32 real k (128 bytes, 128-byte swizzle).  The A stage in TMEM
+// is 32 columns (128 lanes = rows): K step h (16 real k, 8 columns of
+// packed bf16 pairs, lower k in the low half) holds hi in columns
+// 16 h .. 16 h + 7 and lo in the next 8.  The MMAs then read only B from
+// shared memory.
+//
+// Quarter q (real k 8 q .. 8 q + 7, logical 16-byte units 2 q, 2 q + 1) of
+// this thread's row: read from the swizzled slot, split into hi and lo,
+// stored to hi columns 16 (q / 2) + 4 (q % 2) .. + 3 and the lo columns 8
+// further on, relative to ta (this lane's row of the stage).  tcgen05.st is
+// warp-wide (.sync.aligned).
+__device__ __forceinline__ void split_a_quarter(const uint8_t *slot, int row, int q, uint32_t ta) {
+    const int sw = row & 7;
+    const uint8_t *rowp = slot + row * 128;
+    const float4 v0 = *reinterpret_cast<const float4 *>(rowp + (((2 * q) ^ sw) << 4));
+    const float4 v1 = *reinterpret_cast<const float4 *>(rowp + (((2 * q + 1) ^ sw) << 4));
+    const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    uint32_t hw[4], lw[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 v = *reinterpret_cast<const float4 *>(rowp + (((4 * half + i) ^ sw) << 4));
-        x[4 * i] = v.x;
-        x[4 * i + 1] = v.y;
-        x[4 * i + 2] = v.z;
-        x[4 * i + 3] = v.w;
-    }
-    uint32_t hw[8], lw[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+    for (int p = 0; p < 4; ++p) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * p], x[2 * p + 1]);
         const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 lo = __floats2bfloat162_rn(x[2 * q] - hf.x, x[2 * q + 1] - hf.y);
-        hw[q] = *reinterpret_cast<const uint32_t *>(&h);
-        lw[q] = *reinterpret_cast<const uint32_t *>(&lo);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(x[2 * p] - hf.x, x[2 * p + 1] - hf.y);
+        hw[p] = *reinterpret_cast<const uint32_t *>(&h);
+        lw[p] = *reinterpret_cast<const uint32_t *>(&lo);
     }
-    *reinterpret_cast<uint4 *>(rowp + (((4 * half + 0) ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *reinterpret_cast<uint4 *>(rowp + (((4 * half + 1) ^ sw) << 4)) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-    *reinterpret_cast<uint4 *>(rowp + (((4 * half + 2) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-    *reinterpret_cast<uint4 *>(rowp + (((4 * half + 3) ^ sw) << 4)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+    const uint32_t c = ta + uint32_t(16 * (q >> 1) + 4 * (q & 1));
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(c), "r"(hw[0]), "r"(hw[1]),
+                 "r"(hw[2]), "r"(hw[3])
+                 : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(c + 8u), "r"(lw[0]), "r"(lw[1]),
+                 "r"(lw[2]), "r"(lw[3])
+                 : "memory");
 }
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Resident B: the producer threads load the B operand of a group's column
 // tiles ct0 .. ct0 + nct - 1 (schedule 0: all of the group's; schedule 1:
@@ -623,7 +676,7 @@ __device__ __forceinline__ void fold_max16(const uint32_t (&r)[32], EpiMeta &em,
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 warps on a sub-partition)
     k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA, int nrs,
-                   int acw, int ow) {
+                   int acw, int ow, int tblk) {
     // MODE 0: B streamed chunk by chunk; 1: B resident (a group's or a
     // column tile's), rescale folded into it; 2: B dictionary, every B
     // instance of the step (at most 64 columns) resident for the whole
@@ -661,13 +714,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
     const int nepi = narrow ? NEPI / 2 : NEPI;  // epilogue threads that drain one tile
     // one contiguous range of tiles per CTA (a unit's tiles run back to
     // back: its B and its records are reused)
-    const int64_t t_begin = n_tiles * blockIdx.x / gridDim.x;
-    const int64_t my_tiles = n_tiles * (blockIdx.x + 1) / gridDim.x - t_begin;
+    // tblk = 0: one contiguous range of tiles per CTA; else blocks of tblk
+    // tiles dealt round-robin, so that the CTAs work on neighbouring tiles
+    // at any time (their A and B stay in L2)
+    int64_t my_tiles;
+    if (tblk <= 0) {
+        my_tiles = n_tiles * (blockIdx.x + 1) / gridDim.x - n_tiles * blockIdx.x / gridDim.x;
+    } else {
+        const int64_t nblk = (n_tiles + tblk - 1) / tblk;
+        const int64_t mine = nblk > blockIdx.x ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        my_tiles = mine * tblk;
+        if (mine > 0 && (blockIdx.x + (mine - 1) * int64_t(gridDim.x)) == nblk - 1) my_tiles -= nblk * tblk - n_tiles;
+    }
     const int64_t total_chunks = my_tiles * nch;
 
     if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&X.tmem_base)),
-                     "r"(TMEM_COLS2)
+                     "r"(tmem_alloc_cols<PREC>())
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -678,8 +741,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         }
         for (int s = 0; s < C::RST; ++s) {
             mbar_init(&X.rfull[s], 1);
-            mbar_init(&X.rempty[s], 1);
-            mbar_init(&X.afull[s], NPROD);
+            // BF16x3 (not packed B): the producers release the A slot once
+            // they hold its values; otherwise the MMAs' commit does
+            mbar_init(&X.rempty[s], (PREC == 2 && MODE != 3) ? NAW : 1);
+            mbar_init(&X.afull[s], NAW);
+            mbar_init(&X.taempty[s], 1);
         }
         mbar_init(&X.bfull, NPROD);
         mbar_init(&X.bempty, 1);
@@ -759,13 +825,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             int64_t issued = 0;
             bool ok = true;
             TileIter it;
-            if (my_tiles > 0) it.init(d, t_begin, mtiles);
+            if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
             int rs = 0;
             uint32_t rph = 0;
             const uint8_t *bsrc = nullptr;  // packed B: the tile's first chunk
             int64_t fprev = -1;
             int ctprev = -1;
-            for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles)) {
+            for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles, n_tiles, tblk)) {
                 const int4 r = it.record(d);
                 const int m0 = int(it.mt * TBM);
                 if (BPACK && (it.f != fprev || it.ct != ctprev)) {
@@ -803,20 +869,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         // ------------------------------------------------------------ B loads, A split
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(PROD_REGS));
         const int bcol = tid & 63, kqb = tid >> 6;
+        // BF16x3 A (warps 0-3): this thread's row, its warp's TMEM lane
+        // quadrant
+        const bool awriter = PREC == 2 && warp < NAW / 32;
+        const int arow = 32 * (warp & 3) + lane;
+        const uint32_t ta_row = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(TM_A);
+        // one chunk of A from the TMA slot into TMEM stage `stage` (both K
+        // steps); the slot is released once read (rel: its barrier, or null)
+        auto a_to_tmem = [&](const uint8_t *slot, int stage, uint64_t *rel) {
+            const uint32_t ta = ta_row + uint32_t(stage * TM_ASTAGE);
+            split_a_quarter(slot, arow, 0, ta);
+            split_a_quarter(slot, arow, 1, ta);
+            split_a_quarter(slot, arow, 2, ta);
+            split_a_quarter(slot, arow, 3, ta);
+            if (rel) mbar_arrive(rel);
+        };
+        // loop exits and waits are made warp-uniform: the TMEM stores below
+        // are warp-wide instructions
+        auto aborted = [&]() { return __any_sync(0xffffffffu, *abort_flag != 0); };
       if constexpr (BRES || BPACK) {
         // resident B: at each group switch (once the MMAs stopped reading
         // the previous group's B) load the group's B into the pool; BF16x3
-        // also splits every A chunk in place
+        // also splits every A chunk into a TMEM stage
         int rs = 0;
         uint32_t rph = 0, u = 0;
         int64_t gprev = -1;
         TileIter it;
-        if (my_tiles > 0) it.init(d, t_begin, mtiles);
-        for (int64_t l = 0; l < my_tiles && !*abort_flag; ++l, it.next(d, mtiles)) {
+        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
+        for (int64_t l = 0; l < my_tiles && !aborted(); ++l, it.next(d, mtiles, n_tiles, tblk)) {
             const int4 r = it.record(d);
             const int64_t g = MODE == 2 ? 0 : it.f;  // the dictionary is loaded once
             if (BRES && g != gprev) {
-                if (u > 0 && !mbar_wait(&X.bempty, (u - 1) & 1u)) {
+                if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&X.bempty, (u - 1) & 1u))) {
                     give_up();
                     break;
                 }
@@ -826,15 +910,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 ++u;
                 gprev = g;
             }
-            if (PREC == 2) {
+            if (awriter) {
                 bool ok = true;
                 for (int c = 0; c < nch; ++c) {
-                    if (!mbar_wait(&X.rfull[rs], rph)) {
+                    // the chunk has landed and the MMAs are done with the
+                    // TMEM stage's previous chunk
+                    bool w = mbar_wait(&X.rfull[rs], rph);
+                    w = w && mbar_wait(&X.taempty[rs], rph ^ 1u);
+                    if (!__all_sync(0xffffffffu, w)) {
                         ok = false;
                         break;
                     }
-                    split_a_inplace(sm + C::OFF_RAW + rs * C::SLOT_RAW, tid);
-                    proxy_fence();
+                    tc_fence_after();
+                    // packed B: the slot pair waits for the MMAs
+                    a_to_tmem(sm + C::OFF_RAW + rs * C::SLOT_RAW, rs, MODE != 3 ? &X.rempty[rs] : nullptr);
+                    tmem_wait_st();
+                    tc_fence_before();
                     mbar_arrive(&X.afull[rs]);
                     if (++rs == nrs) {
                         rs = 0;
@@ -856,8 +947,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         int ctprev = -1;
         int c_iss = 0;  // chunk of the tile being issued
         TileIter it;
-        if (my_tiles > 0) it.init(d, t_begin, mtiles);
-        for (int64_t gch = 0; gch < total_chunks && !*abort_flag; ++gch) {
+        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
+        for (int64_t gch = 0; gch < total_chunks && !aborted(); ++gch) {
             // B pieces run LOOK chunks ahead.  Each thread reads back only
             // the 32 bytes it copied, and its raw slot was last used by a
             // chunk it has already expanded, so the ring needs no barrier.
@@ -865,7 +956,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 const int c = c_iss;
                 const int bslot = int(issued % C::BRST);
                 if (c == 0) {
-                    if (issued > 0) it.next(d, mtiles);
+                    if (issued > 0) it.next(d, mtiles, n_tiles, tblk);
                     if (it.f != fprev || it.ct != ctprev) {
                         const int4 r = it.record(d);
                         const int64_t gc = int64_t(r.w) + bcol;
@@ -880,39 +971,45 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     }
                 }
                 if (++c_iss == nch) c_iss = 0;
-                {  // B: this thread's column, k quad kqb
+                {  // B: this thread's column, k quad kqb (its two 16-byte
+                   // halves in the order that spreads a warp over all banks)
                     const uint32_t dst = smem_u32(sm + C::OFF_BRAW + bslot * C::SLOT_BRAW) + uint32_t(tid) * 32;
                     const int k = c * TBK + 4 * kqb;
                     const bool v = bb >= 0 && k + 3 < K;
                     const float2 *src = v ? d.B + bb + k : d.B;
-                    cp_async16(dst, src, v ? 16 : 0);
-                    cp_async16(dst + 16, v ? src + 2 : d.B, v ? 16 : 0);
+                    const int h = (tid >> 2) & 1;
+                    cp_async16(dst + 16 * h, v ? src + 2 * h : d.B, v ? 16 : 0);
+                    cp_async16(dst + 16 * (1 - h), v ? src + 2 * (1 - h) : d.B, v ? 16 : 0);
                 }
                 cp_async_commit();
                 ++issued;
             }
             const int slot = int(gch % C::ST);
-            // the MMA stage is free once the MMAs of chunk gch - ST are done
-            if (!mbar_wait(&X.empty[slot], (uint32_t(gch / C::ST) & 1u) ^ 1u)) {
+            // the MMA stage (B slot, BF16x3: and the TMEM A stage of the
+            // same index) is free once the MMAs of chunk gch - ST are done
+            const int rs = int(gch % C::RST);
+            bool w = mbar_wait(&X.empty[slot], (uint32_t(gch / C::ST) & 1u) ^ 1u);
+            if (awriter) w = w && mbar_wait(&X.rfull[rs], uint32_t(gch / C::RST) & 1u);
+            if (!__all_sync(0xffffffffu, w)) {
                 give_up();
                 break;
             }
-            if (PREC == 2) {  // A: split in place
-                const int rs = int(gch % C::RST);
-                if (!mbar_wait(&X.rfull[rs], uint32_t(gch / C::RST) & 1u)) {
-                    give_up();
-                    break;
-                }
-                split_a_inplace(sm + C::OFF_RAW + rs * C::SLOT_RAW, tid);
+            if (awriter) {  // A: into the TMEM stage; the TMA slot is free once read
+                tc_fence_after();
+                a_to_tmem(sm + C::OFF_RAW + rs * C::SLOT_RAW, slot, &X.rempty[rs]);
             }
             cp_async_wait(int(issued - gch - 1));
             // B: expand this thread's prefetched piece into the MMA layout
             {
                 const uint8_t *braw = sm + C::OFF_BRAW + int(gch % C::BRST) * C::SLOT_BRAW + tid * 32;
-                expand_b<PREC>(sm + C::OFF_B + slot * C::SLOT_B, bcol, kqb, *reinterpret_cast<const float4 *>(braw),
-                               *reinterpret_cast<const float4 *>(braw + 16));
+                const int h = (tid >> 2) & 1;
+                const float4 q0 = *reinterpret_cast<const float4 *>(braw + 16 * h);
+                const float4 q1 = *reinterpret_cast<const float4 *>(braw + 16 * (1 - h));
+                expand_b<PREC>(sm + C::OFF_B + slot * C::SLOT_B, bcol, kqb, h ? q1 : q0, h ? q0 : q1);
             }
+            if (awriter) tmem_wait_st();
             proxy_fence();
+            if (PREC == 2) tc_fence_before();
             mbar_arrive(&X.full[slot]);
         }
         cp_async_wait(0);
@@ -931,19 +1028,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                         mma_tf32(dtm, sdesc_sw128(a0 + 32 * j), sdesc(b0 + off, LBO, SBO), id, (!first || j > 0) ? 1u : 0u);
                     }
                 } else {
-                    // A: hi and lo K steps alternate in the slot (32 bytes
-                    // each, swizzled rows); B: hi plane, lo plane 8 KB on
+                    // A: the TMEM stage at column a0 (K step j: hi at
+                    // a0 + 16 j, lo 8 columns on); B: hi plane, lo plane
+                    // 8 KB on
                     const uint32_t id = idesc(1u, awr);
                     const uint32_t bl = b0 + TBNR * TBKR * 2;
 #pragma unroll
                     for (int j = 0; j < TBKR / 16; ++j) {
                         const uint32_t off = uint32_t(2 * j) * LBO;
-                        const uint64_t ah = sdesc_sw128(a0 + 64 * j), al = sdesc_sw128(a0 + 64 * j + 32);
-                        mma_f16(dtm, ah, sdesc(b0 + off, LBO, SBO), id, (!first || j > 0) ? 1u : 0u);
-                        mma_f16(dtm, ah, sdesc(bl + off, LBO, SBO), id, 1u);
-                        mma_f16(dtm, al, sdesc(b0 + off, LBO, SBO), id, 1u);
+                        const uint32_t ah = a0 + uint32_t(16 * j), al = ah + 8u;
+                        mma_f16_ts(dtm, ah, sdesc(b0 + off, LBO, SBO), id, (!first || j > 0) ? 1u : 0u);
+                        mma_f16_ts(dtm, ah, sdesc(bl + off, LBO, SBO), id, 1u);
+                        mma_f16_ts(dtm, al, sdesc(b0 + off, LBO, SBO), id, 1u);
                     }
                 }
+            };
+            // the A operand of a chunk: TF32, the TMA slot; BF16x3, the TMEM stage
+            auto a_of = [&](int rs, int tstage) {
+                return PREC == 1 ? smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW)
+                                 : tmem + uint32_t(TM_A + tstage * TM_ASTAGE);
             };
             bool ok = true;
             if constexpr (BRES || BPACK) {
@@ -951,8 +1054,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 uint32_t rph = 0, u = 0;
                 int64_t gprev = -1;
                 TileIter it;
-                if (my_tiles > 0) it.init(d, t_begin, mtiles);
-                for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles)) {
+                if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
+                for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles, n_tiles, tblk)) {
                     const int4 r = it.record(d);
                     const int64_t g = MODE == 2 ? 0 : it.f;
                     const int acc = int(l & (nacc - 1));
@@ -981,8 +1084,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                         tc_fence_after();
                         const uint32_t bch = BPACK ? smem_u32(sm + C::OFF_RAW + (PACK_ST + rs) * C::SLOT_RAW)
                                                    : bset + c * C::SLOT_RAW;
-                        issue_chunk(dtm, smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), bch, c == 0);
-                        mma_commit(&X.rempty[rs]);
+                        issue_chunk(dtm, a_of(rs, rs), bch, c == 0);
+                        if (PREC == 2) mma_commit(&X.taempty[rs]);
+                        if (PREC == 1 || MODE == 3) mma_commit(&X.rempty[rs]);
                         if (++rs == nrs) {
                             rs = 0;
                             rph ^= 1u;
@@ -1012,10 +1116,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                             break;
                         }
                         tc_fence_after();
-                        issue_chunk(dtm, smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW),
-                                    smem_u32(sm + C::OFF_B + slot * C::SLOT_B), c == 0);
+                        issue_chunk(dtm, a_of(rs, slot), smem_u32(sm + C::OFF_B + slot * C::SLOT_B), c == 0);
                         mma_commit(&X.empty[slot]);
-                        mma_commit(&X.rempty[rs]);
+                        if (PREC == 1) mma_commit(&X.rempty[rs]);
                     }
                     if (ok) mma_commit(&X.tfull[acc]);
                 }
@@ -1046,14 +1149,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             return gc < (int64_t(r.y) << d.nb) ? r.x + int(gc >> d.nb) : -1;
         };
         TileIter it;
-        if (my_tiles > 0) it.init(d, t_begin, mtiles);
+        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
         int64_t fprev = -1;
         int ctprev = -1;
         int inst_c[2] = {-1, -1}, ib_c[2] = {-1, -1}, eb_c[2] = {0, 0}, EB_c[2] = {0, 0};
         int ea_c = 0, EA_c = 0, ncv_c = 0, w_c = 0;
         int64_t base_c = 0;  // C offset of the tile's (row 0, column 0) with the row tile's bits left out
         bool ok = true;
-        for (int64_t j = 0; j < my_tiles; ++j, it.next(d, mtiles)) {
+        for (int64_t j = 0; j < my_tiles; ++j, it.next(d, mtiles, n_tiles, tblk)) {
             if (it.f != fprev || it.ct != ctprev) {
                 const int4 r = it.record(d);
                 const uint32_t mxa = d.mxA ? __ldg(d.mxA + r.z) : 0u;
@@ -1292,7 +1395,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
     __syncthreads();
     if (warp == MMA_WARP) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS2) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_alloc_cols<PREC>()) : "memory");
     }
 }
 
@@ -1433,6 +1536,14 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
     };
     const int ow = width(int64_t(d.max_group) << d.nb);
     const int acw = ndict > 0 ? width(d.nInstB << d.nb) : ow;
+    // B streamed or packed (not held per unit): blocks of tiles dealt
+    // round-robin, each block the tiles that share one operand tile
+    // (schedule 1: a column tile's row tiles; schedule 0: a row tile's
+    // column tiles), so that the operands the CTAs read at any time fit L2
+    auto block_of = [&]() -> int {
+        const int64_t b = d.sched != 0 ? mtiles : ((int64_t(d.max_group) << d.nb) + TBN - 1) / TBN;
+        return (b >= 1 && b * grid * 2 <= tiles) ? int(b) : 0;
+    };
     // B packed once per launch in MMA form and streamed from L2 where it is
     // neither a dictionary nor resident and N >= 64 (a tile's columns lie
     // in one B instance), if the plan reserved room for it
@@ -1443,29 +1554,31 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
         if (precision == 1) {
             k_pack_b<1><<<dim3((unsigned)blocks), 256, 0, s>>>(d, nch);
-            k_step_gemm_tc<1, 3><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, PACK_ST, acw, ow);
+            k_step_gemm_tc<1, 3><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, PACK_ST, acw, ow,
+                                                                            block_of());
         } else {
             k_pack_b<2><<<dim3((unsigned)blocks), 256, 0, s>>>(d, nch);
-            k_step_gemm_tc<2, 3><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, PACK_ST, acw, ow);
+            k_step_gemm_tc<2, 3><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, PACK_ST, acw, ow,
+                                                                            block_of());
         }
         return cudaGetLastError();
     }
     if (ndict > 0) {
         if (precision == 1)
-            k_step_gemm_tc<1, 2><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);
+            k_step_gemm_tc<1, 2><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow, 0);
         else
-            k_step_gemm_tc<2, 2><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);
+            k_step_gemm_tc<2, 2><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow, 0);
     } else if (nbset > 0) {
         if (precision == 1)
-            k_step_gemm_tc<1, 1><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);
+            k_step_gemm_tc<1, 1><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow, 0);
         else
-            k_step_gemm_tc<2, 1><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow);
+            k_step_gemm_tc<2, 1><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, nrs, acw, ow, 0);
     } else if (precision == 1) {
         k_step_gemm_tc<1, 0><<<g, NTHREADS, smem_bytes<1, false>(), s>>>(d, mtiles, err, *a_map, Cfg<1, false>::RST,
-                                                                         acw, ow);
+                                                                         acw, ow, block_of());
     } else {
         k_step_gemm_tc<2, 0><<<g, NTHREADS, smem_bytes<2, false>(), s>>>(d, mtiles, err, *a_map, Cfg<2, false>::RST,
-                                                                         acw, ow);
+                                                                         acw, ow, block_of());
     }
     return cudaGetLastError();
 }

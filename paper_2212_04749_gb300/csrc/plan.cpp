@@ -804,13 +804,15 @@ struct Builder {
         // room for the packed B operand of the largest step that can take it
         // (N >= 64, K >= 8, 64 <= M < 2^31: every B instance, 16 bytes per
         // complex entry, K padded to chunks of 16); steps run one at a time,
-        // so one region serves all; steps above 256 MiB stream B instead
+        // so one region serves all; steps above the cap (256 MiB, or 1/32 of
+        // the workspace limit if that is more) stream B instead
         p.bpack_bytes = 0;
+        const int64_t bpack_cap = std::max(int64_t(256) << 20, p.opt.workspace_limit / 32);
         for (const Step &st : p.steps) {
             if (st.nb < 6 || st.kb < 3 || st.kb > 24 || st.mb < 6 || st.mb > 30) continue;
             const int64_t nch = ((int64_t(1) << st.kb) + 15) / 16;
             const int64_t bytes = p.nodes[st.b].n_inst * (int64_t(1) << (st.nb - 6)) * nch * 16384;
-            if (bytes <= (int64_t(256) << 20)) p.bpack_bytes = std::max(p.bpack_bytes, bytes);
+            if (bytes <= bpack_cap) p.bpack_bytes = std::max(p.bpack_bytes, bytes);
         }
         p.off_bpack = p.bpack_bytes > 0 ? take(p.bpack_bytes) : -1;
         for (Chain &c : p.chains) {
