@@ -281,6 +281,12 @@ constexpr int TMEM_COLS2 = 256;  // accumulators
 // BF16x3 also keeps the split A chunks in TMEM, 32 columns a stage after
 // the accumulators (at most 8 stages), so it allocates all 512 columns
 constexpr int TM_A = TMEM_COLS2, TM_ASTAGE = 32;
+// resident B: the TMEM A stages (8) run apart from the TMA ring (the ring
+// slot is free once the producers have read it), so the A stream runs up
+// to nrs + 8 chunks ahead of the MMAs; packed B ties a stage to its ring
+// slot (the slot also holds the chunk's B)
+constexpr int NTS = 8;
+static_assert(TM_A + NTS * TM_ASTAGE <= 512, "TMEM A stages within the allocation");
 template <int PREC>
 __host__ __device__ constexpr uint32_t tmem_alloc_cols() { return PREC == 2 ? 512u : uint32_t(TMEM_COLS2); }
 
@@ -744,6 +750,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             // BF16x3 (not packed B): the producers release the A slot once
             // they hold its values; otherwise the MMAs' commit does
             mbar_init(&X.rempty[s], (PREC == 2 && MODE != 3) ? NAW : 1);
+        }
+        for (int s = 0; s < NTS; ++s) {
             mbar_init(&X.afull[s], NAW);
             mbar_init(&X.taempty[s], 1);
         }
@@ -891,8 +899,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         // resident B: at each group switch (once the MMAs stopped reading
         // the previous group's B) load the group's B into the pool; BF16x3
         // also splits every A chunk into a TMEM stage
-        int rs = 0;
-        uint32_t rph = 0, u = 0;
+        int rs = 0, ts = 0;
+        uint32_t rph = 0, tph = 0, u = 0;
+        const int nts = BPACK ? nrs : NTS;
         int64_t gprev = -1;
         TileIter it;
         if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
@@ -916,20 +925,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     // the chunk has landed and the MMAs are done with the
                     // TMEM stage's previous chunk
                     bool w = mbar_wait(&X.rfull[rs], rph);
-                    w = w && mbar_wait(&X.taempty[rs], rph ^ 1u);
+                    w = w && mbar_wait(&X.taempty[ts], tph ^ 1u);
                     if (!__all_sync(0xffffffffu, w)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     // packed B: the slot pair waits for the MMAs
-                    a_to_tmem(sm + C::OFF_RAW + rs * C::SLOT_RAW, rs, MODE != 3 ? &X.rempty[rs] : nullptr);
+                    a_to_tmem(sm + C::OFF_RAW + rs * C::SLOT_RAW, ts, MODE != 3 ? &X.rempty[rs] : nullptr);
                     tmem_wait_st();
                     tc_fence_before();
-                    mbar_arrive(&X.afull[rs]);
+                    mbar_arrive(&X.afull[ts]);
                     if (++rs == nrs) {
                         rs = 0;
                         rph ^= 1u;
+                    }
+                    if (++ts == nts) {
+                        ts = 0;
+                        tph ^= 1u;
                     }
                 }
                 if (!ok) {
@@ -1050,8 +1063,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             };
             bool ok = true;
             if constexpr (BRES || BPACK) {
-                int rs = 0;
-                uint32_t rph = 0, u = 0;
+                int rs = 0, ts = 0;
+                uint32_t rph = 0, tph = 0, u = 0;
+                const int nts = BPACK ? nrs : NTS;
                 int64_t gprev = -1;
                 TileIter it;
                 if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
@@ -1077,19 +1091,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     const int ctl = (MODE == 2 || d.sched != 0) ? 0 : r.w / TBN;  // the tile's column tile within the resident B
                     const uint32_t bset = smem_u32(sm + C::OFF_RAW + (nrs + ctl * nch) * C::SLOT_RAW);
                     for (int c = 0; c < nch; ++c) {
-                        if (!mbar_wait(PREC == 2 ? &X.afull[rs] : &X.rfull[rs], rph)) {
+                        if (!mbar_wait(PREC == 2 ? &X.afull[ts] : &X.rfull[rs], PREC == 2 ? tph : rph)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                         const uint32_t bch = BPACK ? smem_u32(sm + C::OFF_RAW + (PACK_ST + rs) * C::SLOT_RAW)
                                                    : bset + c * C::SLOT_RAW;
-                        issue_chunk(dtm, a_of(rs, rs), bch, c == 0);
-                        if (PREC == 2) mma_commit(&X.taempty[rs]);
+                        issue_chunk(dtm, a_of(rs, ts), bch, c == 0);
+                        if (PREC == 2) mma_commit(&X.taempty[ts]);
                         if (PREC == 1 || MODE == 3) mma_commit(&X.rempty[rs]);
                         if (++rs == nrs) {
                             rs = 0;
                             rph ^= 1u;
+                        }
+                        if (++ts == nts) {
+                            ts = 0;
+                            tph ^= 1u;
                         }
                     }
                     if (ok) mma_commit(&X.tfull[acc]);
@@ -1548,7 +1566,14 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
     // neither a dictionary nor resident and N >= 64 (a tile's columns lie
     // in one B instance), if the plan reserved room for it
     const int64_t pack = tc_packed_b_bytes(d);
-    if (ndict == 0 && nbset == 0 && d.tc_resident_b && pack > 0 && d.bpack && pack <= d.bpack_bytes) {
+    const int nch_all = int(((int64_t(1) << d.kb) + TBK - 1) / TBK);
+    // a resident B whose unit (schedule 1: a column tile, 0: a group) runs
+    // fewer than 64 chunks is packed instead where it can be: its load does
+    // not overlap the MMAs, and the unit's MMAs would not hide it
+    const int64_t unit_chunks =
+        (d.sched != 0 ? mtiles : mtiles * (((int64_t(d.max_group) << d.nb) + TBN - 1) / TBN)) * nch_all;
+    if (ndict == 0 && (nbset == 0 || unit_chunks < 64) && d.tc_resident_b && pack > 0 && d.bpack &&
+        pack <= d.bpack_bytes) {
         const int nch = int(((int64_t(1) << d.kb) + TBK - 1) / TBK);
         const int64_t blocks = pack / (TBNR * TBKR * 4);
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;

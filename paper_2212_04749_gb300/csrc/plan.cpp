@@ -804,10 +804,10 @@ struct Builder {
         // room for the packed B operand of the largest step that can take it
         // (N >= 64, K >= 8, 64 <= M < 2^31: every B instance, 16 bytes per
         // complex entry, K padded to chunks of 16); steps run one at a time,
-        // so one region serves all; steps above the cap (256 MiB, or 1/32 of
-        // the workspace limit if that is more) stream B instead
+        // so one region serves all; steps above the cap (256 MiB, or 1/16 of
+        // the workspace limit if that is more) keep B resident or stream it
         p.bpack_bytes = 0;
-        const int64_t bpack_cap = std::max(int64_t(256) << 20, p.opt.workspace_limit / 32);
+        const int64_t bpack_cap = std::max(int64_t(256) << 20, p.opt.workspace_limit / 16);
         for (const Step &st : p.steps) {
             if (st.nb < 6 || st.kb < 3 || st.kb > 24 || st.mb < 6 || st.mb > 30) continue;
             const int64_t nch = ((int64_t(1) << st.kb) + 15) / 16;
