@@ -259,6 +259,33 @@ def test_fused_chains_are_well_formed(tn, name):
     assert p1.info["flops_exec"] == p0.info["flops_exec"]
 
 
+def test_chains_follow_data_dependency_not_step_order(tn):
+    # The TNCO rearrangement of paper SM Sec. V.B: a chain is a run of
+    # producer -> consumer steps, and it runs at its last step, which moves
+    # its earlier steps next to their consumers.  That is legal because every
+    # side operand B_j is produced earlier in the tree's order.  Fusing only
+    # steps that are adjacent in the tree's own order finds fewer fused steps.
+    w = make_workload("grid5x6_m14")
+    p = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, fuse=1)
+    st = p.tn_plan_steps()
+    step_of = {s["node"]: i for i, s in enumerate(st)}
+    chains = {}
+    for i, s in enumerate(st):
+        if s["chain"] >= 0:
+            chains.setdefault(s["chain"], []).append(i)
+    rearranged = [ids for ids in chains.values() if ids[-1] - ids[0] != len(ids) - 1]
+    assert rearranged
+    for ids in rearranged:
+        for i in ids:
+            b = st[i]["b"]
+            assert b not in step_of or step_of[b] < ids[-1]  # side operands exist by the chain's last step
+    # steps fused when a chain may only continue into the next step in order
+    adjacent = sum(len(ids) for ids in chains.values()
+                   if all(j == i + 1 for i, j in zip(ids, ids[1:])))
+    fused = sum(len(ids) for ids in chains.values())
+    assert fused > adjacent
+
+
 def test_open_qubits_plan_structure(tn):
     # correlated batches: open output qubits reach the root, whose instances
     # then hold 2^r amplitudes; rows equal up to their open bits share one
