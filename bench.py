@@ -549,6 +549,8 @@ def run_ours(args, world, rank, local):
     t_plan = time.perf_counter() - t0
     info = plan.info
     lo, hi = batch_range(info["n_batches"], rank, world)
+    if args.batches:
+        hi = min(hi, lo + args.batches)
     ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
     plan.tn_plan_bind(ws, stream=stream)
     amps = torch.zeros(2 * k, dtype=torch.float64, device="cuda")
@@ -749,7 +751,7 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": args.workload, "qubits": w.circuit.n_qubits, "cycles": w.spec.cycles,
                    "bitstrings": k, "rows_of_workload": args.rows or None, "sliced_edges": len(sliced), "slices": 2 ** len(sliced),
-                   "slice_batch": 2 ** info["slice_batch_log2"], "batches_per_rank": hi - lo,
+                   "slice_batch": 2 ** info["slice_batch_log2"], "batches_per_rank": hi - lo, "partial": bool(args.batches) or None,
                    "precision": args.precision,
                    "l2": "512 MiB write between steps; intermediates exceed L2",
                    "flops_eq1": info["flops_ma"], "flops_single_amplitude_x_k": info["flops_sa"],
@@ -798,6 +800,9 @@ def main():
     ap.add_argument("--rows", type=int, default=0,
                     help="contract only the first ROWS bitstrings of the workload with its own tree (a smaller "
                          "case of the same step shapes, e.g. for profiler captures); 0: all")
+    ap.add_argument("--batches", type=int, default=0,
+                    help="contract only the first BATCHES slice batches of each rank's range (a partial "
+                         "contraction, e.g. for profiler captures of a heavily sliced --case); 0: all")
     ap.add_argument("--case", type=int, default=None,
                     help="instead of a named workload, the seeded random circuit and tree of "
                          "costmodel.random_case(CASE) (small plans of a few GB, e.g. for profiler captures)")
