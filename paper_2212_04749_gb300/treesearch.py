@@ -224,6 +224,66 @@ def search(ranker: Ranker, start: np.ndarray, seeds=(), trials=16, steps=40, flo
     return out
 
 
+def measured_climb(ranker: Ranker, start: np.ndarray, measure_fn, steps=20, per_step=150, k_measure=4,
+                   flops_slack=1.5, min_gain=0.01, log=None):
+    """Hill climb that moves only on measured time: per step, up to
+    per_step seeded random rotations of the current tree are ranked by the
+    cost model, the k_measure best (distinct predictions) are measured, and
+    the best of them replaces the current tree if it is at least min_gain
+    faster.  Returns the walk: every measured tree with its times."""
+    from rqc.tree import estimate_cost
+    T = ranker.struct.n_tensors
+    sl, _ = ranker.slice(start)
+    cur = {"ssa": np.asarray(start).tolist(), "sliced": [int(e) for e in sl]}
+    cur["measured_ms"] = measure_fn(np.asarray(start), cur["sliced"])
+    walk = [dict(cur, step=-1)]
+    seen = {np.asarray(start).tobytes()}
+    if log:
+        log(f"measured climb: start {cur['measured_ms']:.2f} ms")
+    for it in range(steps):
+        base = np.asarray(cur["ssa"])
+        base_flops = estimate_cost(ranker.struct, base, ranker.k).flops
+        nbrs = rotations(base, T)
+        cands = []
+        for j in np.random.default_rng(1000 + it).permutation(len(nbrs))[:per_step]:
+            ssa = nbrs[j]
+            key = ssa.tobytes()
+            if key in seen or estimate_cost(ranker.struct, ssa, ranker.k).flops > flops_slack * base_flops:
+                continue
+            seen.add(key)
+            sl2, c = ranker.slice(ssa)
+            if ranker.max_rank is not None and c.max_rank > ranker.max_rank:
+                continue
+            r = ranker.predict(ssa, sl2)
+            if r is not None:
+                r.update({"ssa": ssa.tolist(), "sliced": [int(e) for e in sl2]})
+                cands.append(r)
+        cands.sort(key=lambda r: r["predicted_ms"])
+        picked, preds = [], set()
+        for r in cands:
+            key = round(r["predicted_ms"], 3)
+            if key not in preds:
+                preds.add(key)
+                picked.append(r)
+            if len(picked) == k_measure:
+                break
+        best = None
+        for r in picked:
+            r["measured_ms"] = measure_fn(np.asarray(r["ssa"]), r["sliced"])
+            walk.append(dict(r, step=it))
+            if r["measured_ms"] is not None and (best is None or r["measured_ms"] < best["measured_ms"]):
+                best = r
+        moved = best is not None and best["measured_ms"] < cur["measured_ms"] * (1 - min_gain)
+        if moved:
+            cur = best
+        if log:
+            log(f"measured climb {it}: {len(picked)} measured, best {best['measured_ms'] if best else None} ms, "
+                f"current {cur['measured_ms']:.2f} ms")
+        if not moved:
+            break
+    return cur, walk
+
+
 def main():
     import argparse
     import torch
@@ -242,6 +302,9 @@ def main():
     ap.add_argument("--start", default=None, help="JSON with a start tree (its 'ssa' and 'sliced', e.g. "
                                                     "an earlier --out's 'best')")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--measured-climb", type=int, default=0,
+                    help="instead of ranking by prediction alone: hill-climb from the start tree, measuring the "
+                         "N best predicted rotations per step and moving only on a measured gain")
     args = ap.parse_args()
     torch.cuda.init()
     log = lambda m: print(m, flush=True)  # noqa: E731
@@ -267,6 +330,19 @@ def main():
         with open(args.start) as f:
             st = json.load(f)
         start = np.asarray(st.get("best", st)["ssa"])
+    if args.measured_climb > 0:
+        mfn = lambda ssa, sl: measure(w.circuit, w.bits, ssa, sl, args.precision, limit)  # noqa: E731
+        best, walk = measured_climb(ranker, start, mfn, steps=args.climb, per_step=args.per_step,
+                                    k_measure=args.measured_climb, log=log)
+        res = {"workload": args.workload, "precision": args.precision, "search_s": time.time() - t0,
+               "corpus_rows": int(len(corpus.y)), "start_ms": walk[0]["measured_ms"],
+               "best_ms": best["measured_ms"], "measured": [{k: v for k, v in r.items() if k != "ssa"} for r in walk],
+               "best": best}
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(res, f)
+        print(json.dumps({k: v for k, v in res.items() if k not in ("best", "measured")}))
+        return
     ranked = search(ranker, start, seeds=[int(s) for s in args.seeds.split(",") if s],
                     steps=args.climb, per_step=args.per_step, log=log)
     search_s = time.time() - t0

@@ -57,3 +57,51 @@ def test_stored_diamond53_tree_is_a_valid_tree_of_its_circuit():
     assert c.max_rank <= 32
     seeded = make_workload("diamond53_m12", seeded_tree=True)
     assert c.flops < estimate_cost(seeded.struct, seeded.tree.ssa, w.bits.shape[0]).flops
+
+
+class _FlopsRanker:
+    """Stands in for the cost-model ranker: predicts a tree's time as its
+    Eq. (1) flops (no GPU), unsliced."""
+
+    def __init__(self, w):
+        self.struct, self.k, self.max_rank = w.struct, w.bits.shape[0], None
+
+    def slice(self, ssa):
+        return [], estimate_cost(self.struct, ssa, self.k)
+
+    def predict(self, ssa, sl):
+        return {"predicted_ms": estimate_cost(self.struct, ssa, self.k).flops / 1e6}
+
+
+def test_measured_climb_moves_only_on_measured_gains():
+    # measured time and prediction both = the tree's flops: the walk must
+    # end on a tree no worse than it started, move only on a measured gain
+    # of at least min_gain, and measure only valid trees
+    from paper_2212_04749_gb300.treesearch import measured_climb
+    w = make_workload("grid3x4_m8")
+    T = w.struct.n_tensors
+    rk = _FlopsRanker(w)
+    calls = []
+
+    def fake_measure(ssa, sl):
+        _valid(ssa, T)
+        calls.append(1)
+        return estimate_cost(w.struct, ssa, rk.k).flops / 1e6
+
+    start = np.asarray(w.tree.ssa)
+    best, walk = measured_climb(rk, start, fake_measure, steps=6, per_step=60, k_measure=3, min_gain=0.01)
+    t0 = walk[0]["measured_ms"]
+    assert best["measured_ms"] <= t0
+    assert len(calls) == len(walk) and len(walk) <= 1 + 6 * 3
+    cur = t0
+    for step in sorted({r["step"] for r in walk if r["step"] >= 0}):
+        got = min(r["measured_ms"] for r in walk if r["step"] == step)
+        if got < cur * 0.99:
+            cur = got
+    assert best["measured_ms"] == cur
+    _valid(np.asarray(best["ssa"]), T)
+
+    # a measurement that never improves: the walk stops after one step
+    flat = lambda ssa, sl: 1.0  # noqa: E731
+    best2, walk2 = measured_climb(rk, start, flat, steps=6, per_step=60, k_measure=3)
+    assert best2["measured_ms"] == 1.0 and max(r["step"] for r in walk2) == 0
