@@ -305,6 +305,7 @@ def main():
     ap.add_argument("--measured-climb", type=int, default=0,
                     help="instead of ranking by prediction alone: hill-climb from the start tree, measuring the "
                          "N best predicted rotations per step and moving only on a measured gain")
+    ap.add_argument("--min-gain", type=float, default=0.01, help="measured climb: smallest relative gain to move")
     args = ap.parse_args()
     torch.cuda.init()
     log = lambda m: print(m, flush=True)  # noqa: E731
@@ -333,7 +334,7 @@ def main():
     if args.measured_climb > 0:
         mfn = lambda ssa, sl: measure(w.circuit, w.bits, ssa, sl, args.precision, limit)  # noqa: E731
         best, walk = measured_climb(ranker, start, mfn, steps=args.climb, per_step=args.per_step,
-                                    k_measure=args.measured_climb, log=log)
+                                    k_measure=args.measured_climb, min_gain=args.min_gain, log=log)
         res = {"workload": args.workload, "precision": args.precision, "search_s": time.time() - t0,
                "corpus_rows": int(len(corpus.y)), "start_ms": walk[0]["measured_ms"],
                "best_ms": best["measured_ms"], "measured": [{k: v for k, v in r.items() if k != "ssa"} for r in walk],
