@@ -9,17 +9,18 @@ Seeds: circuit 1000+i, bitstrings 2000+i, tree search 3000+i for workload i.
                      with the largest per-instance intermediate capped at 2^28.
 * ``grid6x7_m10``  : 42 qubits, 6x7 grid, 10 cycles (ABCDCDABAB), 178 fSim
                      gates, 1024 bitstrings, 14 sliced bond edges (2^14
-                     slices).  At 16 cycles the seeded search's trees keep
-                     per-slice intermediates of rank 39 after 14 slices
-                     (~6e18 flops), beyond one GPU; 10 cycles gives rank 23.
+                     slices).  At 16 cycles the search's trees keep
+                     per-slice intermediates of rank 35 or more after 14
+                     slices, beyond one GPU; 10 cycles gives rank 23.
 * ``diamond53_m12``: 53 qubits, 54-site diamond with one dead site,
                      12 cycles, 258 fSim gates, 8192 bitstrings, sliced until
                      the largest per-instance intermediate has <= 2^32 entries.
                      Its tree is the one stored in ``rqc/trees/``: the best
-                     measured tree of the time-ranked tree search
-                     (``paper_2212_04749_gb300.treesearch``), which needs no
-                     slicing (largest intermediate 2^24); ``seeded_tree=True``
-                     gives the seeded random-greedy tree instead.
+                     measured tree of the tree search
+                     (``paper_2212_04749_gb300.treesearch``, its measured
+                     climb over rotations), which needs no slicing (largest
+                     intermediate 2^23); ``seeded_tree=True`` gives the
+                     seeded random-greedy tree instead.
 """
 
 from dataclasses import dataclass

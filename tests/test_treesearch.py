@@ -47,7 +47,7 @@ def test_contracting_along_a_rotated_tree_gives_the_same_amplitudes():
 
 
 def test_stored_diamond53_tree_is_a_valid_tree_of_its_circuit():
-    # the benchmark's tree comes from the time-ranked search; it must be a
+    # the benchmark's tree comes from the tree search; it must be a
     # tree of exactly this circuit's network and keep every intermediate
     # within the 2^32-entry cap of the workload
     w = make_workload("diamond53_m12")
