@@ -718,18 +718,23 @@ def run_ours(args, world, rank, local):
         cfg_now = plan.tn_plan_get_configs()
         chains_now = plan.tn_plan_get_chains()
         marks = []
-        ws_b = torch.empty_like(ws)  # second workspace: the next batch binds while this one runs
+        # further workspaces: the next batches are planned (two host threads)
+        # and bound while this one runs, as far as device memory allows
+        free_b, _ = torch.cuda.mem_get_info()
+        n_extra = max(1, min(2, int(free_b * 0.9) // max(ws.numel(), 1)))
+        extra = [torch.empty_like(ws) for _ in range(n_extra)]
         for _i, _a in contract_batches(w.circuit, [bits] * (args.e2e_steps + 1), w.tree.ssa, sliced,
-                                       args.precision, (ws, ws_b), stream=stream, configs=cfg_now,
+                                       args.precision, [ws] + extra, stream=stream, configs=cfg_now,
                                        chains=chains_now, **popts):
             marks.append(time.perf_counter())
-        del ws_b
+        del extra
         torch.cuda.empty_cache()  # the later measurements size themselves by free device memory
         plan.tn_plan_bind(ws, stream=stream)
         e2e_s = (marks[-1] - marks[0]) / args.e2e_steps
         e2e = {"value": k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(info["upload_bytes"]),
                "d2h_bytes_per_step": int(16 * k), "host_plan_s": t_plan,
-               "planning": "overlapped", "table_upload": "overlapped (two workspaces)"}
+               "planning": f"overlapped ({n_extra} host threads)",
+               "table_upload": f"overlapped ({n_extra + 1} workspaces)"}
 
     correlated = None
     if rank == 0 and world == 1 and args.correlated:
@@ -808,7 +813,7 @@ def main():
                          "costmodel.random_case(CASE) (small plans of a few GB, e.g. for profiler captures)")
     ap.add_argument("--no-peaks", dest="peaks", action="store_false",
                     help="skip the live FP32/TF32/FP64 peak measurements")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0,

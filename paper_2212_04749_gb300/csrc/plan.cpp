@@ -217,47 +217,91 @@ struct Builder {
     void out_instances() {
         const int64_t ku = P.k_unique;
         oi.assign(NN, {});
+        // leaves: the values of their (at most a few) output qubits
+        std::vector<int32_t> key(ku);
         for (int v = 0; v < T; ++v) {
             Node &nd = P.nodes[v];
-            std::vector<int32_t> key(ku);
+            const int no = (int)nd.outs.size();
             for (int64_t u = 0; u < ku; ++u) {
                 int val = 0;
-                for (size_t t = 0; t < nd.outs.size(); ++t) val |= int(P.ubits[u][nd.outs[t]]) << t;
+                for (int t = 0; t < no; ++t) val |= int(P.ubits[u][nd.outs[t]]) << t;
                 key[u] = val;
             }
-            std::vector<int32_t> vals(key);
-            std::sort(vals.begin(), vals.end());
-            vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+            std::vector<int32_t> id(size_t(1) << no, -1);
+            for (int64_t u = 0; u < ku; ++u) id[key[u]] = 0;
+            std::vector<int32_t> vals;
+            for (int32_t x = 0; x < int32_t(id.size()); ++x)
+                if (id[x] >= 0) {
+                    id[x] = (int32_t)vals.size();
+                    vals.push_back(x);
+                }
             if (vals.empty()) vals.push_back(0);
             nd.leaf_outval = vals;
             nd.n_out = (int)vals.size();
             oi[v].resize(ku);
-            for (int64_t u = 0; u < ku; ++u)
-                oi[v][u] = int32_t(std::lower_bound(vals.begin(), vals.end(), key[u]) - vals.begin());
+            for (int64_t u = 0; u < ku; ++u) oi[v][u] = ku > 0 ? id[key[u]] : 0;
         }
+        // internal nodes: the distinct (A instance, B instance) pairs of the
+        // bitstrings, in that order -- two counting-sort passes (by B, then
+        // stably by A) instead of a comparison sort per node
+        std::vector<int32_t> ord(ku), tmp(ku), cnt;
         for (int v = T; v < NN; ++v) {
             Node &nd = P.nodes[v];
             // major key: the operand the step reads as A (the larger one)
             const bool left_big = a_is_left(P.nodes[nd.left], P.nodes[nd.right]);
             const int a = left_big ? nd.left : nd.right, b = left_big ? nd.right : nd.left;
-            const int64_t nb = P.nodes[b].n_out;
-            std::vector<int64_t> key(ku);
-            for (int64_t u = 0; u < ku; ++u) key[u] = int64_t(oi[a][u]) * nb + oi[b][u];
-            std::vector<int64_t> vals(key);
-            std::sort(vals.begin(), vals.end());
-            vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
-            if (vals.empty()) vals.push_back(0);
-            nd.n_out = (int)vals.size();
+            const int32_t na = P.nodes[a].n_out, nb = P.nodes[b].n_out;
+            const std::vector<int32_t> &ka = oi[a], &kb = oi[b];
             std::vector<int32_t> &oa = left_big ? nd.outL : nd.outR, &ob = left_big ? nd.outR : nd.outL;
-            oa.resize(vals.size());
-            ob.resize(vals.size());
-            for (size_t i = 0; i < vals.size(); ++i) {
-                oa[i] = int32_t(vals[i] / nb);
-                ob[i] = int32_t(vals[i] % nb);
-            }
+            oa.clear();
+            ob.clear();
             oi[v].resize(ku);
-            for (int64_t u = 0; u < ku; ++u)
-                oi[v][u] = int32_t(std::lower_bound(vals.begin(), vals.end(), key[u]) - vals.begin());
+            if (int64_t(na) * nb <= (int64_t(1) << 16)) {
+                // few possible pairs: a table over all of them, scanned in
+                // (A, B) order
+                const int32_t np = na * nb;
+                cnt.assign(size_t(np), -1);
+                for (int64_t u = 0; u < ku; ++u) cnt[size_t(ka[u]) * nb + kb[u]] = 0;
+                for (int32_t x = 0; x < np; ++x)
+                    if (cnt[x] == 0) {
+                        cnt[x] = (int32_t)oa.size();
+                        oa.push_back(x / nb);
+                        ob.push_back(x % nb);
+                    }
+                for (int64_t u = 0; u < ku; ++u) oi[v][u] = cnt[size_t(ka[u]) * nb + kb[u]];
+                if (oa.empty()) {
+                    oa.push_back(0);
+                    ob.push_back(0);
+                }
+                nd.n_out = (int)oa.size();
+                continue;
+            }
+            auto pass = [&](const std::vector<int32_t> &k, int32_t nk, const std::vector<int32_t> &in,
+                            std::vector<int32_t> &out) {
+                cnt.assign(size_t(nk) + 1, 0);
+                for (int64_t i = 0; i < ku; ++i) ++cnt[k[in[i]] + 1];
+                for (int32_t x = 0; x < nk; ++x) cnt[x + 1] += cnt[x];
+                for (int64_t i = 0; i < ku; ++i) out[cnt[k[in[i]]]++] = in[i];
+            };
+            std::iota(tmp.begin(), tmp.end(), 0);
+            pass(kb, nb, tmp, ord);
+            pass(ka, na, ord, tmp);  // tmp: u sorted by (A, B), ties in input order
+            int32_t pa = -1, pb = -1;
+            for (int64_t i = 0; i < ku; ++i) {
+                const int32_t u = tmp[i];
+                if (ka[u] != pa || kb[u] != pb) {
+                    pa = ka[u];
+                    pb = kb[u];
+                    oa.push_back(pa);
+                    ob.push_back(pb);
+                }
+                oi[v][u] = int32_t(oa.size()) - 1;
+            }
+            if (oa.empty()) {
+                oa.push_back(0);
+                ob.push_back(0);
+            }
+            nd.n_out = (int)oa.size();
         }
     }
 

@@ -8,9 +8,10 @@ max(planning, contraction) per batch instead of their sum.  Planning is the
 library's host code (the C call releases the interpreter lock); binding,
 contraction and the copy of the amplitudes to pinned host memory stay on the
 calling thread, one batch at a time, so every plan uses the same workspace.
-Given two workspaces, the worker thread also binds batch i + 1 (uploads its
-tables on a side stream) into the one batch i - 1 used, while batch i
-runs in the other.
+Given w >= 2 workspaces, w - 1 worker threads plan batches i + 1 .. i + w - 1
+at once and bind each (upload its tables on a side stream) into the
+workspace an earlier, finished batch used, while batch i runs in its own:
+a batch then costs about max(planning / (w - 1), contraction).
 """
 
 from concurrent.futures import ThreadPoolExecutor
@@ -27,8 +28,9 @@ def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stre
     circ, tree_ssa, sliced, **opts: as for tn.Plan; every batch is planned
     with them.  batches: a sequence of (k_i x n) 0/1 arrays.  precision: a
     precision name or TN_* code.  workspace: a CUDA uint8 tensor of at least
-    the largest plan's workspace_bytes, or a pair of them (the next batch's
-    tables then upload while the current batch runs).  stream: the torch CUDA stream the
+    the largest plan's workspace_bytes, or a list of w >= 2 of them (w - 1
+    later batches are then planned and their tables uploaded while the
+    current batch runs).  stream: the torch CUDA stream the
     contractions run on (default: the current stream).  configs: optional
     per-step configurations applied to every plan (all batches must then
     yield plans with the same step count); chains: optional per-chain fused
@@ -45,27 +47,31 @@ def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stre
         return
     amps = host = None  # grown to the largest batch (rows x amplitudes per row)
     spaces = list(workspace) if isinstance(workspace, (list, tuple)) else [workspace]
-    if len(spaces) not in (1, 2):
-        raise ValueError("workspace: one buffer or a pair")
-    side = torch.cuda.Stream(device=stream.device) if len(spaces) == 2 else None
+    if not spaces:
+        raise ValueError("workspace: at least one buffer")
+    nws = len(spaces)
+    ahead = max(1, nws - 1)  # batches planned while one runs
+    sides = [torch.cuda.Stream(device=stream.device) for _ in range(ahead)] if nws >= 2 else None
 
     def plan_of(i):
         p = tn.Plan(circ, batches[i], tree_ssa, sliced, **opts)
-        if side is not None:  # bind here, into the buffer batch i - 1 has released
-            ws = spaces[i % 2]
+        if sides is not None:  # bind here, into the buffer batch i - nws (finished) used
+            ws = spaces[i % nws]
             if p.info["workspace_bytes"] > ws.numel():
                 raise ValueError(f"batch {i}: plan needs {p.info['workspace_bytes']} workspace bytes, "
                                  f"workspace holds {ws.numel()}")
+            side = sides[i % ahead]
             p.tn_plan_bind(ws, stream=side)
             side.synchronize()
         return p
 
-    with ThreadPoolExecutor(max_workers=1) as ex:
-        nxt = ex.submit(plan_of, 0)
+    with ThreadPoolExecutor(max_workers=ahead) as ex:
+        futs = {j: ex.submit(plan_of, j) for j in range(min(ahead, n))}
         for i in range(n):
-            p = nxt.result()
-            if i + 1 < n:
-                nxt = ex.submit(plan_of, i + 1)
+            p = futs.pop(i).result()
+            # batch i + ahead binds into the buffer of batch i - 1, which has finished
+            if i + ahead < n:
+                futs[i + ahead] = ex.submit(plan_of, i + ahead)
             if configs is not None:
                 for s, c in enumerate(configs):
                     p.tn_plan_set_config(s, int(c))
@@ -76,7 +82,7 @@ def contract_batches(circ, batches, tree_ssa, sliced, precision, workspace, stre
             if amps is None or amps.numel() < 2 * m:
                 amps = torch.zeros(2 * max(m, 1), dtype=torch.float64, device="cuda")
                 host = torch.empty(2 * max(m, 1), dtype=torch.float64, pin_memory=True)
-            if side is None:
+            if sides is None:
                 if p.info["workspace_bytes"] > spaces[0].numel():
                     raise ValueError(f"batch {i}: plan needs {p.info['workspace_bytes']} workspace bytes, "
                                      f"workspace holds {spaces[0].numel()}")

@@ -225,12 +225,13 @@ def search(ranker: Ranker, start: np.ndarray, seeds=(), trials=16, steps=40, flo
 
 
 def measured_climb(ranker: Ranker, start: np.ndarray, measure_fn, steps=20, per_step=150, k_measure=4,
-                   flops_slack=1.5, min_gain=0.01, log=None):
+                   flops_slack=1.5, min_gain=0.01, explore=0, seed=0, log=None):
     """Hill climb that moves only on measured time: per step, up to
     per_step seeded random rotations of the current tree are ranked by the
-    cost model, the k_measure best (distinct predictions) are measured, and
-    the best of them replaces the current tree if it is at least min_gain
-    faster.  Returns the walk: every measured tree with its times."""
+    cost model, the k_measure best (distinct predictions) and `explore`
+    more drawn at random from the rest are measured, and the best of them
+    replaces the current tree if it is at least min_gain faster.  Returns
+    the walk: every measured tree with its times."""
     from rqc.tree import estimate_cost
     T = ranker.struct.n_tensors
     sl, _ = ranker.slice(start)
@@ -245,7 +246,7 @@ def measured_climb(ranker: Ranker, start: np.ndarray, measure_fn, steps=20, per_
         base_flops = estimate_cost(ranker.struct, base, ranker.k).flops
         nbrs = rotations(base, T)
         cands = []
-        for j in np.random.default_rng(1000 + it).permutation(len(nbrs))[:per_step]:
+        for j in np.random.default_rng([seed, 1000 + it]).permutation(len(nbrs))[:per_step]:
             ssa = nbrs[j]
             key = ssa.tobytes()
             if key in seen or estimate_cost(ranker.struct, ssa, ranker.k).flops > flops_slack * base_flops:
@@ -260,13 +261,20 @@ def measured_climb(ranker: Ranker, start: np.ndarray, measure_fn, steps=20, per_
                 cands.append(r)
         cands.sort(key=lambda r: r["predicted_ms"])
         picked, preds = [], set()
+        rest = []
         for r in cands:
             key = round(r["predicted_ms"], 3)
-            if key not in preds:
-                preds.add(key)
+            if key in preds:
+                continue
+            preds.add(key)
+            if len(picked) < k_measure:
                 picked.append(r)
-            if len(picked) == k_measure:
-                break
+            else:
+                rest.append(r)
+        # a few more at random: the ones the model ranks wrongly
+        if explore > 0 and rest:
+            for j in np.random.default_rng([seed, 2000 + it]).permutation(len(rest))[:explore]:
+                picked.append(rest[j])
         best = None
         for r in picked:
             r["measured_ms"] = measure_fn(np.asarray(r["ssa"]), r["sliced"])
@@ -306,6 +314,9 @@ def main():
                     help="instead of ranking by prediction alone: hill-climb from the start tree, measuring the "
                          "N best predicted rotations per step and moving only on a measured gain")
     ap.add_argument("--min-gain", type=float, default=0.01, help="measured climb: smallest relative gain to move")
+    ap.add_argument("--climb-seed", type=int, default=0, help="measured climb: seed of the rotations it samples")
+    ap.add_argument("--explore", type=int, default=0,
+                    help="measured climb: rotations measured per step beyond the best predicted, drawn at random")
     args = ap.parse_args()
     torch.cuda.init()
     log = lambda m: print(m, flush=True)  # noqa: E731
@@ -334,7 +345,8 @@ def main():
     if args.measured_climb > 0:
         mfn = lambda ssa, sl: measure(w.circuit, w.bits, ssa, sl, args.precision, limit)  # noqa: E731
         best, walk = measured_climb(ranker, start, mfn, steps=args.climb, per_step=args.per_step,
-                                    k_measure=args.measured_climb, min_gain=args.min_gain, log=log)
+                                    k_measure=args.measured_climb, min_gain=args.min_gain, explore=args.explore,
+                                    seed=args.climb_seed, log=log)
         res = {"workload": args.workload, "precision": args.precision, "search_s": time.time() - t0,
                "corpus_rows": int(len(corpus.y)), "start_ms": walk[0]["measured_ms"],
                "best_ms": best["measured_ms"], "measured": [{k: v for k, v in r.items() if k != "ssa"} for r in walk],

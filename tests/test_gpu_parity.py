@@ -177,21 +177,21 @@ def test_empty_bitstring_batch_is_a_no_op():
     assert torch.all(sentinel == 7.0)
 
 
-@pytest.mark.parametrize("buffers", [1, 2])
+@pytest.mark.parametrize("buffers", [1, 2, 3])
 def test_pipelined_batches_match_state_vector(buffers):
     # successive bitstring batches of different sizes through the pipeline
-    # (batch i + 1 planned, with two workspaces also bound, while batch i
-    # runs): each against the state vector
+    # (batches i + 1 .. i + w - 1 planned, and with w >= 2 workspaces also
+    # bound, while batch i runs): each against the state vector
     torch, tn = require_cuda()
     from paper_2212_04749_gb300.pipeline import contract_batches
     from rqc import grid_layout, network_structure, random_circuit
     from rqc.bitstrings import uniform_bitstrings
     from rqc.tree import candidate_trees
     c = random_circuit(grid_layout(3, 4), 8, seed=3)
-    batches = [uniform_bitstrings(12, k, seed=s) for s, k in ((1, 300), (2, 77), (3, 512))]
+    batches = [uniform_bitstrings(12, k, seed=s) for s, k in ((1, 300), (2, 77), (3, 512), (4, 64), (5, 200))]
     ssa = candidate_trees(network_structure(c), 300, seed=1, trials=1)[0]
     ws = [torch.empty(256 << 20, dtype=torch.uint8, device="cuda") for _ in range(buffers)]
     got = dict(contract_batches(c, batches, ssa, [], "fp32", ws[0] if buffers == 1 else tuple(ws)))
-    assert sorted(got) == [0, 1, 2]
+    assert sorted(got) == list(range(len(batches)))
     for i, b in enumerate(batches):
         assert rel_l2(got[i], sv.amplitudes(c, b)) <= 1e-5
