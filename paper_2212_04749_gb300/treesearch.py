@@ -292,6 +292,24 @@ def measured_climb(ranker: Ranker, start: np.ndarray, measure_fn, steps=20, per_
     return cur, walk
 
 
+def kick(ranker: Ranker, start: np.ndarray, moves: int, seed: int, flops_slack=1.5) -> np.ndarray:
+    """`moves` seeded random rotations in a row, each keeping the estimated
+    flops within flops_slack of the start tree's and the rank cap."""
+    from rqc.tree import estimate_cost
+    T = ranker.struct.n_tensors
+    rng = np.random.default_rng([seed, 7])
+    base = estimate_cost(ranker.struct, start, ranker.k).flops
+    cur = np.asarray(start)
+    for _ in range(moves):
+        nbrs = rotations(cur, T)
+        for j in rng.permutation(len(nbrs)):
+            c = estimate_cost(ranker.struct, nbrs[j], ranker.k)
+            if c.flops <= flops_slack * base and (ranker.max_rank is None or c.max_rank <= ranker.max_rank):
+                cur = nbrs[j]
+                break
+    return cur
+
+
 def main():
     import argparse
     import torch
@@ -315,6 +333,9 @@ def main():
                          "N best predicted rotations per step and moving only on a measured gain")
     ap.add_argument("--min-gain", type=float, default=0.01, help="measured climb: smallest relative gain to move")
     ap.add_argument("--climb-seed", type=int, default=0, help="measured climb: seed of the rotations it samples")
+    ap.add_argument("--kick", type=int, default=0,
+                    help="measured climb: start from this many seeded random rotations (within the flops slack) "
+                         "of the start tree, to leave its local optimum")
     ap.add_argument("--explore", type=int, default=0,
                     help="measured climb: rotations measured per step beyond the best predicted, drawn at random")
     args = ap.parse_args()
@@ -344,6 +365,8 @@ def main():
         start = np.asarray(st.get("best", st)["ssa"])
     if args.measured_climb > 0:
         mfn = lambda ssa, sl: measure(w.circuit, w.bits, ssa, sl, args.precision, limit)  # noqa: E731
+        if args.kick > 0:
+            start = kick(ranker, start, args.kick, args.climb_seed)
         best, walk = measured_climb(ranker, start, mfn, steps=args.climb, per_step=args.per_step,
                                     k_measure=args.measured_climb, min_gain=args.min_gain, explore=args.explore,
                                     seed=args.climb_seed, log=log)
