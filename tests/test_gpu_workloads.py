@@ -52,3 +52,22 @@ def test_diamond53_sampled_amplitudes(prec):
     err = rel_l2(got[rec["rows"]], rec["amplitudes"])
     print(f"diamond53_m12 {prec}: rel-L2 over {len(rec['rows'])} sampled amplitudes {err:.3e}")
     assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("config", [0, 1])
+def test_diamond53_small_rank_steps_on_the_row_kernel(config):
+    # every step the per-row kernel can take runs on it, under either
+    # schedule (blocks of up to 64 or 4 row passes), among them K = N = 16
+    # steps with groups of one and of several instances; FP32 against the
+    # stored oracle sample
+    mg = _mg()
+    rec = mg.read_json(mg.sample_path("diamond53_m12"))
+    w = make_workload("diamond53_m12")
+    fits = lambda st: st["nb"] <= 4 and st["kb"] + st["nb"] <= 8  # noqa: E731
+    got, p = run_plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, precision="fp32",
+                      force_config=lambda st: config if fits(st) else None, workspace_limit=160 << 30)
+    big = [s for s in p.tn_plan_steps() if s["kb"] == 4 and s["nb"] == 4 and s["mb"] >= 7]
+    assert big and any(s["n_inst"] > s["n_groups"] for s in big)
+    err = rel_l2(got[rec["rows"]], rec["amplitudes"])
+    print(f"diamond53_m12 fp32, row kernel (configuration {config}): rel-L2 {err:.3e}")
+    assert err <= TOL["fp32"], err
