@@ -239,6 +239,10 @@ def measured_climb(ranker: Ranker, start: np.ndarray, measure_fn, steps=20, per_
     cur["measured_ms"] = measure_fn(np.asarray(start), cur["sliced"])
     walk = [dict(cur, step=-1)]
     seen = {np.asarray(start).tobytes()}
+    if cur["measured_ms"] is None:  # the start tree does not plan within the workspace limit
+        if log:
+            log("measured climb: the start tree cannot be planned within the workspace limit")
+        return cur, walk
     if log:
         log(f"measured climb: start {cur['measured_ms']:.2f} ms")
     for it in range(steps):

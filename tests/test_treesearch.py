@@ -105,3 +105,10 @@ def test_measured_climb_moves_only_on_measured_gains():
     flat = lambda ssa, sl: 1.0  # noqa: E731
     best2, walk2 = measured_climb(rk, start, flat, steps=6, per_step=60, k_measure=3)
     assert best2["measured_ms"] == 1.0 and max(r["step"] for r in walk2) == 0
+
+
+def test_measured_climb_stops_on_an_unplannable_start():
+    from paper_2212_04749_gb300.treesearch import measured_climb
+    w = make_workload("grid3x4_m8")
+    best, walk = measured_climb(_FlopsRanker(w), np.asarray(w.tree.ssa), lambda ssa, sl: None, steps=3)
+    assert best["measured_ms"] is None and len(walk) == 1
