@@ -283,7 +283,7 @@ int tn_plan_set_kernel(tn_plan_t plan, int32_t step, int32_t kernel);
  * cost model predicts, each step's time under each configuration.
  *
  * A configuration c in [0, TN_NCONFIG) is a kernel family and a schedule:
- *   0  per-row kernel, blocks of up to 64 row passes   (needs N <= 16, K*N <= 256)
+ *   0  per-row kernel, blocks of up to 16 row passes   (needs N <= 16, K*N <= 256)
  *   1  per-row kernel, blocks of up to 4 row passes; where M is small,
  *      one output instance row per lane group       (same condition)
  *   2  grouped GEMM, consecutive blocks walk the rows of one column tile

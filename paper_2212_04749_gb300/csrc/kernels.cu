@@ -83,7 +83,6 @@ __global__ void k_fill(const FillJobD *__restrict__ jobs, int64_t njobs, const L
 constexpr int ROW_THREADS = 256;
 constexpr int ROW_SB = 2048;  // staged B entries (complex) per block: 16 KB
 constexpr int ROW_CH = 32;    // most instances staged at once
-constexpr int ROW_MAX_PASSES = 64;  // row passes per block (uniform schedule 0)
 
 // Small-rank step (N = 2^NB <= 16, K*N <= 256), grouped: the output
 // instances that read one A instance (a group) are computed together, so
@@ -111,7 +110,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int 
     __shared__ int64_t s_ib[ROW_CH];
     __shared__ int32_t s_e[ROW_CH], s_EC[ROW_CH];
     __shared__ uint32_t s_mx[ROW_CH];
-    __shared__ int64_t s_pass_off[ROW_MAX_PASSES];
+    __shared__ int64_t s_pass_off[16];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = 1 << d.kb;
     const int KN = K * N;
@@ -236,25 +235,14 @@ __global__ void __launch_bounds__(ROW_THREADS) k_step_row(const StepDesc d, int 
             // chunk has at most 4 instances, reduced over the warp once
             const bool few = ch <= 4;
             uint32_t mxr[4] = {0u, 0u, 0u, 0u};
-            // the A rows of the next PF passes are in flight while a pass
-            // computes: PF row slots, slot p holding passes p, p + PF, ...
-            // (a slot is refilled right after its row is taken, and the
-            // pass loop is unrolled by PF so that every slot index is a
-            // constant: no register copy waits on a load in flight)
-            constexpr int PF = KL <= 4 ? 3 : (KL <= 8 ? 2 : 1);
-            float2 a_nx[PF][KL];
-#pragma unroll
-            for (int p = 0; p < PF; ++p)
-                if (p < passes) load_row(a_nx[p], ia, m0 + (int64_t(p) * 8 + warp) * R + sub, true);
-            for (int it0 = 0; it0 < passes; it0 += PF)
-#pragma unroll
-            for (int p = 0; p < PF; ++p) {
-                const int it = it0 + p;
-                if (it >= passes) break;
+            // the next pass's A row is loaded while this pass computes
+            float2 a_nx[KL];
+            load_row(a_nx, ia, m0 + int64_t(warp) * R + sub, true);
+            for (int it = 0; it < passes; ++it) {
                 float2 a[KL];
 #pragma unroll
-                for (int q = 0; q < KL; ++q) a[q] = a_nx[p][q];
-                if (it + PF < passes) load_row(a_nx[p], ia, m0 + (int64_t(it + PF) * 8 + warp) * R + sub, true);
+                for (int q = 0; q < KL; ++q) a[q] = a_nx[q];
+                if (it + 1 < passes) load_row(a_nx, ia, m0 + (int64_t(it + 1) * 8 + warp) * R + sub, true);
                 const int64_t offC = lane_off + s_pass_off[it];
                 for (int j = 0; j < ch; ++j) {
                     float2 acc[N];
@@ -931,9 +919,9 @@ cudaError_t launch_step_row(const StepDesc &d, cudaStream_t s) {
     const int64_t M = int64_t(1) << d.mb;
     int64_t blocks, mblocks = 1;
     int rows_per_block;
-    if (M >= 8 * R) {  // blocks inside one group: up to 64 (schedule 1: 4) passes of 8 warps x R rows
+    if (M >= 8 * R) {  // blocks inside one group: up to 16 (schedule 1: 4) passes of 8 warps x R rows
         int64_t passes = M / (8 * R);
-        const int64_t cap = d.sched == 0 ? ROW_MAX_PASSES : 4;
+        const int64_t cap = d.sched == 0 ? 16 : 4;
         passes = passes > cap ? cap : passes;
         rows_per_block = int(8 * R * passes);
         mblocks = M / rows_per_block;
