@@ -44,6 +44,7 @@ struct PlanObj {
     std::vector<tnk::ChainDesc> chain_desc;  // per fused chain
     int32_t *err_flag = nullptr;      // device word for bounded waits
     bool tc_resident_b = true;        // tensor-core GEMM keeps B in shared memory where it fits
+    bool tc_pair = true;              // tensor-core GEMM: column-tile pairs (N = 256 MMAs) where packed B allows
     bool profile = false;
     std::vector<cudaEvent_t> ev;          // pool, two per profiled launch
     std::vector<int> ev_step;             // step of each recorded pair
@@ -213,6 +214,7 @@ int run_step(PlanObj *o, int s, int precision, cudaStream_t st) {
     tnk::StepDesc d = o->desc[s];
     d.sched = cfg & 1;
     d.tc_resident_b = o->tc_resident_b ? 1 : 0;
+    d.tc_pair = o->tc_pair ? 1 : 0;
     cudaError_t e;
     int fam;
     if (cfg < 2) {
@@ -746,6 +748,14 @@ int tn_plan_set_tc_resident_b(tn_plan_t plan, int32_t enable) {
     if (!plan) return set_err(TN_EINVAL, "tn_plan_set_tc_resident_b: null plan");
     PlanObj *o = reinterpret_cast<PlanObj *>(plan);
     o->tc_resident_b = enable != 0;
+    o->drop_graphs();
+    return TN_OK;
+}
+
+int tn_plan_set_tc_pairs(tn_plan_t plan, int32_t enable) {
+    if (!plan) return set_err(TN_EINVAL, "tn_plan_set_tc_pairs: null plan");
+    PlanObj *o = reinterpret_cast<PlanObj *>(plan);
+    o->tc_pair = enable != 0;
     o->drop_graphs();
     return TN_OK;
 }

@@ -184,11 +184,11 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// byte offset of element (row, kr) in a K-major no-swizzle tile of 128 rows,
-// element size es bytes
-__device__ __forceinline__ uint32_t kmaj_off(int row, int kr, int es) {
+// byte offset of element (row, kr) in a K-major no-swizzle tile of nr rows
+// (a multiple of 8), element size es bytes
+__device__ __forceinline__ uint32_t kmaj_off(int row, int kr, int es, int nr = TBM) {
     const int kb = kr * es;
-    return uint32_t((kb >> 4) * (TBM * 16) + (row >> 3) * 128 + (row & 7) * 16 + (kb & 15));
+    return uint32_t((kb >> 4) * (nr * 16) + (row >> 3) * 128 + (row & 7) * 16 + (kb & 15));
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -315,7 +315,11 @@ struct Cfg {
 };
 constexpr int BRES_MAX_B = 8;  // resident B: at most 8 chunks (nct x nch), so at least 3 A stages
 constexpr int PACK_ST = 5;     // packed B: 5 stages of (A chunk, B chunk) in the pool
+// packed B, column-tile pairs (MODE 4): 3 stages of (A chunk, B chunk of
+// 256 real columns = 2 slots): slots 0-2 A, 3-8 B
+constexpr int PAIR_ST = 3;
 static_assert(2 * PACK_ST <= Cfg<2, true>::NSLOT && PACK_ST <= Cfg<2, true>::RST, "packed-B stages fit the pool");
+static_assert(3 * PAIR_ST <= Cfg<2, true>::NSLOT, "paired packed-B stages fit the pool");
 
 // Per-tile epilogue metadata, written by the metadata warp into a ring of
 // MS slots ahead of the epilogue.
@@ -471,9 +475,11 @@ __device__ __forceinline__ int stage_swz(int u) { return u ^ (((u >> 3) ^ (u >> 
 // One producer thread's B piece: column bcol, complex k 4 kqb .. 4 kqb + 3
 // of a chunk (p0, p1 = the four values), expanded into the real 2x2 form
 // (rows 2 bcol: Re, -Im; 2 bcol + 1: Im, Re) in the K-major no-swizzle
-// layout of a B slot; BF16x3 stores the hi plane, then the lo plane 8 KB on.
+// layout of a B chunk of nr rows (MMA N: 128, or 256 for a column-tile
+// pair); BF16x3 stores the hi plane, then the lo plane nr x 64 bytes on.
 template <int PREC>
-__device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const float4 p0, const float4 p1) {
+__device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const float4 p0, const float4 p1,
+                                         int nr = TBNR) {
     const float2 t4[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
                           make_float2(p1.z, p1.w)};
     const float r0[8] = {t4[0].x, -t4[0].y, t4[1].x, -t4[1].y, t4[2].x, -t4[2].y, t4[3].x, -t4[3].y};
@@ -486,10 +492,10 @@ __device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const
     if (PREC == 1) {
         const float4 a0 = make_float4(r0[0], r0[1], r0[2], r0[3]), a1 = make_float4(r0[4], r0[5], r0[6], r0[7]);
         const float4 b0 = make_float4(r1[0], r1[1], r1[2], r1[3]), b1 = make_float4(r1[4], r1[5], r1[6], r1[7]);
-        *reinterpret_cast<float4 *>(base + kmaj_off(ra, 8 * kqb, 4)) = sw ? b0 : a0;
-        *reinterpret_cast<float4 *>(base + kmaj_off(ra, 8 * kqb + 4, 4)) = sw ? b1 : a1;
-        *reinterpret_cast<float4 *>(base + kmaj_off(rb, 8 * kqb, 4)) = sw ? a0 : b0;
-        *reinterpret_cast<float4 *>(base + kmaj_off(rb, 8 * kqb + 4, 4)) = sw ? a1 : b1;
+        *reinterpret_cast<float4 *>(base + kmaj_off(ra, 8 * kqb, 4, nr)) = sw ? b0 : a0;
+        *reinterpret_cast<float4 *>(base + kmaj_off(ra, 8 * kqb + 4, 4, nr)) = sw ? b1 : a1;
+        *reinterpret_cast<float4 *>(base + kmaj_off(rb, 8 * kqb, 4, nr)) = sw ? a0 : b0;
+        *reinterpret_cast<float4 *>(base + kmaj_off(rb, 8 * kqb + 4, 4, nr)) = sw ? a1 : b1;
     } else {
         __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
 #pragma unroll
@@ -499,10 +505,10 @@ __device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const
             h1[q] = __float2bfloat16_rn(r1[q]);
             l1[q] = __float2bfloat16_rn(r1[q] - __bfloat162float(h1[q]));
         }
-        uint8_t *blo = base + TBNR * TBKR * 2;
+        uint8_t *blo = base + nr * TBKR * 2;
         const uint4 H0 = *reinterpret_cast<uint4 *>(h0), L0 = *reinterpret_cast<uint4 *>(l0);
         const uint4 H1 = *reinterpret_cast<uint4 *>(h1), L1 = *reinterpret_cast<uint4 *>(l1);
-        const uint32_t oa = kmaj_off(ra, 8 * kqb, 2), ob = kmaj_off(rb, 8 * kqb, 2);
+        const uint32_t oa = kmaj_off(ra, 8 * kqb, 2, nr), ob = kmaj_off(rb, 8 * kqb, 2, nr);
         *reinterpret_cast<uint4 *>(base + oa) = sw ? H1 : H0;
         *reinterpret_cast<uint4 *>(blo + oa) = sw ? L1 : L0;
         *reinterpret_cast<uint4 *>(base + ob) = sw ? H0 : H1;
@@ -699,7 +705,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
     // launch) and bulk-copied chunk by chunk beside A from L2, B carrying
     // 2^-eb
     constexpr bool BRES = MODE == 1 || MODE == 2;
-    constexpr bool BPACK = MODE == 3;
+    // MODE 4: packed B with two adjacent column tiles of a row tile (one B
+    // instance's 128 columns) per MMA of N = 256, both accumulators at once
+    constexpr bool PAIR = MODE == 4;
+    constexpr bool BPACK = MODE == 3 || PAIR;
+    constexpr int TSTEP = PAIR ? 2 : 1;  // tiles per unit of A / MMA work
     using C = Cfg<PREC, BRES || BPACK>;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment: the swizzled A slots are whole 8-row atoms
@@ -749,7 +759,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             mbar_init(&X.rfull[s], 1);
             // BF16x3 (not packed B): the producers release the A slot once
             // they hold its values; otherwise the MMAs' commit does
-            mbar_init(&X.rempty[s], (PREC == 2 && MODE != 3) ? NAW : 1);
+            mbar_init(&X.rempty[s], (PREC == 2 && !BPACK) ? NAW : 1);
         }
         for (int s = 0; s < NTS; ++s) {
             mbar_init(&X.afull[s], NAW);
@@ -839,15 +849,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             const uint8_t *bsrc = nullptr;  // packed B: the tile's first chunk
             int64_t fprev = -1;
             int ctprev = -1;
-            for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles, n_tiles, tblk)) {
+            for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; l += TSTEP) {
                 const int4 r = it.record(d);
                 const int m0 = int(it.mt * TBM);
                 if (BPACK && (it.f != fprev || it.ct != ctprev)) {
-                    // the tile's 64 columns lie in one B instance (N >= 64):
-                    // its chunks for this column tile are consecutive
+                    // the tile's 64 columns (a pair's 128) lie in one B
+                    // instance (N >= 64, pairs N >= 128): its chunks for
+                    // this column tile (pair) are consecutive
                     const int ib = __ldg(d.instab + (int64_t(r.x) + (r.w >> d.nb))).y;
-                    const int64_t blk = (int64_t(ib) << (d.nb - 6)) + ((r.w & (N - 1)) >> 6);
-                    bsrc = d.bpack + blk * nch * int64_t(C::SLOT_B);
+                    const int pb = PAIR ? 7 : 6;
+                    const int64_t blk = (int64_t(ib) << (d.nb - pb)) + ((r.w & (N - 1)) >> pb);
+                    bsrc = d.bpack + blk * nch * int64_t(TSTEP * C::SLOT_B);
                     fprev = it.f;
                     ctprev = it.ct;
                 }
@@ -856,16 +868,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&X.rfull[rs], BPACK ? C::SLOT_RAW + C::SLOT_B : C::SLOT_RAW);
+                    mbar_expect_tx(&X.rfull[rs], BPACK ? C::SLOT_RAW + TSTEP * C::SLOT_B : C::SLOT_RAW);
                     tma_load_3d(smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), &tmA, TBKR * c, m0, r.z, &X.rfull[rs]);
                     if (BPACK)
-                        bulk_load(smem_u32(sm + C::OFF_RAW + (PACK_ST + rs) * C::SLOT_RAW), bsrc + c * C::SLOT_B,
-                                  C::SLOT_B, &X.rfull[rs]);
+                        bulk_load(smem_u32(sm + C::OFF_RAW + (PAIR ? PAIR_ST + 2 * rs : PACK_ST + rs) * C::SLOT_RAW),
+                                  bsrc + c * TSTEP * C::SLOT_B, TSTEP * C::SLOT_B, &X.rfull[rs]);
                     if (++rs == nrs) {
                         rs = 0;
                         rph ^= 1u;
                     }
                 }
+                for (int t = 0; t < TSTEP; ++t) it.next(d, mtiles, n_tiles, tblk);
             }
             if (!ok) give_up();
             // loads still in flight land before the CTA leaves (bounded)
@@ -905,9 +918,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         int64_t gprev = -1;
         TileIter it;
         if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
-        for (int64_t l = 0; l < my_tiles && !aborted(); ++l, it.next(d, mtiles, n_tiles, tblk)) {
+        for (int64_t l = 0; l < my_tiles && !aborted(); l += TSTEP) {
             const int4 r = it.record(d);
             const int64_t g = MODE == 2 ? 0 : it.f;  // the dictionary is loaded once
+            for (int t = 0; t < TSTEP; ++t) it.next(d, mtiles, n_tiles, tblk);
             if (BRES && g != gprev) {
                 if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&X.bempty, (u - 1) & 1u))) {
                     give_up();
@@ -932,7 +946,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     }
                     tc_fence_after();
                     // packed B: the slot pair waits for the MMAs
-                    a_to_tmem(sm + C::OFF_RAW + rs * C::SLOT_RAW, ts, MODE != 3 ? &X.rempty[rs] : nullptr);
+                    a_to_tmem(sm + C::OFF_RAW + rs * C::SLOT_RAW, ts, !BPACK ? &X.rempty[rs] : nullptr);
                     tmem_wait_st();
                     tc_fence_before();
                     mbar_arrive(&X.afull[ts]);
@@ -1056,6 +1070,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     }
                 }
             };
+            // a column-tile pair: one MMA of N = 256 per product into both
+            // accumulators (2 x 128 columns, adjacent); B chunk of 256 rows
+            auto issue_pair = [&](uint32_t dtm, uint32_t a0, uint32_t b0, bool first) {
+                constexpr uint32_t LBO2 = 2 * TBM * 16;
+                const uint32_t id = idesc(1u, 2 * TBNR);
+                const uint32_t bl = b0 + 2 * TBNR * TBKR * 2;
+#pragma unroll
+                for (int j = 0; j < TBKR / 16; ++j) {
+                    const uint32_t off = uint32_t(2 * j) * LBO2;
+                    const uint32_t ah = a0 + uint32_t(16 * j), al = ah + 8u;
+                    mma_f16_ts(dtm, ah, sdesc(b0 + off, LBO2, SBO), id, (!first || j > 0) ? 1u : 0u);
+                    mma_f16_ts(dtm, ah, sdesc(bl + off, LBO2, SBO), id, 1u);
+                    mma_f16_ts(dtm, al, sdesc(b0 + off, LBO2, SBO), id, 1u);
+                }
+            };
             // the A operand of a chunk: TF32, the TMA slot; BF16x3, the TMEM stage
             auto a_of = [&](int rs, int tstage) {
                 return PREC == 1 ? smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW)
@@ -1069,11 +1098,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 int64_t gprev = -1;
                 TileIter it;
                 if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
-                for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; ++l, it.next(d, mtiles, n_tiles, tblk)) {
+                for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; l += TSTEP) {
                     const int4 r = it.record(d);
                     const int64_t g = MODE == 2 ? 0 : it.f;
-                    const int acc = int(l & (nacc - 1));
-                    if (!mbar_wait(&X.tempty[acc], (uint32_t(l >> nacc_sh) & 1u) ^ 1u)) {
+                    for (int t = 0; t < TSTEP; ++t) it.next(d, mtiles, n_tiles, tblk);
+                    const int acc = int(l & (nacc - 1));  // pairs: acc 0 (and 1)
+                    bool wok = true;
+                    for (int t = 0; t < TSTEP; ++t)
+                        wok = wok && mbar_wait(&X.tempty[acc + t], (uint32_t((l + t) >> nacc_sh) & 1u) ^ 1u);
+                    if (!wok) {
                         ok = false;
                         break;
                     }
@@ -1096,11 +1129,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t bch = BPACK ? smem_u32(sm + C::OFF_RAW + (PACK_ST + rs) * C::SLOT_RAW)
-                                                   : bset + c * C::SLOT_RAW;
-                        issue_chunk(dtm, a_of(rs, ts), bch, c == 0);
+                        const uint32_t bch =
+                            BPACK ? smem_u32(sm + C::OFF_RAW + (PAIR ? PAIR_ST + 2 * rs : PACK_ST + rs) * C::SLOT_RAW)
+                                  : bset + c * C::SLOT_RAW;
+                        if (PAIR)
+                            issue_pair(dtm, a_of(rs, ts), bch, c == 0);
+                        else
+                            issue_chunk(dtm, a_of(rs, ts), bch, c == 0);
                         if (PREC == 2) mma_commit(&X.taempty[ts]);
-                        if (PREC == 1 || MODE == 3) mma_commit(&X.rempty[rs]);
+                        if (PREC == 1 || BPACK) mma_commit(&X.rempty[rs]);
                         if (++rs == nrs) {
                             rs = 0;
                             rph ^= 1u;
@@ -1110,7 +1147,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                             tph ^= 1u;
                         }
                     }
-                    if (ok) mma_commit(&X.tfull[acc]);
+                    if (ok)
+                        for (int t = 0; t < TSTEP; ++t) mma_commit(&X.tfull[acc + t]);
                 }
             } else {
                 int64_t gch = 0;
@@ -1444,6 +1482,35 @@ __global__ void __launch_bounds__(256) k_pack_b(const StepDesc d, int nch) {
                    make_float4(p1.x * s, p1.y * s, p1.z * s, p1.w * s));
 }
 
+// Packed B for column-tile pairs (MODE 4): 128 columns x 16 complex k per
+// 32 KB block (block (ib * N/128 + pair) * nch + chunk) in the layout of a
+// B operand of 256 rows; thread (column, k quad) expands columns c and
+// c + 64 of its pair.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_pack_b_pair(const StepDesc d, int nch) {
+    const int tid = threadIdx.x, bcol = tid & 63, kqb = tid >> 6;
+    const int64_t blk = blockIdx.x;
+    const int c = int(blk % nch);
+    const int64_t cp_all = blk / nch;  // ib * (N / 128) + pair
+    const int64_t ib = cp_all >> (d.nb - 7);
+    const int64_t n0 = (cp_all & ((int64_t(1) << (d.nb - 7)) - 1)) << 7;
+    const int K = 1 << d.kb;
+    const int k = c * TBK + 4 * kqb;
+    const float s = d.mxB ? pow2f(-exp_of(__ldg(d.mxB + ib))) : 1.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
+        if (k + 3 < K) {
+            const float4 *src = reinterpret_cast<const float4 *>(d.B + ib * d.sB + ((n0 + 64 * h + bcol) << d.kb) + k);
+            p0 = __ldg(src);
+            p1 = __ldg(src + 1);
+        }
+        expand_b<PREC>(d.bpack + blk * (2 * TBNR * TBKR * 4), bcol + 64 * h, kqb,
+                       make_float4(p0.x * s, p0.y * s, p0.z * s, p0.w * s),
+                       make_float4(p1.x * s, p1.y * s, p1.z * s, p1.w * s), 2 * TBNR);
+    }
+}
+
 }  // namespace
 
 int64_t tc_packed_b_bytes(const StepDesc &d) {
@@ -1494,6 +1561,9 @@ cudaError_t init_kernels() {
         if (e != cudaSuccess) return e;
         if (q != cudaDriverEntryPointSuccess || !g_encode) return cudaErrorNotSupported;
     }
+    e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k_step_gemm_tc<2, 4>),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2, true>());
+    if (e != cudaSuccess) return e;
     const void *fns[8] = {reinterpret_cast<const void *>(k_step_gemm_tc<1, 0>),
                           reinterpret_cast<const void *>(k_step_gemm_tc<2, 0>),
                           reinterpret_cast<const void *>(k_step_gemm_tc<1, 1>),
@@ -1577,6 +1647,17 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
         const int nch = int(((int64_t(1) << d.kb) + TBK - 1) / TBK);
         const int64_t blocks = pack / (TBNR * TBKR * 4);
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        // BF16x3, schedule 0, N >= 128: column tiles in pairs (a row tile's
+        // consecutive tiles), one MMA of N = 256 for both; blocks of a row
+        // tile's column tiles dealt round-robin, so that every CTA's tiles
+        // come in pairs
+        if (precision == 2 && d.sched == 0 && d.nb >= 7 && d.tc_pair) {
+            const int64_t nct = ((int64_t(d.max_group) << d.nb) + TBN - 1) / TBN;  // even: N >= 128
+            k_pack_b_pair<2><<<dim3((unsigned)(blocks / 2)), 256, 0, s>>>(d, nch);
+            k_step_gemm_tc<2, 4><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, PAIR_ST, acw, ow,
+                                                                            int(nct));
+            return cudaGetLastError();
+        }
         if (precision == 1) {
             k_pack_b<1><<<dim3((unsigned)blocks), 256, 0, s>>>(d, nch);
             k_step_gemm_tc<1, 3><<<g, NTHREADS, smem_bytes<1, true>(), s>>>(d, mtiles, err, *a_map, PACK_ST, acw, ow,

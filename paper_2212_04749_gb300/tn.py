@@ -21,7 +21,7 @@ PRECISIONS = {"fp32": TN_FP32, "tf32": TN_TF32, "bf16x3": TN_BF16X3}
 
 EXPORTS = ("tn_options_default", "tn_network", "tn_plan", "tn_plan_query", "tn_plan_widths", "tn_plan_steps",
            "tn_plan_bind", "tn_contract", "tn_contract_slices", "tn_xeb", "tn_plan_profile",
-           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_set_tc_resident_b", "tn_plan_get_configs", "tn_pt_moments", "tn_pt_histogram", "tn_sample_completions",
+           "tn_plan_step_times", "tn_plan_set_kernel", "tn_plan_set_config", "tn_plan_set_tc_resident_b", "tn_plan_set_tc_pairs", "tn_plan_get_configs", "tn_pt_moments", "tn_pt_histogram", "tn_sample_completions",
            "tn_plan_features", "tn_plan_autotune", "tn_plan_select", "tn_mlp_grad_scratch_bytes",
            "tn_mlp_forward", "tn_mlp_grad", "tn_mlp_adam", "tn_mlp_to_half", "tn_mlp_forward_f16",
            "tn_plan_check", "tn_contract_static", "tn_fma_probe", "tn_plan_batch_slices", "tn_plan_set_chain",
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = False):
         "tn_plan_set_kernel": (ctypes.c_int, [vp, i32, i32]),
         "tn_plan_set_config": (ctypes.c_int, [vp, i32, i32]),
         "tn_plan_set_tc_resident_b": (ctypes.c_int, [vp, i32]),
+        "tn_plan_set_tc_pairs": (ctypes.c_int, [vp, i32]),
         "tn_plan_get_configs": (ctypes.c_int, [vp, vp, i32]),
         "tn_plan_features": (ctypes.c_int, [vp, ctypes.c_int, i32, vp, vp, i32]),
         "tn_plan_autotune": (ctypes.c_int, [vp, ctypes.c_int, i32, vp, vp, vp, vp]),
@@ -329,6 +330,9 @@ class Plan:
 
     def tn_plan_set_tc_resident_b(self, enable):
         _check(self._lib.tn_plan_set_tc_resident_b(self.h, int(bool(enable))))
+
+    def tn_plan_set_tc_pairs(self, enable):
+        _check(self._lib.tn_plan_set_tc_pairs(self.h, int(bool(enable))))
 
     def tn_plan_get_configs(self):
         n = self.info["n_steps"]

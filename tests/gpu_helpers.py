@@ -13,11 +13,12 @@ def require_cuda():
 
 
 def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, force_kernel=None, force_config=None,
-             **opts):
+             tc_pairs=None, **opts):
     """Amplitudes (complex128, input order) summed over every slice batch.
     force_kernel: a function step_info -> kernel family (or None) applied to
     every step before the run; force_config likewise for the step's
-    configuration (family x schedule)."""
+    configuration (family x schedule); tc_pairs switches the tensor-core
+    column-tile pairs on or off (None: the plan's default)."""
     torch, tn = require_cuda()
     p = tn.Plan(circ, bits, ssa, sliced, **opts)
     if force_kernel is not None:
@@ -30,6 +31,8 @@ def run_plan(circ, bits, ssa, sliced=(), precision="fp32", batches=None, force_k
             c = force_config(st)
             if c is not None:
                 p.tn_plan_set_config(s, c)
+    if tc_pairs is not None:
+        p.tn_plan_set_tc_pairs(tc_pairs)
     ws = torch.empty(max(p.info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
     p.tn_plan_bind(ws, stream=torch.cuda.current_stream())
     amps = torch.zeros(2 * len(bits) * p.info["amps_per_row"], dtype=torch.float64, device="cuda")
