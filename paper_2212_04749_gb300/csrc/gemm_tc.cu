@@ -1648,14 +1648,14 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
         const int64_t blocks = pack / (TBNR * TBKR * 4);
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
         // BF16x3, schedule 0, N >= 128: column tiles in pairs (a row tile's
-        // consecutive tiles), one MMA of N = 256 for both; blocks of a row
-        // tile's column tiles dealt round-robin, so that every CTA's tiles
-        // come in pairs
+        // consecutive tiles; N >= 128 gives every group an even count), one
+        // MMA of N = 256 for both; the pairs dealt round-robin one at a
+        // time, so that the CTAs walking one row tile's pairs run side by
+        // side and read its A from L2 (blocks of the whole row tile per CTA
+        // re-read A from DRAM once per pair: 10 % slower on 2^12 x 2^9 x 2^8)
         if (precision == 2 && d.sched == 0 && d.nb >= 7 && d.tc_pair) {
-            const int64_t nct = ((int64_t(d.max_group) << d.nb) + TBN - 1) / TBN;  // even: N >= 128
             k_pack_b_pair<2><<<dim3((unsigned)(blocks / 2)), 256, 0, s>>>(d, nch);
-            k_step_gemm_tc<2, 4><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, PAIR_ST, acw, ow,
-                                                                            int(nct));
+            k_step_gemm_tc<2, 4><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, PAIR_ST, acw, ow, 2);
             return cudaGetLastError();
         }
         if (precision == 1) {
