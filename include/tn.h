@@ -307,10 +307,11 @@ int tn_plan_set_config(tn_plan_t plan, int32_t step, int32_t config);
 int tn_plan_set_tc_resident_b(tn_plan_t plan, int32_t enable);
 
 /* Column-tile pairs in the tensor-core BF16x3 form with packed B
- * (configuration 2, N >= 128 per instance): enable = 1 (the default) walks
+ * (configuration 2, N >= 64 per instance, K >= 256): enable = 1 (the default) walks
  * a row tile's column tiles two at a time, one MMA of N = 256 writing both
- * accumulators, so one issued instruction does twice the work; 0 walks
- * them one at a time.  Both compute the same values; the switch exists to
+ * accumulators, so one issued instruction does twice the work (N = 64: two
+ * instances of a group; a group of odd size ends with a pad tile whose
+ * columns are not stored); 0 walks them one at a time.  Both compute the same values; the switch exists to
  * measure and test the single-tile form.  TN_EINVAL for a null plan. */
 int tn_plan_set_tc_pairs(tn_plan_t plan, int32_t enable);
 

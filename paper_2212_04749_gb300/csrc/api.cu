@@ -124,6 +124,8 @@ void build_descs(PlanObj *o) {
         d.ctab = at<const int64_t>(o, st.off_col_tiles);
         d.n_ctab = (int64_t)st.col_tiles.size();
         d.trec = at<const int4>(o, st.off_tile_rec);
+        d.ptab = st.n_pair_tiles > 0 ? at<const int2>(o, st.off_pair_tab) : nullptr;
+        d.n_ptab = st.n_pair_tiles;
         d.instab = at<const int2>(o, st.off_inst_ab);
         d.bpack = P.bpack_bytes > 0 ? at<uint8_t>(o, P.off_bpack) : nullptr;
         d.bpack_bytes = P.bpack_bytes;

@@ -191,6 +191,15 @@ __device__ __forceinline__ uint32_t kmaj_off(int row, int kr, int es, int nr = T
     return uint32_t((kb >> 4) * (nr * 16) + (row >> 3) * 128 + (row & 7) * 16 + (kb & 15));
 }
 
+// The same core matrices ordered by 8-row group first: group (row >> 3) at
+// 8 TBKR es bytes, the K core matrices of a group contiguous (128 bytes
+// apart).  Two such chunks of 128 rows placed back to back form one operand
+// of 256 rows (a column-tile pair of two B instances).
+__device__ __forceinline__ uint32_t rmaj_off(int row, int kr, int es) {
+    const int kb = kr * es;
+    return uint32_t((row >> 3) * (8 * TBKR * es) + (kb >> 4) * 128 + (row & 7) * 16 + (kb & 15));
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -408,6 +417,11 @@ struct TileIter {
     // left in the current block
     int64_t bnext;
     int bleft;
+    // pp: column-tile pairs of N = 64 steps, each group's column tiles
+    // padded to an even count nctp (the pad tile has no valid columns);
+    // tile indices count padded tiles (d.ptab)
+    bool pp;
+    int nctp;
 
     __device__ __forceinline__ static int unit_tiles(const StepDesc &d, const int4 &r) {
         return d.sched != 0 ? 1 : int(((int64_t(r.y) << d.nb) + TBN - 1) / TBN);
@@ -417,6 +431,18 @@ struct TileIter {
         nrec = fn < d.n_ctab ? __ldg(d.trec + fn) : make_int4(0, 0, 0, 0);
     }
     __device__ __forceinline__ void init(const StepDesc &d, int64_t T, int64_t mtiles) {
+        if (pp) {
+            const int2 q = __ldg(d.ptab + T / mtiles);  // {group's first column tile, its first padded one}
+            f = q.x;
+            rec = __ldg(d.trec + f);  // column offset 0
+            nct = unit_tiles(d, rec);
+            nctp = nct + (nct & 1);
+            const int64_t local = T - int64_t(q.y) * mtiles;
+            mt = int(local / nctp);
+            ct = int(local - int64_t(mt) * nctp);
+            fetch_next(d);
+            return;
+        }
         int64_t m, g;
         rec = tile_decode(d, T, mtiles, m, &g);
         f = g;
@@ -427,6 +453,7 @@ struct TileIter {
             rec.w = 0;
         }
         nct = unit_tiles(d, rec);
+        nctp = nct;
         fetch_next(d);
     }
     // the current tile's record (first instance, count, A instance, first column)
@@ -436,7 +463,9 @@ struct TileIter {
         return r;
     }
     // the CTA's first tile (blocks: its first block's)
-    __device__ __forceinline__ void start(const StepDesc &d, int64_t mtiles, int64_t n_tiles, int tblk) {
+    __device__ __forceinline__ void start(const StepDesc &d, int64_t mtiles, int64_t n_tiles, int tblk,
+                                          bool padded = false) {
+        pp = padded;
         if (tblk <= 0) {
             bleft = 0x7fffffff;
             init(d, n_tiles * blockIdx.x / gridDim.x, mtiles);
@@ -456,13 +485,14 @@ struct TileIter {
             }
             return;
         }
-        if (++ct < nct) return;
+        if (++ct < nctp) return;
         ct = 0;
         if (++mt < mtiles) return;
         mt = 0;
         f += nct;
         rec = nrec;
         nct = unit_tiles(d, rec);
+        nctp = pp ? nct + (nct & 1) : nct;
         fetch_next(d);
     }
 };
@@ -477,9 +507,11 @@ __device__ __forceinline__ int stage_swz(int u) { return u ^ (((u >> 3) ^ (u >> 
 // (rows 2 bcol: Re, -Im; 2 bcol + 1: Im, Re) in the K-major no-swizzle
 // layout of a B chunk of nr rows (MMA N: 128, or 256 for a column-tile
 // pair); BF16x3 stores the hi plane, then the lo plane nr x 64 bytes on.
-template <int PREC>
+template <int PREC, bool RM = false>
 __device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const float4 p0, const float4 p1,
                                          int nr = TBNR) {
+    // RM: row-group-major order (rmaj_off; nr = TBNR)
+    auto off = [&](int row, int kr, int es) { return RM ? rmaj_off(row, kr, es) : kmaj_off(row, kr, es, nr); };
     const float2 t4[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
                           make_float2(p1.z, p1.w)};
     const float r0[8] = {t4[0].x, -t4[0].y, t4[1].x, -t4[1].y, t4[2].x, -t4[2].y, t4[3].x, -t4[3].y};
@@ -492,10 +524,10 @@ __device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const
     if (PREC == 1) {
         const float4 a0 = make_float4(r0[0], r0[1], r0[2], r0[3]), a1 = make_float4(r0[4], r0[5], r0[6], r0[7]);
         const float4 b0 = make_float4(r1[0], r1[1], r1[2], r1[3]), b1 = make_float4(r1[4], r1[5], r1[6], r1[7]);
-        *reinterpret_cast<float4 *>(base + kmaj_off(ra, 8 * kqb, 4, nr)) = sw ? b0 : a0;
-        *reinterpret_cast<float4 *>(base + kmaj_off(ra, 8 * kqb + 4, 4, nr)) = sw ? b1 : a1;
-        *reinterpret_cast<float4 *>(base + kmaj_off(rb, 8 * kqb, 4, nr)) = sw ? a0 : b0;
-        *reinterpret_cast<float4 *>(base + kmaj_off(rb, 8 * kqb + 4, 4, nr)) = sw ? a1 : b1;
+        *reinterpret_cast<float4 *>(base + off(ra, 8 * kqb, 4)) = sw ? b0 : a0;
+        *reinterpret_cast<float4 *>(base + off(ra, 8 * kqb + 4, 4)) = sw ? b1 : a1;
+        *reinterpret_cast<float4 *>(base + off(rb, 8 * kqb, 4)) = sw ? a0 : b0;
+        *reinterpret_cast<float4 *>(base + off(rb, 8 * kqb + 4, 4)) = sw ? a1 : b1;
     } else {
         __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
 #pragma unroll
@@ -508,7 +540,7 @@ __device__ __forceinline__ void expand_b(uint8_t *base, int bcol, int kqb, const
         uint8_t *blo = base + nr * TBKR * 2;
         const uint4 H0 = *reinterpret_cast<uint4 *>(h0), L0 = *reinterpret_cast<uint4 *>(l0);
         const uint4 H1 = *reinterpret_cast<uint4 *>(h1), L1 = *reinterpret_cast<uint4 *>(l1);
-        const uint32_t oa = kmaj_off(ra, 8 * kqb, 2, nr), ob = kmaj_off(rb, 8 * kqb, 2, nr);
+        const uint32_t oa = off(ra, 8 * kqb, 2), ob = off(rb, 8 * kqb, 2);
         *reinterpret_cast<uint4 *>(base + oa) = sw ? H1 : H0;
         *reinterpret_cast<uint4 *>(blo + oa) = sw ? L1 : L0;
         *reinterpret_cast<uint4 *>(base + ob) = sw ? H0 : H1;
@@ -706,17 +738,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
     // 2^-eb
     constexpr bool BRES = MODE == 1 || MODE == 2;
     // MODE 4: packed B with two adjacent column tiles of a row tile (one B
-    // instance's 128 columns) per MMA of N = 256, both accumulators at once
+    // instance's 128 columns, or with N = 64 two instances' 64) per MMA of
+    // N = 256, both accumulators at once
     constexpr bool PAIR = MODE == 4;
     constexpr bool BPACK = MODE == 3 || PAIR;
     constexpr int TSTEP = PAIR ? 2 : 1;  // tiles per unit of A / MMA work
+    // pairs with N = 64: the pair's two column tiles are two instances of
+    // the group (B packed per instance in row-group-major order, four bulk
+    // copies per chunk), groups padded to an even tile count
+    const bool PP = PAIR && d.nb == 6;
     using C = Cfg<PREC, BRES || BPACK>;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment: the swizzled A slots are whole 8-row atoms
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     Ctrl &X = *reinterpret_cast<Ctrl *>(sm + C::OFF_CTRL);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t n_tiles = d.n_ctab * mtiles;
+    const int64_t n_tiles = (PP ? d.n_ptab : d.n_ctab) * mtiles;
     const int N = 1 << d.nb;
     const int K = 1 << d.kb;
     const int nch = (K + TBK - 1) / TBK;
@@ -843,23 +880,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             int64_t issued = 0;
             bool ok = true;
             TileIter it;
-            if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
+            if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
             int rs = 0;
             uint32_t rph = 0;
-            const uint8_t *bsrc = nullptr;  // packed B: the tile's first chunk
+            const uint8_t *bsrc = nullptr;   // packed B: the tile's first chunk
+            const uint8_t *bsrc1 = nullptr;  // N = 64 pairs: the second tile's
             int64_t fprev = -1;
             int ctprev = -1;
             for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; l += TSTEP) {
                 const int4 r = it.record(d);
                 const int m0 = int(it.mt * TBM);
                 if (BPACK && (it.f != fprev || it.ct != ctprev)) {
-                    // the tile's 64 columns (a pair's 128) lie in one B
-                    // instance (N >= 64, pairs N >= 128): its chunks for
-                    // this column tile (pair) are consecutive
-                    const int ib = __ldg(d.instab + (int64_t(r.x) + (r.w >> d.nb))).y;
-                    const int pb = PAIR ? 7 : 6;
-                    const int64_t blk = (int64_t(ib) << (d.nb - pb)) + ((r.w & (N - 1)) >> pb);
-                    bsrc = d.bpack + blk * nch * int64_t(TSTEP * C::SLOT_B);
+                    const int64_t i0 = int64_t(r.x) + (r.w >> d.nb);
+                    const int ib = __ldg(d.instab + i0).y;
+                    if (PP) {
+                        // N = 64: tile ct is instance ct of the group; the
+                        // pad tile (odd groups) repeats the first tile's B
+                        const int ib1 = it.ct + 1 < it.nct ? __ldg(d.instab + i0 + 1).y : ib;
+                        bsrc = d.bpack + int64_t(ib) * nch * C::SLOT_B;
+                        bsrc1 = d.bpack + int64_t(ib1) * nch * C::SLOT_B;
+                    } else {
+                        // the tile's 64 columns (a pair's 128) lie in one B
+                        // instance (N >= 64, pairs N >= 128): its chunks for
+                        // this column tile (pair) are consecutive
+                        const int pb = PAIR ? 7 : 6;
+                        const int64_t blk = (int64_t(ib) << (d.nb - pb)) + ((r.w & (N - 1)) >> pb);
+                        bsrc = d.bpack + blk * nch * int64_t(TSTEP * C::SLOT_B);
+                    }
                     fprev = it.f;
                     ctprev = it.ct;
                 }
@@ -870,9 +917,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                     }
                     mbar_expect_tx(&X.rfull[rs], BPACK ? C::SLOT_RAW + TSTEP * C::SLOT_B : C::SLOT_RAW);
                     tma_load_3d(smem_u32(sm + C::OFF_RAW + rs * C::SLOT_RAW), &tmA, TBKR * c, m0, r.z, &X.rfull[rs]);
-                    if (BPACK)
-                        bulk_load(smem_u32(sm + C::OFF_RAW + (PAIR ? PAIR_ST + 2 * rs : PACK_ST + rs) * C::SLOT_RAW),
-                                  bsrc + c * TSTEP * C::SLOT_B, TSTEP * C::SLOT_B, &X.rfull[rs]);
+                    const uint32_t bdst = smem_u32(sm + C::OFF_RAW + (PAIR ? PAIR_ST + 2 * rs : PACK_ST + rs) * C::SLOT_RAW);
+                    if (PP) {  // hi planes of both tiles, then both lo planes
+                        constexpr int PL = C::SLOT_B / 2;
+                        const uint8_t *s0 = bsrc + int64_t(c) * C::SLOT_B, *s1 = bsrc1 + int64_t(c) * C::SLOT_B;
+                        bulk_load(bdst, s0, PL, &X.rfull[rs]);
+                        bulk_load(bdst + PL, s1, PL, &X.rfull[rs]);
+                        bulk_load(bdst + 2 * PL, s0 + PL, PL, &X.rfull[rs]);
+                        bulk_load(bdst + 3 * PL, s1 + PL, PL, &X.rfull[rs]);
+                    } else if (BPACK) {
+                        bulk_load(bdst, bsrc + c * TSTEP * C::SLOT_B, TSTEP * C::SLOT_B, &X.rfull[rs]);
+                    }
                     if (++rs == nrs) {
                         rs = 0;
                         rph ^= 1u;
@@ -917,7 +972,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         const int nts = BPACK ? nrs : NTS;
         int64_t gprev = -1;
         TileIter it;
-        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
+        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
         for (int64_t l = 0; l < my_tiles && !aborted(); l += TSTEP) {
             const int4 r = it.record(d);
             const int64_t g = MODE == 2 ? 0 : it.f;  // the dictionary is loaded once
@@ -974,7 +1029,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         int ctprev = -1;
         int c_iss = 0;  // chunk of the tile being issued
         TileIter it;
-        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
+        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
         for (int64_t gch = 0; gch < total_chunks && !aborted(); ++gch) {
             // B pieces run LOOK chunks ahead.  Each thread reads back only
             // the 32 bytes it copied, and its raw slot was last used by a
@@ -1072,17 +1127,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             };
             // a column-tile pair: one MMA of N = 256 per product into both
             // accumulators (2 x 128 columns, adjacent); B chunk of 256 rows
+            // (hi plane, lo plane 16 KB on), K-major core matrices in the
+            // pair packing's order (K step 8 KB apart) or, N = 64 pairs,
+            // row-group-major (a row group's K core matrices contiguous)
+            const uint32_t plbo = PP ? 128u : 2 * TBM * 16, psbo = PP ? uint32_t(8 * TBKR * 2) : SBO;
+            const uint32_t pks = PP ? 256u : 4 * TBM * 16;  // bytes per K step of 16
             auto issue_pair = [&](uint32_t dtm, uint32_t a0, uint32_t b0, bool first) {
-                constexpr uint32_t LBO2 = 2 * TBM * 16;
                 const uint32_t id = idesc(1u, 2 * TBNR);
                 const uint32_t bl = b0 + 2 * TBNR * TBKR * 2;
 #pragma unroll
                 for (int j = 0; j < TBKR / 16; ++j) {
-                    const uint32_t off = uint32_t(2 * j) * LBO2;
+                    const uint32_t off = uint32_t(j) * pks;
                     const uint32_t ah = a0 + uint32_t(16 * j), al = ah + 8u;
-                    mma_f16_ts(dtm, ah, sdesc(b0 + off, LBO2, SBO), id, (!first || j > 0) ? 1u : 0u);
-                    mma_f16_ts(dtm, ah, sdesc(bl + off, LBO2, SBO), id, 1u);
-                    mma_f16_ts(dtm, al, sdesc(b0 + off, LBO2, SBO), id, 1u);
+                    mma_f16_ts(dtm, ah, sdesc(b0 + off, plbo, psbo), id, (!first || j > 0) ? 1u : 0u);
+                    mma_f16_ts(dtm, ah, sdesc(bl + off, plbo, psbo), id, 1u);
+                    mma_f16_ts(dtm, al, sdesc(b0 + off, plbo, psbo), id, 1u);
                 }
             };
             // the A operand of a chunk: TF32, the TMA slot; BF16x3, the TMEM stage
@@ -1097,7 +1156,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 const int nts = BPACK ? nrs : NTS;
                 int64_t gprev = -1;
                 TileIter it;
-                if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
+                if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
                 for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; l += TSTEP) {
                     const int4 r = it.record(d);
                     const int64_t g = MODE == 2 ? 0 : it.f;
@@ -1205,7 +1264,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             return gc < (int64_t(r.y) << d.nb) ? r.x + int(gc >> d.nb) : -1;
         };
         TileIter it;
-        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk);
+        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
         int64_t fprev = -1;
         int ctprev = -1;
         int inst_c[2] = {-1, -1}, ib_c[2] = {-1, -1}, eb_c[2] = {0, 0}, EB_c[2] = {0, 0};
@@ -1460,7 +1519,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
 // layout of a B stage (real 2x2 form, K-major, TF32 or BF16 hi and lo
 // planes), each column multiplied by its instance's 2^-eb (exact).  One
 // block per CTA; thread (column, k quad) as in the producers' expansion.
-template <int PREC>
+// RM: row-group-major order (N = 64 column-tile pairs: two instances'
+// blocks side by side form one operand of 256 rows).
+template <int PREC, bool RM = false>
 __global__ void __launch_bounds__(256) k_pack_b(const StepDesc d, int nch) {
     const int tid = threadIdx.x, bcol = tid & 63, kqb = tid >> 6;
     const int64_t blk = blockIdx.x;
@@ -1477,7 +1538,7 @@ __global__ void __launch_bounds__(256) k_pack_b(const StepDesc d, int nch) {
         p0 = __ldg(src);
         p1 = __ldg(src + 1);
     }
-    expand_b<PREC>(d.bpack + blk * (TBNR * TBKR * 4), bcol, kqb,
+    expand_b<PREC, RM>(d.bpack + blk * (TBNR * TBKR * 4), bcol, kqb,
                    make_float4(p0.x * s, p0.y * s, p0.z * s, p0.w * s),
                    make_float4(p1.x * s, p1.y * s, p1.z * s, p1.w * s));
 }
@@ -1647,14 +1708,24 @@ cudaError_t launch_step_gemm_tc(const StepDesc &d, const CUtensorMap *a_map, int
         const int nch = int(((int64_t(1) << d.kb) + TBK - 1) / TBK);
         const int64_t blocks = pack / (TBNR * TBKR * 4);
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-        // BF16x3, schedule 0, N >= 128: column tiles in pairs (a row tile's
-        // consecutive tiles; N >= 128 gives every group an even count), one
-        // MMA of N = 256 for both; the pairs dealt round-robin one at a
-        // time, so that the CTAs walking one row tile's pairs run side by
-        // side and read its A from L2 (blocks of the whole row tile per CTA
-        // re-read A from DRAM once per pair: 10 % slower on 2^12 x 2^9 x 2^8)
-        if (precision == 2 && d.sched == 0 && d.nb >= 7 && d.tc_pair) {
-            k_pack_b_pair<2><<<dim3((unsigned)(blocks / 2)), 256, 0, s>>>(d, nch);
+        // BF16x3, schedule 0, N >= 64: column tiles in pairs (a row tile's
+        // consecutive tiles; N >= 128 gives every group an even count, with
+        // N = 64 groups of odd size get a pad tile), one MMA of N = 256 for
+        // both; the pairs dealt round-robin one at a time, so that the CTAs
+        // walking one row tile's pairs run side by side and read its A from
+        // L2 (blocks of the whole row tile per CTA re-read A from DRAM once
+        // per pair: 10 % slower on 2^12 x 2^9 x 2^8); N = 64 only where pad
+        // tiles add at most 1/8 (groups of one instance would double the
+        // MMAs).  K >= 256 only: a pair holds both accumulators, so its
+        // epilogue does not overlap the next pair's MMAs, which costs more
+        // than the halved MMA issue gains on short K (measured: K = 128
+        // 5-12 % slower, K = 256 1-10 % faster, K = 512 22-49 % faster)
+        const bool pad_ok = d.nb == 6 && d.ptab && d.n_ptab * 8 <= d.n_ctab * 9;
+        if (precision == 2 && d.sched == 0 && d.kb >= 8 && (d.nb >= 7 || pad_ok) && d.tc_pair) {
+            if (d.nb == 6)
+                k_pack_b<2, true><<<dim3((unsigned)blocks), 256, 0, s>>>(d, nch);
+            else
+                k_pack_b_pair<2><<<dim3((unsigned)(blocks / 2)), 256, 0, s>>>(d, nch);
             k_step_gemm_tc<2, 4><<<g, NTHREADS, smem_bytes<2, true>(), s>>>(d, mtiles, err, *a_map, PAIR_ST, acw, ow, 2);
             return cudaGetLastError();
         }

@@ -42,6 +42,9 @@ struct StepDesc {
     const int64_t *ctab;          // non-empty column tiles: (group << 20) | tile of 64 columns
     int64_t n_ctab;
     const int4 *trec;             // per column tile: {first instance, count, A instance, first column}
+    const int2 *ptab;             // N = 64: per column tile with groups padded to even counts,
+                                  // {group's first column tile, its first padded one} (else null)
+    int64_t n_ptab;
     const int2 *instab;           // per output instance: {A instance, B instance}
     uint8_t *bpack;               // tensor cores: scratch for B packed in MMA form (null: none)
     int64_t bpack_bytes;

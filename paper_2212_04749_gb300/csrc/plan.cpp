@@ -844,6 +844,30 @@ struct Builder {
                 push_upload(p, st.off_inst_ab, ab);
                 push_upload(p, st.off_tile_rec, rec);
             }
+            st.n_pair_tiles = 0;
+            st.off_pair_tab = -1;
+            if (st.nb == 6) {
+                for (int64_t g = 0; g < st.n_groups; ++g) {
+                    const int64_t nct = st.group_first[g + 1] - st.group_first[g];
+                    st.n_pair_tiles += nct + (nct & 1);
+                }
+                st.off_pair_tab = take(st.n_pair_tiles * 8);
+                if (emit) {
+                    std::vector<int32_t> pt;
+                    pt.reserve(size_t(2 * st.n_pair_tiles));
+                    int64_t f = 0, fp = 0;
+                    for (int64_t g = 0; g < st.n_groups; ++g) {
+                        const int64_t nct = st.group_first[g + 1] - st.group_first[g];
+                        for (int64_t t = 0; t < nct + (nct & 1); ++t) {
+                            pt.push_back(int32_t(f));
+                            pt.push_back(int32_t(fp));
+                        }
+                        f += nct;
+                        fp += nct + (nct & 1);
+                    }
+                    push_upload(p, st.off_pair_tab, pt);
+                }
+            }
         }
         // room for the packed B operand of the largest step that can take it
         // (N >= 64, K >= 8, 64 <= M < 2^31: every B instance, 16 bytes per

@@ -101,6 +101,11 @@ struct Step {
     int64_t off_col_tiles = -1;
     int64_t off_tile_rec = -1;         // per column tile: {first instance, count, A instance, first column}
     int64_t off_inst_ab = -1;          // per output instance: {A instance, B instance} (int32 pairs)
+    // N = 64 (one column tile per instance): column tiles with every group
+    // padded to an even count, for the tensor cores' column-tile pairs;
+    // per padded tile {the group's first column tile, its first padded one}
+    int64_t n_pair_tiles = 0;
+    int64_t off_pair_tab = -1;
     int kernel = 0;          // 0 = per-row SIMT, 1 = tiled SIMT GEMM, 2 = tensor-core GEMM
     int chain = -1;          // fused chain holding this step (-1: none)
     bool chain_last = false; // the chain runs at its last step; the others launch nothing

@@ -75,22 +75,25 @@ def test_diamond53_small_rank_steps_on_the_row_kernel(config):
 
 @pytest.mark.parametrize("pairs", [True, False])
 def test_diamond53_column_tile_pairs(pairs):
-    # every tensor-core step with N >= 128 per instance on configuration 2
-    # (a row tile's column tiles back to back): with pairs on, BF16x3 steps
-    # whose B is packed walk the column tiles two at a time, one MMA of
-    # N = 256 into both accumulators; off, one at a time; both against the
-    # stored oracle sample
+    # every tensor-core step with N >= 64 per instance and K >= 256 on
+    # configuration 2 (a row tile's column tiles back to back): with pairs
+    # on, BF16x3 steps whose B is packed walk the column tiles two at a
+    # time, one MMA of N = 256 into both accumulators (N = 64: two instances
+    # of a group, a group of odd size ending with a pad tile); off, one at a
+    # time; both against the stored oracle sample
     mg = _mg()
     rec = mg.read_json(mg.sample_path("diamond53_m12"))
     w = make_workload("diamond53_m12")
-    wide = lambda st: st["nb"] >= 7 and st["kb"] >= 3 and st["mb"] >= 6  # noqa: E731
+    wide = lambda st: st["nb"] >= 6 and st["kb"] >= 8 and st["mb"] >= 6  # noqa: E731
     got, p = run_plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, precision="bf16x3",
                       force_config=lambda st: 2 if wide(st) else None, tc_pairs=pairs,
                       workspace_limit=160 << 30)
     kinds = p.tn_plan_step_times()[1]
     steps = [s for s, k in zip(p.tn_plan_steps(), kinds) if k == 2 and wide(s)]
-    # several groups and several K chunks among them
+    # several groups and several K chunks among them; N = 64 steps whose
+    # groups are not all of even size (pad tiles)
     assert any(s["n_groups"] > 1 for s in steps) and any(s["kb"] >= 6 for s in steps)
+    assert any(s["nb"] == 6 and s["n_inst"] % 2 and s["n_inst"] >= 8 * s["n_groups"] for s in steps)
     err = rel_l2(got[rec["rows"]], rec["amplitudes"])
     print(f"diamond53_m12 bf16x3, column-tile pairs {pairs}: {len(steps)} wide steps, rel-L2 {err:.3e}")
     assert err <= TOL["bf16x3"], err
