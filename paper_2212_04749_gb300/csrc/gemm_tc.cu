@@ -719,7 +719,7 @@ __device__ __forceinline__ void fold_max16(const uint32_t (&r)[32], EpiMeta &em,
 
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 warps on a sub-partition)
-    k_step_gemm_tc(const StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA, int nrs,
+    k_step_gemm_tc(const __grid_constant__ StepDesc d, int64_t mtiles, int32_t *err, const __grid_constant__ CUtensorMap tmA, int nrs,
                    int acw, int ow, int tblk) {
     // MODE 0: B streamed chunk by chunk; 1: B resident (a group's or a
     // column tile's), rescale folded into it; 2: B dictionary, every B
@@ -819,19 +819,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         constexpr int64_t NONE = 0x7fffffffffffffffLL;  // row bits at or above mb: never stored
         auto rowkey = [&](int b) -> int64_t { return b < d.mb ? (int64_t(1) << d.pCm[b]) : NONE; };
         auto colkey = [&](int j) -> int64_t { return j < d.nb ? (int64_t(1) << d.pCn[j]) : (d.sC << (j - d.nb)); };
+        // rank of each bit by destination stride (ties by index); unrolled
+        // so that the keys stay in registers
         int64_t key[9];
+#pragma unroll
         for (int b = 0; b < 5; ++b) key[b] = rowkey(b);
+#pragma unroll
         for (int j = 0; j < 4; ++j) key[5 + j] = colkey(j);
-        int perm[9];
-        for (int b = 0; b < 9; ++b) perm[b] = b;
-        for (int a = 1; a < 9; ++a)
-            for (int b = a; b > 0 && key[perm[b]] < key[perm[b - 1]]; --b) {
-                const int t = perm[b];
-                perm[b] = perm[b - 1];
-                perm[b - 1] = t;
-            }
-        for (int k = 0; k < 9; ++k) {
-            const int b = perm[k];
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            int k = 0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) k += (key[a] < key[b] || (key[a] == key[b] && a < b)) ? 1 : 0;
             mp.rank[b] = k;
             mp.doff[k] = key[b];
             mp.dcol[k] = b < 5 ? 0 : (1 << (b - 5));
