@@ -970,12 +970,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         uint32_t rph = 0, tph = 0, u = 0;
         const int nts = BPACK ? nrs : NTS;
         int64_t gprev = -1;
+        // packed B: only the chunk count matters here, no tile positions
         TileIter it;
-        if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
+        if (!BPACK && my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
         for (int64_t l = 0; l < my_tiles && !aborted(); l += TSTEP) {
-            const int4 r = it.record(d);
-            const int64_t g = MODE == 2 ? 0 : it.f;  // the dictionary is loaded once
-            for (int t = 0; t < TSTEP; ++t) it.next(d, mtiles, n_tiles, tblk);
+            int4 r = make_int4(0, 0, 0, 0);
+            int64_t g = 0;  // the dictionary is loaded once
+            if constexpr (!BPACK) {
+                r = it.record(d);
+                if (MODE != 2) g = it.f;
+                it.next(d, mtiles, n_tiles, tblk);
+            }
             if (BRES && g != gprev) {
                 if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&X.bempty, (u - 1) & 1u))) {
                     give_up();
@@ -1154,12 +1159,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                 uint32_t rph = 0, tph = 0, u = 0;
                 const int nts = BPACK ? nrs : NTS;
                 int64_t gprev = -1;
+                // packed B: the MMAs need no tile positions (a unit is nch
+                // chunks of the rings whatever its tile)
                 TileIter it;
-                if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
+                if (!BPACK && my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
                 for (int64_t l = 0; l < my_tiles && ok && !*abort_flag; l += TSTEP) {
-                    const int4 r = it.record(d);
-                    const int64_t g = MODE == 2 ? 0 : it.f;
-                    for (int t = 0; t < TSTEP; ++t) it.next(d, mtiles, n_tiles, tblk);
+                    int4 r = make_int4(0, 0, 0, 0);
+                    int64_t g = 0;
+                    if constexpr (!BPACK) {
+                        r = it.record(d);
+                        if (MODE != 2) g = it.f;
+                        it.next(d, mtiles, n_tiles, tblk);
+                    }
                     const int acc = int(l & (nacc - 1));  // pairs: acc 0 (and 1)
                     bool wok = true;
                     for (int t = 0; t < TSTEP; ++t)
