@@ -174,6 +174,9 @@ typedef struct {
     int32_t chain_last;       /* 1 if the chain runs at this step (its last) */
     int8_t c_pos_m[40];       /* address bit of C holding each m bit, and each n bit */
     int8_t c_pos_n[24];
+    int64_t max_group;        /* output instances in the largest group */
+    int64_t n_pair_tiles;     /* N = 64: 64-column tiles with every group padded to an even
+                                 count (the tensor cores' column-tile pairs), else 0 */
 } tn_step_info;
 
 int tn_plan_steps(tn_plan_t plan, tn_step_info *steps, int32_t n);

@@ -473,6 +473,10 @@ int tn_plan_steps(tn_plan_t plan, tn_step_info *out, int32_t n) {
         r.chain_last = st.chain_last ? 1 : 0;
         for (int j = 0; j < 40; ++j) r.c_pos_m[j] = j < st.mb ? st.pCm[j] : -1;
         for (int j = 0; j < 24; ++j) r.c_pos_n[j] = j < st.nb ? st.pCn[j] : -1;
+        int64_t mg = 0;
+        for (int64_t g = 0; g < st.n_groups; ++g) mg = std::max(mg, st.group_first[g + 1] - st.group_first[g]);
+        r.max_group = mg;
+        r.n_pair_tiles = st.n_pair_tiles;
     }
     return TN_OK;
 }

@@ -79,7 +79,8 @@ class tn_step_info(ctypes.Structure):
                 ("a_run_m", ctypes.c_int32), ("a_run_k", ctypes.c_int32), ("b_run_k", ctypes.c_int32),
                 ("b_run_n", ctypes.c_int32), ("n_groups", ctypes.c_int64),
                 ("chain", ctypes.c_int32), ("chain_last", ctypes.c_int32),
-                ("c_pos_m", ctypes.c_int8 * 40), ("c_pos_n", ctypes.c_int8 * 24)]
+                ("c_pos_m", ctypes.c_int8 * 40), ("c_pos_n", ctypes.c_int8 * 24),
+                ("max_group", ctypes.c_int64), ("n_pair_tiles", ctypes.c_int64)]
 
 
 _lib = None

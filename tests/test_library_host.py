@@ -133,6 +133,33 @@ def test_plan_cost_is_eq1_and_executed_without_recomputation(tn, name):
     assert sum(s["flops"] * s["runs"] for s in steps) == pytest.approx(info["flops_exec"], rel=1e-12)
 
 
+def test_n64_steps_carry_padded_pair_tiles(tn):
+    # steps with N = 64 (one 64-column tile per output instance) carry the
+    # tile space of the tensor cores' column-tile pairs: each group's tiles
+    # padded to an even count, so the pad tiles are the groups of odd size
+    w = make_workload("diamond53_m12")
+    p = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, workspace_limit=120 << 30)
+    steps = p.tn_plan_steps()
+    n64 = [s for s in steps if s["nb"] == 6]
+    assert n64
+    for s in steps:
+        if s["nb"] != 6:
+            assert s["n_pair_tiles"] == 0
+            continue
+        n, g, mg, npt = s["n_inst"], s["n_groups"], s["max_group"], s["n_pair_tiles"]
+        odd = npt - n  # groups of odd size
+        assert npt % 2 == 0 and 0 <= odd <= g
+        assert odd % 2 == n % 2  # the sizes sum to n
+        assert 1 <= mg <= n and mg * g >= n
+        if mg == 1:
+            assert odd == g
+        if n == g * mg and mg % 2 == 0:
+            assert odd == 0
+    # groups of both parities in one step (the 2^10 x 2^9 x 2^6 step: 8113
+    # instances in 256 groups)
+    assert any(0 < s["n_pair_tiles"] - s["n_inst"] < s["n_groups"] for s in n64)
+
+
 def test_slice_batch_trades_memory_for_passes(tn):
     w = make_workload("grid5x6_m14")
     infos = [tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced, slice_batch_log2=b).info for b in (2, 5)]
