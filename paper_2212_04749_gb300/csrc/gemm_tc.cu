@@ -604,24 +604,19 @@ __device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int 
     // dictionary: column gc is column gc mod N of B instance gc / N, scaled
     // by 2^-eb only (the A exponent changes from group to group)
     const int ea = (!DICT && d.mxA) ? exp_of(__ldg(d.mxA + r.z)) : 0;
-    int64_t cb[BRES_MAX_B];  // this thread's column in each column tile: element offset in B, or -1
-    float sc[BRES_MAX_B];    // its power-of-two rescale 2^-(ea + eb), applied here instead of in the epilogue
-#pragma unroll
-    for (int ct = 0; ct < BRES_MAX_B; ++ct) {
-        const int64_t gc = int64_t(ct0 + ct) * TBN + bcol;
-        cb[ct] = -1;
-        sc[ct] = 1.f;
-        if (ct < nct && gc < ncols) {
-            const int ib = DICT ? int(gc >> d.nb) : __ldg(d.instab + r.x + (gc >> d.nb)).y;
-            cb[ct] = int64_t(ib) * d.sB + ((gc & (N - 1)) << d.kb);
-            sc[ct] = pow2f(-(ea + (d.mxB ? exp_of(__ldg(d.mxB + ib)) : 0)));
-        }
-    }
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int ct = 0; ct < BRES_MAX_B; ++ct) {
-        if (ct >= nct) break;
-        const int64_t bb = cb[ct];
+    for (int ct = 0; ct < nct && ct < BRES_MAX_B; ++ct) {
+        // this thread's column in the column tile: element offset in B (or
+        // -1) and its power-of-two rescale 2^-(ea + eb), applied here
+        // instead of in the epilogue
+        const int64_t gc = int64_t(ct0 + ct) * TBN + bcol;
+        int64_t bb = -1;
+        float s = 1.f;
+        if (gc < ncols) {
+            const int ib = DICT ? int(gc >> d.nb) : __ldg(d.instab + r.x + (gc >> d.nb)).y;
+            bb = int64_t(ib) * d.sB + ((gc & (N - 1)) << d.kb);
+            s = pow2f(-(ea + (d.mxB ? exp_of(__ldg(d.mxB + ib)) : 0)));
+        }
         for (int c = 0; c < nch; c += 2) {
             float4 p[2][2];
 #pragma unroll
@@ -632,7 +627,6 @@ __device__ __forceinline__ void load_bset(const StepDesc &d, const int4 &r, int 
                 p[i][0] = v ? __ldg(src) : z;
                 p[i][1] = v ? __ldg(src + 1) : z;
             }
-            const float s = sc[ct];
 #pragma unroll
             for (int i = 0; i < 2; ++i)
                 if (c + i < nch)
@@ -802,7 +796,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
             mbar_init(&X.afull[s], NAW);
             mbar_init(&X.taempty[s], 1);
         }
-        mbar_init(&X.bfull, NPROD);
+        mbar_init(&X.bfull, PREC == 1 ? NPROD : NPROD - NAW);  // the resident-B loaders
         mbar_init(&X.bempty, 1);
         for (int a = 0; a < NACC_MAX; ++a) {
             mbar_init(&X.tfull[a], 1);
@@ -964,36 +958,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
         auto aborted = [&]() { return __any_sync(0xffffffffu, *abort_flag != 0); };
       if constexpr (BRES || BPACK) {
         // resident B: at each group switch (once the MMAs stopped reading
-        // the previous group's B) load the group's B into the pool; BF16x3
-        // also splits every A chunk into a TMEM stage
-        int rs = 0, ts = 0;
-        uint32_t rph = 0, tph = 0, u = 0;
-        const int nts = BPACK ? nrs : NTS;
-        int64_t gprev = -1;
-        // packed B: only the chunk count matters here, no tile positions
-        TileIter it;
-        if (!BPACK && my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
-        for (int64_t l = 0; l < my_tiles && !aborted(); l += TSTEP) {
-            int4 r = make_int4(0, 0, 0, 0);
-            int64_t g = 0;  // the dictionary is loaded once
-            if constexpr (!BPACK) {
-                r = it.record(d);
-                if (MODE != 2) g = it.f;
+        // the previous group's B) the group's B goes into the pool -- BF16x3:
+        // by warps 4-7 (two k quads per thread), while warps 0-3 split every
+        // A chunk into a TMEM stage, so that neither loop carries the other's
+        // registers; TF32: by all producer warps
+        if (BRES && (PREC == 1 || warp >= NAW / 32)) {
+            uint32_t u = 0;
+            int64_t gprev = -1;
+            TileIter it;
+            if (my_tiles > 0) it.start(d, mtiles, n_tiles, tblk, PP);
+            for (int64_t l = 0; l < my_tiles && !aborted(); ++l) {
+                const int4 r = it.record(d);
+                const int64_t g = MODE == 2 ? 0 : it.f;  // the dictionary is loaded once
                 it.next(d, mtiles, n_tiles, tblk);
-            }
-            if (BRES && g != gprev) {
+                if (g == gprev) continue;
                 if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&X.bempty, (u - 1) & 1u))) {
                     give_up();
                     break;
                 }
-                if constexpr (BRES) load_bset<PREC, MODE == 2>(d, r, nch, K, sm + C::OFF_RAW + nrs * C::SLOT_RAW, bcol, kqb);
+                uint8_t *bset = sm + C::OFF_RAW + nrs * C::SLOT_RAW;
+                if constexpr (BRES) {
+                    if (PREC == 1) {
+                        load_bset<PREC, MODE == 2>(d, r, nch, K, bset, bcol, kqb);
+                    } else {
+#pragma unroll 1
+                        for (int q = (tid - NAW) >> 6; q < 4; q += 2)  // k quads 0, 2 or 1, 3
+                            load_bset<PREC, MODE == 2>(d, r, nch, K, bset, bcol, q);
+                    }
+                }
                 proxy_fence();
                 mbar_arrive(&X.bfull);
                 ++u;
                 gprev = g;
+                if (MODE == 2) break;  // the dictionary: one load for the launch
             }
-            if (awriter) {
-                bool ok = true;
+        } else if (awriter) {
+            int rs = 0, ts = 0;
+            uint32_t rph = 0, tph = 0;
+            const int nts = BPACK ? nrs : NTS;
+            bool ok = true;
+            for (int64_t l = 0; l < my_tiles && ok && !aborted(); l += TSTEP) {
                 for (int c = 0; c < nch; ++c) {
                     // the chunk has landed and the MMAs are done with the
                     // TMEM stage's previous chunk
@@ -1018,11 +1022,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)  // 20 warps: 96 registers (5 war
                         tph ^= 1u;
                     }
                 }
-                if (!ok) {
-                    give_up();
-                    break;
-                }
             }
+            if (!ok) give_up();
         }
       } else {
         int64_t issued = 0;
