@@ -27,7 +27,7 @@ struct StepDesc {
     int32_t nOutA, nOutB, nOut;
     int32_t sched;                // schedule variant of the step's kernel (0 or 1; the autotuner's choice)
     int32_t tc_resident_b;        // tensor cores: keep B resident in shared memory where it fits
-    int32_t tc_pair;              // tensor cores: packed B, schedule 0, N >= 128: column tiles in pairs (N = 256 MMAs)
+    int32_t tc_pair;              // tensor cores: BF16x3 packed B, schedule 0, N >= 64, K >= 256: column tiles in pairs (N = 256 MMAs)
     int32_t pad_;
     int64_t nInst;
     int64_t nInstB;               // B instances (tensor-core B dictionary)
