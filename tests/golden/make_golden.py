@@ -1,7 +1,7 @@
 """Write stored expected values computed by the CPU oracle only.
 
     python tests/golden/make_golden.py grid5x6_m14     # all amplitudes, state vector
-    python tests/golden/make_golden.py diamond53_m12   # 64 sampled amplitudes, TN oracle
+    python tests/golden/make_golden.py diamond53_m12   # 320 sampled amplitudes, TN oracle
     python tests/golden/make_golden.py grid6x7_m10     # 32 slices x 16 bitstrings, TN oracle
 
 ``<workload>_sv.txt``: one line per bitstring (input order) with the real
@@ -99,7 +99,7 @@ def _rows(k, n, seed):
     return sorted(int(x) for x in rng.choice(k, size=n, replace=False))
 
 
-def write_sample(name, n=64):
+def write_sample(name, n=320):
     """Amplitudes of n seeded bitstring rows from the unsliced TN oracle."""
     from oracle import tn
     from rqc.configs import make_workload
