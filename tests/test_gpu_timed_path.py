@@ -9,7 +9,7 @@ element by element with the oracle:
 * grid5x6_m14 (30 qubits, 14 cycles, 2^10 slices): all 4096 amplitudes
   against the complex128 state vector (tests/golden/grid5x6_m14_sv.txt);
 * diamond53_m12 (53 qubits, 12 cycles, 8192 bitstrings, the benchmark's
-  default workload): 64 sampled amplitudes against the complex128
+  default workload): 320 sampled amplitudes against the complex128
   tensor-network oracle (tests/golden/diamond53_m12_sample.json).
 
 Bounds: FP32 1e-5, BF16x3 (the mixed form) 1e-3 relative L2.
