@@ -259,6 +259,22 @@ def test_config_override_rules(tn):
     assert p.tn_plan_get_configs()[big] == base[big]
 
 
+def test_tensor_core_switches(tn):
+    # the resident-B and column-tile-pair switches act at launch time: a
+    # null plan is an argument error, and either setting leaves the plan's
+    # configuration choices as they were
+    lib = tn.load()
+    for fn in ("tn_plan_set_tc_resident_b", "tn_plan_set_tc_pairs"):
+        assert getattr(lib, fn)(None, 1) == tn.TN_EINVAL
+    w = make_workload("grid5x6_m14")
+    p = tn.Plan(w.circuit, w.bits, w.tree.ssa, w.tree.sliced)
+    base = p.tn_plan_get_configs()
+    for on in (False, True):
+        p.tn_plan_set_tc_pairs(on)
+        p.tn_plan_set_tc_resident_b(on)
+        assert np.array_equal(p.tn_plan_get_configs(), base)
+
+
 @pytest.mark.parametrize("name", ["grid3x4_m8", "grid5x6_m14"])
 def test_fused_chains_are_well_formed(tn, name):
     # every chain: consecutive producer -> consumer steps on the A side,
